@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the Lancelot server evaluation on B300.
+
+Metric: encrypted client-pair distances/s at N = 2^15, d = 2^20 (n = 10 clients, 64 ciphertexts
+per client, 45 pairs).  One step = one pass of the whole hot path over one batch of synthetic
+input: all 45 encrypted pair distances (sub, square, lazy relinearisation, rescale,
+rotate-and-sum with 14 rotations) plus the masked aggregate over all 64 chunks.  Inputs are
+generated on the device once (client ciphertexts: 4.8 GB, larger than L2) and stay resident.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode batched|perop] [--impl reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (weak scaling); rank 0 prints
+one JSON line.  The reference arm (--impl reference) times the CPU oracle on the host cores on a
+bounded sample per step (1 pair + 1 aggregate chunk), extrapolated to the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth as S  # noqa: E402
+
+METRIC = "encrypted client-pair distances/s (N=2^15, d=2^20); p50/p99 round latency"
+UNIT = "pairs/s"
+WORKLOAD = "plain_N32768_L14_K4_dnum4_n10_d2^20_64chunks_45pairs+masked_aggregate"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks sampler
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- workload (GPU)
+def build_workload(LC, g, w: S.Workload):
+    N = g.N
+    sched = [1] * (g.log_n - 1)
+    rots = LC.rotations_of_schedule(sched)
+    s = S.secret_key(w.seed, w.config, N)
+    pa, pe = S.pk_rand(w.seed, w.config, g.q, N)
+    pk = g.pk_gen(s, pa, pe)
+    evk = g.evk()
+    qp = g.q + g.p
+    evk.add(s, None, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, None))
+    for r in rots:
+        evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
+    W = S.client_updates(w)
+    X = S.split_chunks(W, g.slots)
+    cts = g.empty(w.n_clients, w.chunks, 2, g.nq, N)
+    flat = cts.view(w.n_clients * w.chunks, 2, g.nq, N)
+    for i in range(w.n_clients):
+        m = np.stack([g.encode(X[i, k], g.scale) for k in range(w.chunks)])
+        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [i], range(w.chunks), N)
+        g.encrypt(pk, m, r, e0, e1, out=flat[i * w.chunks:(i + 1) * w.chunks])
+    # KGC side (plaintext, untimed): Multi-Krum on the FP64 distances of the synthetic updates
+    from paper_2408_06197_b300 import kgc
+    d = np.array([[np.sum((W[i] - W[j]) ** 2) for j in range(w.n_clients)] for i in range(w.n_clients)])
+    sel = kgc.krum_select(d, w.f, w.n_select)
+    wts = kgc.mask_weights(w.n_clients, sel, average=True)
+    mm = np.stack([g.encode(np.full(g.slots, wts[i]), g.scale) for i in range(w.n_clients)])
+    r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), [S.MASK_CHUNK], N)
+    masks = g.encrypt(pk, mm, r, e0, e1)
+    return evk, cts, masks, sched, s
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(w: S.Workload, reps: int = 1):
+    """Times the oracle (as it stands) on 1 pair of distances + 1 aggregate chunk, `reps` times.
+    Returns (pairs/s extrapolated to the workload, per-rep seconds, threads)."""
+    import oracle as O
+    prm = O.params_production()
+    o = O.Context(prm)
+    threads = O.set_threads(0)
+    N = prm.N
+    sched = O.default_schedule(prm.slots)
+    s = S.secret_key(w.seed, w.config, N)
+    pk = o.pk_gen(s, *S.pk_rand(w.seed, w.config, prm.q, N))
+    qp = prm.q + prm.p
+    rlk = o.swk_gen(s, 0, *S.swk_rand(w.seed, w.config, qp, prm.dnum, N, None))
+    rk = {r: o.swk_gen(s, o.galois(r), *S.swk_rand(w.seed, w.config, qp, prm.dnum, N, r))
+          for r in O.rotations_of_schedule(sched)}
+    W = S.client_updates(w)
+    X = S.split_chunks(W, prm.slots)
+    # pair sample: clients 0 and 1, all chunks; aggregate sample: chunk 0 of every client
+    cts = np.zeros((2, w.chunks, 2, prm.L + 1, N), dtype=np.uint64)
+    agg_in = np.zeros((w.n_clients, 1, 2, prm.L + 1, N), dtype=np.uint64)
+    for i in range(w.n_clients):
+        ks = range(w.chunks) if i < 2 else [0]
+        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [i], ks, N)
+        for t, k in enumerate(ks):
+            ct = o.encrypt(pk, o.encode(X[i, k], prm.scale), r[t], e0[t], e1[t])
+            if i < 2:
+                cts[i, k] = ct
+            if k == 0:
+                agg_in[i, 0] = ct
+    masks = np.ascontiguousarray(agg_in[:, 0])
+    per = []
+    t_pair = t_chunk = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o.distances(cts, rlk, sched, rk)
+        t1 = time.perf_counter()
+        o.masked_aggregate(agg_in, masks, rlk)
+        t2 = time.perf_counter()
+        t_pair, t_chunk = t1 - t0, t2 - t1
+        per.append((t_pair, t_chunk))
+    t_pair = min(p[0] for p in per)
+    t_chunk = min(p[1] for p in per)
+    step = w.n_pairs * t_pair + w.chunks * t_chunk
+    return w.n_pairs / step, per, threads, step
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = S.PLAIN
+    total = args.warmup + args.steps
+    value, per, threads, step = oracle_sample(w, reps=total)
+    timed = per[args.warmup:]
+    t_pair = statistics.median(p[0] for p in timed)
+    t_chunk = statistics.median(p[1] for p in timed)
+    step = w.n_pairs * t_pair + w.chunks * t_chunk
+    value = w.n_pairs / step
+    sample = (f"per step: oracle distances of 1 pair (64 chunks, 14 rotations) and masked aggregate of 1 chunk; "
+              f"throughput extrapolated to 45 pairs + 64 chunks (median pair {t_pair:.2f} s, chunk {t_chunk:.2f} s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- kernel micro case
+def run_micro(args):
+    """Small isolated case for profiler captures (a few hundred MB on the device, inputs larger
+    than L2): 16 degree-2 triples relinearised and rescaled at level 14, 16 ciphertexts rotated at
+    level 13, and 960 limbs transformed forward and back.  Prints per-class timings."""
+    import torch
+    from paper_2408_06197_b300 import lancelot as LC
+    w = S.PLAIN
+    g = LC.Context.production()
+    N = g.N
+    s = S.secret_key(w.seed, w.config, N)
+    evk = g.evk()
+    qp = g.q + g.p
+    evk.add(s, None, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, None))
+    evk.add(s, 1, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, 1))
+    B = 16
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    ct3 = torch.randint(0, 1 << 40, (B, 3, g.nq, N), device="cuda", generator=gen)
+    cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
+    limbs = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
+    for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            g.profile_start()
+        x = g.to_eval(limbs, g.L)
+        g.to_coeff(x, g.L)
+        r2 = g.relin(evk, ct3, g.L)
+        g.rescale(r2, g.L)
+        for b in range(B):
+            g.rotate(evk, cts[b], g.L - 1, [1])
+    prof = g.profile_stop()
+    print(json.dumps({"micro": {k: {"ms_per_iter": v["ms"] / args.steps, "GBps": v["bytes"] / v["ms"] / 1e6
+                                    if v["ms"] else 0.0, "launches_per_iter": v["launches"] / args.steps}
+                                for k, v in prof.items()}}), flush=True)
+
+
+# ----------------------------------------------------------------------------- main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--mode", choices=["batched", "perop"], default="batched")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--micro", action="store_true", help="small isolated kernel case for profiler captures")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.micro:
+        run_micro(args)
+        return
+
+    import torch
+    from paper_2408_06197_b300 import lancelot as LC
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    w = S.PLAIN
+    with torch.cuda.stream(stream):
+        g = LC.Context.production(device=local, stream=stream)
+        evk, cts, masks, sched, s = build_workload(LC, g, w)
+        mode = LC.LC_MODE_BATCHED if args.mode == "batched" else LC.LC_MODE_PER_OP
+        out_d = g.empty(w.n_pairs, 2, g.L, g.N)
+        out_a = g.empty(w.chunks, 2, g.L, g.N)
+
+        def step():
+            g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=mode, out=out_d)
+            g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, mode=mode, out=out_a)
+
+        def barrier():
+            if world > 1:
+                torch.distributed.barrier()
+
+        for _ in range(args.warmup):
+            step()
+        g.sync()
+        clocks = Clocks(local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        time.sleep(0.3)
+        l0 = LC.launches()
+        g.profile_start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = g.profile_stop()
+        launches = LC.launches() - l0
+        barrier()
+        ck = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        ms_per_step = ms / args.steps
+        value = world * w.n_pairs * args.steps / (ms / 1e3)
+
+        # end-to-end through the C ABI: pinned host inputs copied in, results copied out, every step
+        e2e = None
+        if not args.no_e2e:
+            h_cts = LC.pinned_empty(tuple(cts.shape))
+            h_masks = LC.pinned_empty(tuple(masks.shape))
+            h_out_d = LC.pinned_empty(tuple(out_d.shape))
+            h_out_a = LC.pinned_empty(tuple(out_a.shape))
+            h_cts[...] = LC.torch_to_u64(cts)
+            h_masks[...] = LC.torch_to_u64(masks)
+            d_cts = torch.empty_like(cts)
+            d_masks = torch.empty_like(masks)
+
+            def e2e_step():
+                g.h2d(d_cts, h_cts)
+                g.h2d(d_masks, h_masks)
+                g.distances(evk, d_cts, w.n_clients, w.chunks, g.scale, mode=mode, out=out_d)
+                g.masked_aggregate(evk, d_cts, w.n_clients, w.chunks, g.scale, d_masks, g.scale, mode=mode,
+                                   out=out_a)
+                g.d2h(h_out_d, out_d)
+                g.d2h(h_out_a, out_a)
+                g.sync()
+
+            e2e_step()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                e2e_step()
+            el = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([el], device=f"cuda:{local}")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                el = float(t.item())
+            e2e = {"value": world * w.n_pairs * args.steps / el, "unit": UNIT,
+                   "h2d_bytes_per_step": int(h_cts.nbytes + h_masks.nbytes),
+                   "d2h_bytes_per_step": int(h_out_d.nbytes + h_out_a.nbytes)}
+            del d_cts, d_masks
+
+    # roofline of the dominant kernel class
+    hbm, peak_kind = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+            "launches": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(1, d["launches"]),
+            "share_of_step": d["ms"] / ms if ms > 0 else None,
+            "classes": {k: {"ms_per_step": v["ms"] / args.steps, "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9)
+                            if v["ms"] > 0 else 0.0, "launches_per_step": v["launches"] / args.steps}
+                        for k, v in prof.items()}}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": args.mode, "n_clients": w.n_clients, "d": w.d,
+                       "chunks": w.chunks, "pairs": w.n_pairs, "log_n": 15, "limbs_q": 15, "limbs_p": 4, "dnum": 4,
+                       "rotations": 14, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},
+            "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, per, threads, step_s = oracle_sample(w, reps=1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"1 pair (64 chunks) + 1 aggregate chunk, extrapolated to 45 pairs + 64 "
+                                          f"chunks; pair {per[0][0]:.2f} s, chunk {per[0][1]:.2f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * lancelot.h -- C ABI of the B300 (sm_103a) Lancelot server evaluation library.
+ *
+ * The library computes, on one GPU, the server side of "Lancelot" (arXiv 2408.06197):
+ * RNS-CKKS encrypted pairwise squared distances between client model updates
+ * (Algorithm 1, "Server Executes": HSub, HSquare, lazy relinearisation, rescale,
+ * rotate-and-sum with hoisted rotations) and the masked aggregate of the updates
+ * (Algorithm 1, "ServerUpdate", with the mask of Section "Masked-based Encrypted Sorting").
+ * Key generation, encryption and decryption (Section "CKKS Scheme Description") are
+ * provided for the key generation center and the clients.
+ *
+ * Conventions
+ *  - Every call returns an int status: LC_OK (0) or a negative LC_E* code.  No call aborts,
+ *    exits or traps; lc_last_error() gives a one-line message for the last failure on a ctx.
+ *  - Device work is asynchronous on the context's CUDA stream; lc_sync() waits and reports
+ *    deferred device errors.  A context is used by one host thread at a time.
+ *  - Ciphertext buffers are plain pointers in the layout [poly][limb][N] of uint64 words,
+ *    limb i holding the residues mod q_i, in the library's evaluation ("NTT") domain.
+ *    Batches are contiguous: [count][poly][limb][N].  Unless a parameter says "host or
+ *    device", pointers to ciphertext words are device pointers owned by the caller.
+ *    The canonical interchange form is the COEFFICIENT domain (lc_to_coeff / lc_to_eval):
+ *    it does not depend on the transform's root of unity or ordering.
+ *  - Scales are tracked by the caller (double); each evaluation call documents the
+ *    resulting scale.
+ *  - Randomness (secret, errors, uniform "a" polynomials, encryption ephemerals) is supplied
+ *    by the caller, so that results are reproducible bit for bit.
+ */
+#ifndef LANCELOT_H
+#define LANCELOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LC_OK 0
+#define LC_EINVAL (-1)   /* bad argument, size or layout */
+#define LC_ELEVEL (-2)   /* ciphertext level not valid for the call */
+#define LC_ESCALE (-3)   /* scale mismatch */
+#define LC_ENOMEM (-4)   /* allocation failed */
+#define LC_ECUDA (-5)    /* CUDA runtime error (message in lc_last_error) */
+#define LC_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define LC_EBUSY (-7)    /* resource in use */
+#define LC_EKEY (-8)     /* required evaluation key missing */
+
+typedef struct lc_ctx lc_ctx;
+typedef struct lc_evk lc_evk;
+
+/* RNS-CKKS parameters (Section "CKKS Scheme Description"): ring Z_Q[X]/(X^N+1) with
+ * N = 2^log_n (12 <= log_n <= 16), Q = q_0 ... q_L (n_q = L+1 limbs), special modulus
+ * P = p_0 ... p_{K-1} (n_p = K), dnum decomposition digits at level L, digit size
+ * alpha = ceil((L+1)/dnum).  Every prime is < 2^62 and = 1 mod 2N.  Arrays are copied. */
+typedef struct {
+    uint32_t log_n;
+    uint32_t n_q;
+    uint32_t n_p;
+    uint32_t dnum;
+    const uint64_t* q;
+    const uint64_t* p;
+} lc_params;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc returns a device
+ * pointer of at least `bytes` (256-byte aligned) or NULL; free releases it.  With a NULL
+ * allocator the library uses cudaMalloc / cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} lc_allocator;
+
+/* Evaluation modes of lc_distances / lc_masked_aggregate. */
+#define LC_MODE_PER_OP 0  /* one kernel sequence per HE operation, one pair / chunk at a time */
+#define LC_MODE_BATCHED 1 /* every pair / chunk in each launch, keys read once per launch */
+
+/* ---------------------------------------------------------------- parameters / context */
+
+/* The `count` largest `bits`-bit primes q = 1 mod 2^(log_n+1), after skipping `skip`,
+ * descending, into out[count] (host).  The paper fixes only the bit sizes (scale 2^40,
+ * Section "Baseline and Implementation details"); this is the library's deterministic rule. */
+int lc_gen_primes(uint32_t log_n, uint32_t bits, uint32_t skip, uint32_t count, uint64_t* out);
+
+/* Creates a context on `device` with all device tables (twiddles, base-conversion and
+ * rescale constants).  `stream` is a cudaStream_t (NULL = legacy default stream). */
+int lc_ctx_create(const lc_params* prm, int device, void* stream, const lc_allocator* alloc, lc_ctx** out);
+void lc_ctx_destroy(lc_ctx* ctx);
+int lc_set_stream(lc_ctx* ctx, void* stream);
+int lc_sync(lc_ctx* ctx);
+const char* lc_last_error(const lc_ctx* ctx);
+/* Key switches and ModUps issued since the last reset (lazy relinearisation and hoisting
+ * counters): out[0] = key switches, out[1] = ModUp decompositions. */
+int lc_counters(lc_ctx* ctx, uint64_t* out, int reset);
+
+/* Stream-ordered copies on the context's stream (no counterpart in the paper: the explicit
+ * host<->device transfers that replace unified memory, Appendix "CPU-GPU Computation Model").
+ * dst/src: device pointer on the device side; host side pageable or pinned. */
+int lc_memcpy_h2d(lc_ctx* ctx, uint64_t* dst_dev, const void* src_host, size_t bytes);
+int lc_memcpy_d2h(lc_ctx* ctx, void* dst_host, const uint64_t* src_dev, size_t bytes);
+/* Kernel launches issued by the library in this process so far (*out). */
+int lc_launches(uint64_t* out);
+/* Per-kernel-class device timing with CUDA events on the context stream (measurement only).
+ * start = 1 clears and starts recording; start = 0 stops, synchronises and writes per class
+ * (0 NTT, 1 ModUp, 2 key inner product, 3 ModDown, 4 tensor/accumulate, 5 rescale,
+ * 6 automorphism, 7 other) the summed milliseconds, algorithmic bytes and launches [8]. */
+int lc_profile(lc_ctx* ctx, int start, double* ms, double* bytes, uint64_t* launches);
+
+/* ---------------------------------------------------------------- keys (KGC side) */
+
+/* Public key pk = ([-a s + e]_Q, a) (Section "CKKS Scheme Description", Key generation).
+ * s: host int8[N] ternary; a: host uint64[n_q][N] coefficient domain, row i in [0, q_i);
+ * e: host int32[N]; pk_out: device uint64[2][n_q][N] (evaluation domain). */
+int lc_pk_gen(lc_ctx* ctx, const int8_t* s, const uint64_t* a, const int32_t* e, uint64_t* pk_out);
+
+int lc_evk_create(lc_ctx* ctx, lc_evk** out);
+void lc_evk_free(lc_evk* evk);
+/* Adds one switching key to evk (Key generation, Evaluation key; hybrid form with dnum
+ * digits): rotation < 0 adds the relinearisation key for s~ = s^2, rotation r >= 1 adds the
+ * key for s~ = phi_{5^r}(s) used by left rotation by r slots (Section "Dynamic Hoisting").
+ * Digit j, row t of Q U P: b = -a_j s + e_j + [q_t in D_j] (P mod q_t) s~, a = a_j.
+ * s: host int8[N]; a: host uint64[dnum][n_q+n_p][N] coefficient domain; e: host int32[dnum][N].
+ * The key is stored on the device (for rotations pre-permuted by phi^-1, see DESIGN).
+ * Returns LC_EBUSY if the key already exists. */
+int lc_evk_add(lc_ctx* ctx, lc_evk* evk, const int8_t* s, int32_t rotation, const uint64_t* a, const int32_t* e);
+/* Copies a key back in canonical form: host uint64[dnum][2][n_q+n_p][N], coefficient domain. */
+int lc_evk_export(lc_ctx* ctx, const lc_evk* evk, int32_t rotation, uint64_t* out);
+
+/* ---------------------------------------------------------------- client side */
+
+/* CKKS.Encode (Section "Batch Encoding and Decoding"): m = round(scale * sigma^-1(pi^-1(z)))
+ * for real z[len], len <= N/2 (zero padded); slot j <-> evaluation at xi^(5^j), xi = e^(i pi/N).
+ * FP64 on the host; m_out: host int64[N]. */
+int lc_encode(lc_ctx* ctx, const double* z, size_t len, double scale, int64_t* m_out);
+/* CKKS.Decode of integer coefficients given as doubles: z_j = m(xi^(5^j)) / scale, real part.
+ * m: host double[N]; z_out: host double[N/2]. */
+int lc_decode(lc_ctx* ctx, const double* m, double scale, double* z_out);
+
+/* CKKS.Enc (Section "CKKS Scheme Description", Encryption) of `count` plaintexts at level L:
+ * ct = (m + r u0 + e0, r u1 + e1) mod Q.  pk: device [2][n_q][N] from lc_pk_gen;
+ * m: host int64[count][N] (|m| < 2^63); r: host int8[count][N]; e0, e1: host int32[count][N];
+ * out: device uint64[count][2][n_q][N]. */
+int lc_encrypt(lc_ctx* ctx, const uint64_t* pk, const int64_t* m, const int8_t* r, const int32_t* e0,
+               const int32_t* e1, uint32_t count, uint64_t* out);
+
+/* CKKS.Dec (Section "CKKS Scheme Description", Decryption): residues of c0 + c1 s (+ c2 s^2)
+ * mod Q_level.  ct: device [deg][level+1][N] (deg 2 or 3); s: host int8[N];
+ * res_out: host uint64[level+1][N], coefficient domain. */
+int lc_decrypt(lc_ctx* ctx, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out);
+/* Centred CRT of residues[level+1][N] (host) to doubles m_out[N] (host), exact big-integer. */
+int lc_crt_to_double(lc_ctx* ctx, const uint64_t* res, uint32_t level, double* m_out);
+
+/* ---------------------------------------------------------------- interchange */
+
+/* In-place domain change of n_polys consecutive polynomials of level+1 limbs (device). */
+int lc_to_coeff(lc_ctx* ctx, uint64_t* data, uint32_t n_polys, uint32_t level);
+int lc_to_eval(lc_ctx* ctx, uint64_t* data, uint32_t n_polys, uint32_t level);
+
+/* ---------------------------------------------------------------- evaluation primitives */
+
+/* HAdd / HSub (Section "Private Distance Evaluation"): out = a +/- b mod q_i on n_polys
+ * polynomials of level+1 limbs (device). */
+int lc_add(lc_ctx* ctx, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out);
+int lc_sub(lc_ctx* ctx, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out);
+/* CKKS.Mult tensor (Appendix "Hardware Acceleration on Homomorphic Multiplication"):
+ * out[3] = (a0 b0, a0 b1 + a1 b0, a1 b1); scale multiplies.  Device buffers. */
+int lc_tensor(lc_ctx* ctx, const uint64_t* a, const uint64_t* b, uint32_t level, uint64_t* out);
+/* Relinearisation (Section "Lazy Relinearization"): count degree-2 triples [count][3][level+1][N]
+ * -> [count][2][level+1][N] via hybrid key switching with the relinearisation key. */
+int lc_relin(lc_ctx* ctx, const lc_evk* evk, const uint64_t* ct3, uint32_t count, uint32_t level, uint64_t* out);
+/* Rescale: drop q_level with centred rounding; [count][deg][level+1][N] -> [count][deg][level][N];
+ * the scale divides by q_level. */
+int lc_rescale(lc_ctx* ctx, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out);
+/* Hoisted rotations (Section "Dynamic Hoisting"): one ModUp of c1, then for each r in
+ * rots[n_rot] the left rotation by r slots: out[k] = (phi(c0) + KS0, KS1),
+ * out: device [n_rot][2][level+1][N]. */
+int lc_rotate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* ct, uint32_t level, uint32_t n_rot, const int32_t* rots,
+              uint64_t* out);
+/* Rotate-and-sum in place over `count` ciphertexts [count][2][level+1][N] with a hoisting
+ * schedule: groups[n_groups] with sum = log2(N/2); group g with stride s does
+ * y <- y + sum_{t=1}^{2^g-1} Rot_{t s}(y) from one ModUp, then s <- s 2^g.  All groups 1 is the
+ * plain log-step sum.  Afterwards every slot holds the sum of all slots. */
+int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
+                  const uint32_t* groups);
+
+/* ---------------------------------------------------------------- the method */
+
+/* Encrypted pairwise squared distances (Algorithm 1, "Server Executes"), for every pair i<j
+ * in lexicographic order: Dis = rotate_sum(rescale(relin(sum_k (ct_i[k] - ct_j[k])^2))).
+ * cts: host or device [n][chunks][2][n_q][N] at level L and scale `scale`;
+ * out: host or device [n(n-1)/2][2][n_q-1][N]; *out_scale = scale^2 / q_L.
+ * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits).  groups: hoisting schedule as in
+ * lc_rotate_sum (NULL = all ones).  evk must hold the relinearisation key and every
+ * rotation key the schedule needs. */
+int lc_distances(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
+                 uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale);
+
+/* Masked aggregate (Algorithm 1, "ServerUpdate"): for every chunk k,
+ * out[k] = rescale(relin(sum_i ct_i[k] (x) M_i)), M_i the mask ciphertext of client i
+ * (its selection weight in every slot, Section "Masked-based Encrypted Sorting").
+ * cts: host or device [n][chunks][2][n_q][N]; masks: host or device [n][2][n_q][N];
+ * out: host or device [chunks][2][n_q-1][N]; *out_scale = scale * mask_scale / q_L. */
+int lc_masked_aggregate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks,
+                        double scale, const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out,
+                        double* out_scale);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LANCELOT_H */

@@ -730,7 +730,8 @@ int or_distances(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, in
     }
     const int np_ = (int)pi.size();
     int status = 0;
-#pragma omp parallel for schedule(dynamic, 1)
+    // parallel over pairs when there are enough of them, else over limbs inside each step
+#pragma omp parallel for schedule(dynamic, 1) if (np_ >= omp_get_max_threads())
     for (int k = 0; k < np_; k++) {
         std::vector<u64> acc(3 * P, 0), diff(CT), sq(3 * P);
         for (int ch = 0; ch < chunks; ch++) {
@@ -757,7 +758,7 @@ void or_masked_aggregate(OrCtx* c, const u64* cts, int n, int chunks, const u64*
     const size_t N = c->N;
     const int L = c->nq - 1;
     const size_t P = (size_t)(L + 1) * N, CT = 2 * P;
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (chunks >= omp_get_max_threads())
     for (int k = 0; k < chunks; k++) {
         std::vector<u64> acc(3 * P, 0), prod(3 * P), r2(CT);
         for (int i = 0; i < n; i++) {

@@ -1,0 +1,1101 @@
+// C ABI of the Lancelot server evaluation (include/lancelot.h): context and device tables,
+// key generation, encryption, decryption, and the orchestration of the evaluation kernels
+// (hybrid key switching, relinearisation, rescale, hoisted rotations, distances, masked
+// aggregate).
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include "context.cuh"
+#include "host_math.hpp"
+#include "ops.cuh"
+
+using lc::hinv;
+using lc::hmul;
+using lc::hpow;
+using lc::shoup_of;
+
+namespace {
+
+int fail(lc_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define LC_CUDA(c, call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return fail((c), LC_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+int check_launch(lc_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, LC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return LC_OK;
+}
+
+RowMap rows_seq(int n, int mod0 = 0, int row0 = 0) {
+    RowMap m{};
+    m.n = n;
+    for (int i = 0; i < n; i++) {
+        m.row[i] = (uint16_t)(row0 + i);
+        m.mod[i] = (uint8_t)(mod0 + i);
+    }
+    return m;
+}
+
+bool is_host_ptr(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------ profiling
+static void prof_begin(lc_ctx* c) {
+    if (!c->prof_on) return;
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+        for (int i = 0; i < 256; i++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->ev_pool.push_back(e);
+        }
+    }
+    cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+}
+static void prof_end(lc_ctx* c, int cls, double bytes, uint64_t units) {
+    if (!c->prof_on) return;
+    cudaEvent_t a = c->ev_pool[c->ev_used], b = c->ev_pool[c->ev_used + 1];
+    cudaEventRecord(b, c->stream);
+    c->ev_used += 2;
+    c->prof.push_back(ProfRec{cls, a, b, bytes, units});
+}
+#define PROF(c, cls, bytes, units, stmt) \
+    do {                                 \
+        prof_begin(c);                   \
+        stmt;                            \
+        prof_end(c, cls, bytes, units);  \
+    } while (0)
+
+// ------------------------------------------------------------------------------------ memory
+void* lc_dev_alloc(lc_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (c->has_alloc) return c->alloc.alloc(bytes, c->alloc.user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void lc_dev_free(lc_ctx* c, void* p) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+}
+
+u64* lc_scratch(lc_ctx* c, size_t bytes) {
+    if (bytes <= c->scratch_bytes) return static_cast<u64*>(c->scratch);
+    cudaStreamSynchronize(c->stream);
+    lc_dev_free(c, c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    size_t want = bytes + bytes / 8;
+    c->scratch = lc_dev_alloc(c, want);
+    if (!c->scratch) return nullptr;
+    c->scratch_bytes = want;
+    return static_cast<u64*>(c->scratch);
+}
+
+static u64* stage_buf(lc_ctx* c, size_t bytes) {
+    if (bytes <= c->stage_bytes) return static_cast<u64*>(c->stage);
+    cudaStreamSynchronize(c->stream);
+    lc_dev_free(c, c->stage);
+    c->stage = lc_dev_alloc(c, bytes);
+    c->stage_bytes = c->stage ? bytes : 0;
+    return static_cast<u64*>(c->stage);
+}
+
+// ------------------------------------------------------------------------------------ tables
+static int build_tables(lc_ctx* c) {
+    const int nm = c->nq + c->np;
+    const size_t N = c->N;
+    std::vector<ulonglong2> fwd(nm * N), inv(nm * N);
+    c->mc_host.resize(nm);
+    std::vector<u64> pw(N), pwi(N);
+    for (int m = 0; m < nm; m++) {
+        const u64 q = c->mod[m];
+        const u64 psi = lc::root_2n(q, c->log_n), psi_inv = hinv(psi, q);
+        pw[0] = 1;
+        pwi[0] = 1;
+        for (size_t i = 1; i < N; i++) {
+            pw[i] = hmul(pw[i - 1], psi, q);
+            pwi[i] = hmul(pwi[i - 1], psi_inv, q);
+        }
+        const u64 ninv = hinv(N % q, q);
+        for (size_t k = 0; k < N; k++) {
+            const unsigned r = lc::bit_reverse((unsigned)k, c->log_n);
+            fwd[m * N + k] = make_ulonglong2(pw[r], shoup_of(pw[r], q));
+            inv[m * N + k] = make_ulonglong2(pwi[r], shoup_of(pwi[r], q));
+        }
+        const u64 last = hmul(pwi[lc::bit_reverse(1, c->log_n)], ninv, q);
+        inv[m * N + 0] = make_ulonglong2(last, shoup_of(last, q));
+        ModConst& mc = c->mc_host[m];
+        mc.q = q;
+        mc.two_q = 2 * q;
+        mc.r64 = (u64)(((lc::u128)1 << 64) % q);
+        mc.r64_sh = shoup_of(mc.r64, q);
+        mc.one_sh = (u64)(((lc::u128)1 << 64) / q);
+        mc.n_inv = ninv;
+        mc.n_inv_sh = shoup_of(ninv, q);
+        mc.pad = 0;
+    }
+    // ModUp tables [level][digit]
+    std::vector<ModUpTab> mu((size_t)c->nq * c->dnum);
+    for (int level = 0; level < c->nq; level++) {
+        const int nl = level + 1, rows = nl + c->np;
+        for (int j = 0; j < c->digits(level); j++) {
+            ModUpTab& t = mu[(size_t)level * c->dnum + j];
+            std::memset(&t, 0, sizeof(t));
+            const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, nl);
+            t.n_src = hi - lo;
+            for (int i = lo; i < hi; i++) {
+                const u64 qi = c->mod[i];
+                u64 prod = 1 % qi;
+                for (int k = lo; k < hi; k++)
+                    if (k != i) prod = hmul(prod, c->mod[k] % qi, qi);
+                const int s = i - lo;
+                t.src_row[s] = i;
+                t.src_q[s] = qi;
+                t.hinv[s] = hinv(prod, qi);
+                t.hinv_sh[s] = shoup_of(t.hinv[s], qi);
+            }
+            int nd = 0;
+            for (int r = 0; r < rows; r++) {
+                if (r >= lo && r < hi) continue;
+                const int mi = c->qp_mod(level, r);
+                const u64 mt = c->mod[mi];
+                t.dst_row[nd] = r;
+                t.dst_mod[nd] = mi;
+                for (int i = lo; i < hi; i++) {
+                    u64 prod = 1 % mt;
+                    for (int k = lo; k < hi; k++)
+                        if (k != i) prod = hmul(prod, c->mod[k] % mt, mt);
+                    const int s = i - lo;
+                    t.hat[s][nd] = prod;
+                    const u64 qh = hmul(c->mod[i] % mt, prod, mt);
+                    t.corr[s][nd] = qh ? mt - qh : 0;
+                }
+                nd++;
+            }
+            t.n_dst = nd;
+        }
+    }
+    // ModDown table
+    ModDownTab md;
+    std::memset(&md, 0, sizeof(md));
+    md.K = c->np;
+    for (int k = 0; k < c->np; k++) {
+        const u64 pk = c->mod[c->nq + k];
+        u64 prod = 1 % pk;
+        for (int m = 0; m < c->np; m++)
+            if (m != k) prod = hmul(prod, c->mod[c->nq + m] % pk, pk);
+        md.p[k] = pk;
+        md.phinv[k] = hinv(prod, pk);
+        md.phinv_sh[k] = shoup_of(md.phinv[k], pk);
+        for (int i = 0; i < c->nq; i++) {
+            const u64 qi = c->mod[i];
+            u64 ph = 1 % qi;
+            for (int m = 0; m < c->np; m++)
+                if (m != k) ph = hmul(ph, c->mod[c->nq + m] % qi, qi);
+            md.phat[k][i] = ph;
+            const u64 v = hmul(pk % qi, ph, qi);
+            md.corr[k][i] = v ? qi - v : 0;
+        }
+    }
+    for (int i = 0; i < c->nq; i++) {
+        const u64 qi = c->mod[i];
+        u64 P = 1 % qi;
+        for (int k = 0; k < c->np; k++) P = hmul(P, c->mod[c->nq + k] % qi, qi);
+        md.pinv[i] = hinv(P, qi);
+        md.pinv_sh[i] = shoup_of(md.pinv[i], qi);
+    }
+    // rescale tables
+    std::vector<RescaleTab> rs(c->nq);
+    for (int level = 0; level < c->nq; level++) {
+        RescaleTab& t = rs[level];
+        std::memset(&t, 0, sizeof(t));
+        const u64 ql = c->mod[level];
+        for (int i = 0; i < level; i++) {
+            const u64 qi = c->mod[i];
+            t.qinv[i] = hinv(ql % qi, qi);
+            t.qinv_sh[i] = shoup_of(t.qinv[i], qi);
+            const u64 r = ql % qi;
+            t.negq[i] = r ? qi - r : 0;
+        }
+    }
+    c->tw_fwd = static_cast<ulonglong2*>(lc_dev_alloc(c, fwd.size() * sizeof(ulonglong2)));
+    c->tw_inv = static_cast<ulonglong2*>(lc_dev_alloc(c, inv.size() * sizeof(ulonglong2)));
+    c->mc = static_cast<ModConst*>(lc_dev_alloc(c, nm * sizeof(ModConst)));
+    c->modup = static_cast<ModUpTab*>(lc_dev_alloc(c, mu.size() * sizeof(ModUpTab)));
+    c->moddown = static_cast<ModDownTab*>(lc_dev_alloc(c, sizeof(ModDownTab)));
+    c->rescale = static_cast<RescaleTab*>(lc_dev_alloc(c, rs.size() * sizeof(RescaleTab)));
+    if (!c->tw_fwd || !c->tw_inv || !c->mc || !c->modup || !c->moddown || !c->rescale)
+        return fail(c, LC_ENOMEM, "table allocation failed");
+    LC_CUDA(c, cudaMemcpy(c->tw_fwd, fwd.data(), fwd.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    LC_CUDA(c, cudaMemcpy(c->tw_inv, inv.data(), inv.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    LC_CUDA(c, cudaMemcpy(c->mc, c->mc_host.data(), nm * sizeof(ModConst), cudaMemcpyHostToDevice));
+    LC_CUDA(c, cudaMemcpy(c->modup, mu.data(), mu.size() * sizeof(ModUpTab), cudaMemcpyHostToDevice));
+    LC_CUDA(c, cudaMemcpy(c->moddown, &md, sizeof(ModDownTab), cudaMemcpyHostToDevice));
+    LC_CUDA(c, cudaMemcpy(c->rescale, rs.data(), rs.size() * sizeof(RescaleTab), cudaMemcpyHostToDevice));
+    return LC_OK;
+}
+
+// ------------------------------------------------------------------------------------ helpers
+static void ntt_fwd_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowMap& m) {
+    const double limbs = (double)batch * m.n;
+    PROF(c, PROF_NTT, limbs * c->N * 16.0, (uint64_t)limbs,
+         ntt_forward(base, stride, batch, m, c->log_n, c->tables(), c->stream));
+}
+static void ntt_inv_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowMap& m) {
+    const double limbs = (double)batch * m.n;
+    PROF(c, PROF_NTT, limbs * c->N * 16.0, (uint64_t)limbs,
+         ntt_inverse(base, stride, batch, m, c->log_n, c->tables(), c->stream));
+}
+static void ntt_polys(lc_ctx* c, u64* data, int n_polys, int nl, bool forward) {
+    RowMap m = rows_seq(nl);
+    if (forward) ntt_fwd_p(c, data, (size_t)nl * c->N, n_polys, m);
+    else ntt_inv_p(c, data, (size_t)nl * c->N, n_polys, m);
+}
+
+// Scratch words needed by key switching B polynomials at `level` with `n_out` outputs kept.
+static size_t ks_words(lc_ctx* c, int B, int level) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np, beta = c->digits(level);
+    return (size_t)B * N * (nl + (size_t)beta * rows + 2 * rows + 2 * nl);
+}
+
+struct KsBufs {
+    u64 *coef, *ext, *v, *conv;
+};
+
+static KsBufs ks_layout(lc_ctx* c, u64* base, int B, int level) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np, beta = c->digits(level);
+    KsBufs k;
+    k.coef = base;
+    k.ext = k.coef + (size_t)B * nl * N;
+    k.v = k.ext + (size_t)B * beta * rows * N;
+    k.conv = k.v + (size_t)B * 2 * rows * N;
+    return k;
+}
+
+// decomposition + ModUp of B polys d (evaluation domain, stride d_stride)
+static void ks_modup(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const KsBufs& k) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np, beta = c->digits(level);
+    cudaMemcpy2DAsync(k.coef, (size_t)nl * N * 8, d, d_stride * 8, (size_t)nl * N * 8, B, cudaMemcpyDeviceToDevice,
+                      c->stream);
+    ntt_polys(c, k.coef, B, nl, false);
+    PROF(c, PROF_MODUP, (double)B * N * 8.0 * ((double)nl + (double)beta * rows - nl), (uint64_t)B,
+         op_modup(c, k.coef, (size_t)nl * N, B, level, k.ext));
+    RowMap m{};
+    int n = 0;
+    for (int j = 0; j < beta; j++) {
+        const int lo = j * c->alpha, hi = std::min((j + 1) * c->alpha, nl);
+        for (int t = 0; t < rows; t++) {
+            if (t >= lo && t < hi) continue;
+            m.row[n] = (uint16_t)(j * rows + t);
+            m.mod[n] = (uint8_t)c->qp_mod(level, t);
+            n++;
+        }
+    }
+    m.n = n;
+    ntt_fwd_p(c, k.ext, (size_t)beta * rows * N, B, m);
+    c->n_modup += (uint64_t)B;
+}
+
+// inner product with one key + ModDown; W[b] = (add0 + MD(v0), add1 + MD(v1))
+static void ks_apply(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const u64* key, const KsBufs& k,
+                     const u64* add0, const u64* add1, size_t add_stride, u64* w, size_t w_stride) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np;
+    const int beta = c->digits(level);
+    PROF(c, PROF_INNER, (double)N * 8.0 * ((double)B * beta * rows + 2.0 * beta * rows + 2.0 * B * rows), (uint64_t)B,
+         op_inner(c, k.ext, d, d_stride, B, level, key, k.v));
+    RowMap mp{};
+    mp.n = 2 * c->np;
+    for (int p = 0; p < 2; p++)
+        for (int m = 0; m < c->np; m++) {
+            mp.row[p * c->np + m] = (uint16_t)(p * rows + nl + m);
+            mp.mod[p * c->np + m] = (uint8_t)(c->nq + m);
+        }
+    ntt_inv_p(c, k.v, (size_t)2 * rows * N, B, mp);
+    PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * (c->np + nl), (uint64_t)B,
+         op_moddown_bconv(c, k.v, B, level, k.conv));
+    ntt_polys(c, k.conv, 2 * B, nl, true);
+    PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * nl * (add0 ? 4.0 : 3.0), (uint64_t)B,
+         op_moddown_combine(c, k.v, k.conv, B, level, add0, add1, add_stride, w, w_stride));
+    c->n_keyswitch += (uint64_t)B;
+}
+
+static const SwKey* find_key(const lc_evk* evk, int32_t id) {
+    auto it = evk->keys.find(id);
+    return it == evk->keys.end() ? nullptr : &it->second;
+}
+
+// relinearise B triples ct3 [B][3][nl][N] into out [B][2][nl][N] (tmp = ks scratch)
+static int do_relin(lc_ctx* c, const lc_evk* evk, const u64* ct3, int B, int level, u64* out, u64* tmp) {
+    const SwKey* k = find_key(evk, -1);
+    if (!k) return fail(c, LC_EKEY, "relinearisation key missing");
+    const size_t P = (size_t)(level + 1) * c->N;
+    KsBufs kb = ks_layout(c, tmp, B, level);
+    ks_modup(c, ct3 + 2 * P, 3 * P, B, level, kb);
+    ks_apply(c, ct3 + 2 * P, 3 * P, B, level, k->data, kb, ct3, ct3 + P, 3 * P, out, 2 * P);
+    return LC_OK;
+}
+
+static size_t rescale_words(lc_ctx* c, int B, int deg, int level) {
+    return (size_t)B * deg * c->N * (1 + level);
+}
+
+// rescale B ciphertexts [B][deg][level+1][N] -> out [B][deg][level][N]
+static void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u64* tmp) {
+    const size_t N = c->N;
+    u64* lastc = tmp;
+    u64* r = tmp + (size_t)B * deg * N;
+    cudaMemcpy2DAsync(lastc, N * 8, ct + (size_t)level * N, (size_t)(level + 1) * N * 8, N * 8, (size_t)B * deg,
+                      cudaMemcpyDeviceToDevice, c->stream);
+    RowMap one = rows_seq(1, level);
+    ntt_inv_p(c, lastc, N, B * deg, one);
+    PROF(c, PROF_RESCALE, (double)N * 8.0 * B * deg * (1.0 + level), (uint64_t)B,
+         op_rescale_prep(c, lastc, B * deg, level, r));
+    ntt_polys(c, r, B * deg, level, true);
+    PROF(c, PROF_RESCALE, (double)N * 8.0 * B * deg * (3.0 * level), (uint64_t)B,
+         op_rescale_combine(c, ct, r, B, deg, level, out));
+}
+
+static size_t rotsum_words(lc_ctx* c, int B, int level, int max_group) {
+    const size_t wsz = (size_t)B * 2 * (level + 1) * c->N;
+    return ks_words(c, B, level) + wsz * (((size_t)1 << max_group) - 1);
+}
+
+static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level, int n_groups, const uint32_t* groups,
+                         u64* tmp) {
+    const size_t N = c->N;
+    const size_t P = (size_t)(level + 1) * N;
+    KsBufs kb = ks_layout(c, tmp, B, level);
+    u64* wbase = tmp + ks_words(c, B, level);
+    long stride = 1;
+    for (int gi = 0; gi < n_groups; gi++) {
+        const int g = (int)(groups ? groups[gi] : 1);
+        const int cnt = (1 << g) - 1;
+        std::vector<const SwKey*> keys(cnt);
+        for (int t = 1; t <= cnt; t++) {
+            keys[t - 1] = find_key(evk, (int32_t)(t * stride));
+            if (!keys[t - 1]) return fail(c, LC_EKEY, "rotation key " + std::to_string(t * stride) + " missing");
+        }
+        ks_modup(c, y + P, 2 * P, B, level, kb);
+        for (int t = 0; t < cnt; t++)
+            ks_apply(c, y + P, 2 * P, B, level, keys[t]->data, kb, y, nullptr, 2 * P, wbase + (size_t)t * B * 2 * P,
+                     2 * P);
+        for (int t = 0; t < cnt; t++)
+            PROF(c, PROF_AUTO, (double)B * 2 * P * 8.0 * 3.0, (uint64_t)B,
+                 op_gather(c, wbase + (size_t)t * B * 2 * P, y, B * 2, level + 1, keys[t]->galois, true));
+        stride <<= g;
+    }
+    return LC_OK;
+}
+
+static uint64_t galois_of(lc_ctx* c, long r) { return hpow(5, (u64)r, 2 * (u64)c->N); }
+
+// ------------------------------------------------------------------------------------ host FP64 encode / decode
+namespace {
+void fft_inplace(std::vector<std::complex<double>>& a, bool inverse) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; i++) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = 2 * M_PI / (double)len * (inverse ? 1 : -1);
+        const size_t half = len / 2;
+        std::vector<std::complex<double>> w(half);
+        for (size_t k = 0; k < half; k++) w[k] = std::complex<double>(std::cos(ang * k), std::sin(ang * k));
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < half; k++) {
+                std::complex<double> u = a[i + k], v = a[i + k + half] * w[k];
+                a[i + k] = u + v;
+                a[i + k + half] = u - v;
+            }
+    }
+}
+
+// multi-word unsigned integer (little-endian 64-bit words)
+struct Big {
+    std::vector<u64> w;
+    void mul_add(u64 m, u64 add) {
+        lc::u128 carry = add;
+        for (auto& x : w) {
+            lc::u128 t = (lc::u128)x * m + carry;
+            x = (u64)t;
+            carry = t >> 64;
+        }
+        if (carry) w.push_back((u64)carry);
+    }
+    int cmp(const Big& o) const {
+        size_t n = std::max(w.size(), o.w.size());
+        for (size_t i = n; i-- > 0;) {
+            u64 a = i < w.size() ? w[i] : 0, b = i < o.w.size() ? o.w[i] : 0;
+            if (a != b) return a < b ? -1 : 1;
+        }
+        return 0;
+    }
+    Big sub(const Big& o) const {  // *this - o, requires *this >= o
+        Big r;
+        r.w.resize(w.size());
+        u64 borrow = 0;
+        for (size_t i = 0; i < w.size(); i++) {
+            u64 b = i < o.w.size() ? o.w[i] : 0;
+            lc::u128 t = (lc::u128)w[i] - b - borrow;
+            r.w[i] = (u64)t;
+            borrow = (t >> 64) ? 1 : 0;
+        }
+        return r;
+    }
+    Big half() const {
+        Big r;
+        r.w.resize(w.size());
+        for (size_t i = 0; i < w.size(); i++) {
+            r.w[i] = w[i] >> 1;
+            if (i + 1 < w.size()) r.w[i] |= w[i + 1] << 63;
+        }
+        return r;
+    }
+    double to_double() const {
+        long double v = 0;
+        for (size_t i = w.size(); i-- > 0;) v = v * 18446744073709551616.0L + (long double)w[i];
+        return (double)v;
+    }
+};
+}  // namespace
+
+// ------------------------------------------------------------------------------------ C ABI
+extern "C" {
+
+int lc_gen_primes(uint32_t log_n, uint32_t bits, uint32_t skip, uint32_t count, uint64_t* out) {
+    if (!out || bits < 20 || bits > 62 || log_n < 1 || log_n > 20) return LC_EINVAL;
+    std::vector<u64> v;
+    if (!lc::ntt_primes((int)log_n, (int)bits, (int)skip, (int)count, v)) return LC_EINVAL;
+    std::copy(v.begin(), v.end(), out);
+    return LC_OK;
+}
+
+int lc_ctx_create(const lc_params* prm, int device, void* stream, const lc_allocator* alloc, lc_ctx** out) {
+    if (!prm || !out || !prm->q || !prm->p) return LC_EINVAL;
+    if (prm->log_n < 12 || prm->log_n > 16 || prm->n_q < 2 || prm->n_q > 24 || prm->n_p < 1 || prm->n_p > LC_MAX_P ||
+        prm->dnum < 1 || prm->dnum > prm->n_q)
+        return LC_EINVAL;
+    lc_ctx* c = new (std::nothrow) lc_ctx();
+    if (!c) return LC_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    c->log_n = (int)prm->log_n;
+    c->N = (size_t)1 << prm->log_n;
+    c->nq = (int)prm->n_q;
+    c->np = (int)prm->n_p;
+    c->dnum = (int)prm->dnum;
+    c->alpha = (c->nq + c->dnum - 1) / c->dnum;
+    if (c->alpha > LC_MAX_SRC || c->nq + c->np > LC_MAX_DST) {
+        delete c;
+        return LC_EINVAL;
+    }
+    const u64 twoN = 2 * (u64)c->N;
+    for (uint32_t i = 0; i < prm->n_q; i++) c->mod.push_back(prm->q[i]);
+    for (uint32_t i = 0; i < prm->n_p; i++) c->mod.push_back(prm->p[i]);
+    for (u64 m : c->mod) {
+        if (m >= ((u64)1 << 62) || m % twoN != 1 || !lc::probable_prime(m)) {
+            delete c;
+            return LC_EINVAL;
+        }
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LC_ECUDA;
+    }
+    int st = build_tables(c);
+    if (st != LC_OK) {
+        lc_ctx_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LC_OK;
+}
+
+void lc_ctx_destroy(lc_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    lc_dev_free(c, c->tw_fwd);
+    lc_dev_free(c, c->tw_inv);
+    lc_dev_free(c, c->mc);
+    lc_dev_free(c, c->modup);
+    lc_dev_free(c, c->moddown);
+    lc_dev_free(c, c->rescale);
+    lc_dev_free(c, c->scratch);
+    lc_dev_free(c, c->stage);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+int lc_set_stream(lc_ctx* c, void* stream) {
+    if (!c) return LC_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return LC_OK;
+}
+
+int lc_sync(lc_ctx* c) {
+    if (!c) return LC_EINVAL;
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "deferred");
+}
+
+const char* lc_last_error(const lc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int lc_counters(lc_ctx* c, uint64_t* out, int reset) {
+    if (!c || !out) return LC_EINVAL;
+    out[0] = c->n_keyswitch;
+    out[1] = c->n_modup;
+    if (reset) c->n_keyswitch = c->n_modup = 0;
+    return LC_OK;
+}
+
+int lc_pk_gen(lc_ctx* c, const int8_t* s, const uint64_t* a, const int32_t* e, uint64_t* pk) {
+    if (!c || !s || !a || !e || !pk) return fail(c, LC_EINVAL, "lc_pk_gen: null argument");
+    const size_t N = c->N;
+    const int nq = c->nq;
+    u64* t = lc_scratch(c, (size_t)N * 8 * (3 * nq + 2) + N * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* sr = t;
+    u64* er = sr + (size_t)nq * N;
+    u64* raw = er + (size_t)nq * N;  // int8/int32 staging
+    std::vector<int> mods(nq);
+    for (int i = 0; i < nq; i++) mods[i] = i;
+    LC_CUDA(c, cudaMemcpyAsync(raw, s, N, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), 1, mods.data(), nq, sr);
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    LC_CUDA(c, cudaMemcpyAsync(raw, e, N * 4, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i32(c, reinterpret_cast<const int32_t*>(raw), 1, mods.data(), nq, er);
+    u64* ap = pk + (size_t)nq * N;
+    LC_CUDA(c, cudaMemcpyAsync(ap, a, (size_t)nq * N * 8, cudaMemcpyHostToDevice, c->stream));
+    ntt_polys(c, sr, 1, nq, true);
+    ntt_polys(c, er, 1, nq, true);
+    ntt_polys(c, ap, 1, nq, true);
+    op_key_combine(c, ap, sr, er, nullptr, nullptr, mods.data(), nq, pk);
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_pk_gen");
+}
+
+int lc_evk_create(lc_ctx* c, lc_evk** out) {
+    if (!c || !out) return LC_EINVAL;
+    lc_evk* k = new (std::nothrow) lc_evk();
+    if (!k) return LC_ENOMEM;
+    k->ctx = c;
+    *out = k;
+    return LC_OK;
+}
+
+void lc_evk_free(lc_evk* k) {
+    if (!k) return;
+    cudaStreamSynchronize(k->ctx->stream);
+    for (auto& kv : k->keys) lc_dev_free(k->ctx, kv.second.data);
+    delete k;
+}
+
+int lc_evk_add(lc_ctx* c, lc_evk* evk, const int8_t* s, int32_t rotation, const uint64_t* a, const int32_t* e) {
+    if (!c || !evk || !s || !a || !e) return fail(c, LC_EINVAL, "lc_evk_add: null argument");
+    const int32_t id = rotation < 0 ? -1 : rotation;
+    if (rotation == 0) return fail(c, LC_EINVAL, "rotation 0 has no key");
+    if (evk->keys.count(id)) return fail(c, LC_EBUSY, "key exists");
+    const size_t N = c->N;
+    const int rows = c->nq + c->np;
+    const size_t keywords = (size_t)c->dnum * 2 * rows * N;
+    u64* key = static_cast<u64*>(lc_dev_alloc(c, keywords * 8));
+    if (!key) return fail(c, LC_ENOMEM, "key allocation");
+    u64* t = lc_scratch(c, ((size_t)rows * 4 + 1) * N * 8 + keywords * 8);
+    if (!t) {
+        lc_dev_free(c, key);
+        return fail(c, LC_ENOMEM, "scratch");
+    }
+    u64* sr = t;
+    u64* st = sr + (size_t)rows * N;
+    u64* er = st + (size_t)rows * N;
+    u64* raw = er + (size_t)rows * N;
+    u64* tmpkey = raw + N;
+    std::vector<int> mods(rows);
+    for (int i = 0; i < rows; i++) mods[i] = i;
+    const uint64_t g = id < 0 ? 0 : galois_of(c, id);
+    LC_CUDA(c, cudaMemcpyAsync(raw, s, N, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), 1, mods.data(), rows, sr);
+    {
+        RowMap m = rows_seq(rows);
+        ntt_fwd_p(c, sr, 0, 1, m);
+    }
+    if (id < 0) op_square_rows(c, sr, st, mods.data(), rows);
+    else op_permute_rows(c, sr, st, rows, g);
+    std::vector<u64> Pmod(rows);
+    u64* dst = id < 0 ? key : tmpkey;
+    for (int j = 0; j < c->dnum; j++) {
+        for (int r = 0; r < rows; r++) {
+            const u64 m = c->mod[r];
+            u64 P = 1 % m;
+            for (int k = 0; k < c->np; k++) P = hmul(P, c->mod[c->nq + k] % m, m);
+            const bool in_digit = r < c->nq && r / c->alpha == j;
+            Pmod[r] = in_digit ? P : 0;
+        }
+        u64* kb = dst + (size_t)j * 2 * rows * N;
+        u64* ka = kb + (size_t)rows * N;
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(ka, a + (size_t)j * rows * N, (size_t)rows * N * 8, cudaMemcpyHostToDevice, c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(raw, e + (size_t)j * N, N * 4, cudaMemcpyHostToDevice, c->stream));
+        op_to_rns_i32(c, reinterpret_cast<const int32_t*>(raw), 1, mods.data(), rows, er);
+        RowMap m = rows_seq(rows);
+        ntt_fwd_p(c, ka, 0, 1, m);
+        ntt_fwd_p(c, er, 0, 1, m);
+        op_key_combine(c, ka, sr, er, st, Pmod.data(), mods.data(), rows, kb);
+    }
+    if (id >= 0) {
+        // store phi_g^-1(key): a hoisted rotation then permutes only its two output polys
+        const uint64_t ginv = hpow(g, (u64)c->N / 2 - 1, 2 * (u64)c->N);  // g^(N/2-1) = g^-1 mod 2N
+        op_permute_rows(c, tmpkey, key, c->dnum * 2 * rows, ginv);
+    }
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    int st_ = check_launch(c, "lc_evk_add");
+    if (st_ != LC_OK) {
+        lc_dev_free(c, key);
+        return st_;
+    }
+    evk->keys[id] = SwKey{key, g};
+    return LC_OK;
+}
+
+int lc_evk_export(lc_ctx* c, const lc_evk* evk, int32_t rotation, uint64_t* out) {
+    if (!c || !evk || !out) return fail(c, LC_EINVAL, "lc_evk_export: null argument");
+    const SwKey* k = find_key(evk, rotation < 0 ? -1 : rotation);
+    if (!k) return fail(c, LC_EKEY, "key missing");
+    const size_t N = c->N;
+    const int rows = c->nq + c->np;
+    const size_t words = (size_t)c->dnum * 2 * rows * N;
+    u64* t = lc_scratch(c, words * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    if (k->galois) op_permute_rows(c, k->data, t, c->dnum * 2 * rows, k->galois);
+    else LC_CUDA(c, cudaMemcpyAsync(t, k->data, words * 8, cudaMemcpyDeviceToDevice, c->stream));
+    RowMap m = rows_seq(rows);
+    ntt_inv_p(c, t, (size_t)rows * N, c->dnum * 2, m);
+    LC_CUDA(c, cudaMemcpyAsync(out, t, words * 8, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_evk_export");
+}
+
+int lc_encode(lc_ctx* c, const double* z, size_t len, double scale, int64_t* m_out) {
+    if (!c || !m_out || (len && !z) || len > c->N / 2) return fail(c, LC_EINVAL, "lc_encode: bad argument");
+    const size_t N = c->N, twoN = 2 * N;
+    std::vector<std::complex<double>> A(twoN);
+    u64 e = 1;
+    for (size_t j = 0; j < N / 2; j++) {
+        A[e] = std::complex<double>(j < len ? scale * z[j] : 0.0, 0.0);
+        e = (e * 5) % twoN;
+    }
+    fft_inplace(A, false);
+    for (size_t k = 0; k < N; k++) m_out[k] = (int64_t)std::nearbyint(2.0 / (double)N * A[k].real());
+    return LC_OK;
+}
+
+int lc_decode(lc_ctx* c, const double* m, double scale, double* z_out) {
+    if (!c || !m || !z_out) return fail(c, LC_EINVAL, "lc_decode: null argument");
+    const size_t N = c->N, twoN = 2 * N;
+    std::vector<std::complex<double>> A(twoN);
+    for (size_t k = 0; k < N; k++) A[k] = m[k];
+    fft_inplace(A, true);
+    u64 e = 1;
+    for (size_t j = 0; j < N / 2; j++) {
+        z_out[j] = A[e].real() / scale;
+        e = (e * 5) % twoN;
+    }
+    return LC_OK;
+}
+
+int lc_encrypt(lc_ctx* c, const uint64_t* pk, const int64_t* m, const int8_t* r, const int32_t* e0, const int32_t* e1,
+               uint32_t count, uint64_t* out) {
+    if (!c || !pk || !m || !r || !e0 || !e1 || !out) return fail(c, LC_EINVAL, "lc_encrypt: null argument");
+    if (count == 0) return LC_OK;
+    const size_t N = c->N;
+    const int nq = c->nq;
+    const size_t P = (size_t)nq * N;
+    // process in slices that fit a modest scratch
+    const uint32_t slice = std::max<uint32_t>(1, std::min<uint32_t>(count, 64));
+    u64* t = lc_scratch(c, ((size_t)4 * slice * P + (size_t)slice * N) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    std::vector<int> mods(nq);
+    for (int i = 0; i < nq; i++) mods[i] = i;
+    for (uint32_t b0 = 0; b0 < count; b0 += slice) {
+        const int B = (int)std::min(slice, count - b0);
+        u64* mr = t;
+        u64* rr = mr + (size_t)slice * P;
+        u64* x0 = rr + (size_t)slice * P;
+        u64* x1 = x0 + (size_t)slice * P;
+        u64* raw = x1 + (size_t)slice * P;
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(raw, m + (size_t)b0 * N, (size_t)B * N * 8, cudaMemcpyHostToDevice, c->stream));
+        op_to_rns_i64(c, reinterpret_cast<const int64_t*>(raw), B, mods.data(), nq, mr);
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(raw, r + (size_t)b0 * N, (size_t)B * N, cudaMemcpyHostToDevice, c->stream));
+        op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), B, mods.data(), nq, rr);
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(raw, e0 + (size_t)b0 * N, (size_t)B * N * 4, cudaMemcpyHostToDevice, c->stream));
+        op_to_rns_i32(c, reinterpret_cast<const int32_t*>(raw), B, mods.data(), nq, x0);
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        LC_CUDA(c, cudaMemcpyAsync(raw, e1 + (size_t)b0 * N, (size_t)B * N * 4, cudaMemcpyHostToDevice, c->stream));
+        op_to_rns_i32(c, reinterpret_cast<const int32_t*>(raw), B, mods.data(), nq, x1);
+        if (B == (int)slice) {
+            ntt_polys(c, mr, 4 * B, nq, true);  // mr, rr, x0, x1 are consecutive regions of `slice` polys
+        } else {
+            ntt_polys(c, mr, B, nq, true);
+            ntt_polys(c, rr, B, nq, true);
+            ntt_polys(c, x0, B, nq, true);
+            ntt_polys(c, x1, B, nq, true);
+        }
+        op_enc_combine(c, mr, rr, x0, x1, pk, B, nq, out + (size_t)b0 * 2 * P);
+    }
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_encrypt");
+}
+
+int lc_decrypt(lc_ctx* c, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out) {
+    if (!c || !s || !ct || !res_out || deg < 2 || deg > 3) return fail(c, LC_EINVAL, "lc_decrypt: bad argument");
+    if ((int)level >= c->nq) return fail(c, LC_ELEVEL, "level out of range");
+    const size_t N = c->N;
+    const int nl = (int)level + 1;
+    u64* t = lc_scratch(c, ((size_t)2 * nl + 1) * N * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* sr = t;
+    u64* acc = sr + (size_t)nl * N;
+    u64* raw = acc + (size_t)nl * N;
+    std::vector<int> mods(nl);
+    for (int i = 0; i < nl; i++) mods[i] = i;
+    LC_CUDA(c, cudaMemcpyAsync(raw, s, N, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), 1, mods.data(), nl, sr);
+    ntt_polys(c, sr, 1, nl, true);
+    op_dec_combine(c, ct, sr, (int)deg, nl, acc);
+    ntt_polys(c, acc, 1, nl, false);
+    LC_CUDA(c, cudaMemcpyAsync(res_out, acc, (size_t)nl * N * 8, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_decrypt");
+}
+
+int lc_crt_to_double(lc_ctx* c, const uint64_t* res, uint32_t level, double* m_out) {
+    if (!c || !res || !m_out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_crt_to_double: bad argument");
+    const size_t N = c->N;
+    const int nl = (int)level + 1;
+    // Garner mixed radix: x = v0 + v1 q0 + v2 q0 q1 + ...
+    std::vector<std::vector<u64>> inv(nl, std::vector<u64>(nl, 0));
+    for (int i = 0; i < nl; i++)
+        for (int k = 0; k < i; k++) inv[k][i] = hinv(c->mod[k] % c->mod[i], c->mod[i]);
+    Big Q;
+    Q.w = {1};
+    for (int i = 0; i < nl; i++) Q.mul_add(c->mod[i], 0);
+    const Big half = Q.half();
+    std::vector<u64> v(nl);
+    for (size_t x = 0; x < N; x++) {
+        for (int i = 0; i < nl; i++) {
+            const u64 qi = c->mod[i];
+            u64 t = res[(size_t)i * N + x] % qi;
+            for (int k = 0; k < i; k++) {
+                t = (t + qi - v[k] % qi) % qi;
+                t = hmul(t, inv[k][i], qi);
+            }
+            v[i] = t;
+        }
+        Big X;
+        X.w = {v[nl - 1]};
+        for (int i = nl - 2; i >= 0; i--) X.mul_add(c->mod[i], v[i]);
+        if (X.cmp(half) > 0) m_out[x] = -Q.sub(X).to_double();
+        else m_out[x] = X.to_double();
+    }
+    return LC_OK;
+}
+
+int lc_to_coeff(lc_ctx* c, uint64_t* data, uint32_t n_polys, uint32_t level) {
+    if (!c || !data || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_to_coeff: bad argument");
+    ntt_polys(c, data, (int)n_polys, (int)level + 1, false);
+    return check_launch(c, "lc_to_coeff");
+}
+
+int lc_to_eval(lc_ctx* c, uint64_t* data, uint32_t n_polys, uint32_t level) {
+    if (!c || !data || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_to_eval: bad argument");
+    ntt_polys(c, data, (int)n_polys, (int)level + 1, true);
+    return check_launch(c, "lc_to_eval");
+}
+
+int lc_add(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out) {
+    if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_add: bad argument");
+    op_addsub(c, a, b, out, (int)n_polys, (int)level + 1, false);
+    return check_launch(c, "lc_add");
+}
+
+int lc_sub(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out) {
+    if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_sub: bad argument");
+    op_addsub(c, a, b, out, (int)n_polys, (int)level + 1, true);
+    return check_launch(c, "lc_sub");
+}
+
+int lc_tensor(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t level, uint64_t* out) {
+    if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_tensor: bad argument");
+    op_tensor(c, a, b, out, (int)level + 1);
+    return check_launch(c, "lc_tensor");
+}
+
+int lc_relin(lc_ctx* c, const lc_evk* evk, const uint64_t* ct3, uint32_t count, uint32_t level, uint64_t* out) {
+    if (!c || !evk || !ct3 || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_relin: bad argument");
+    if (count == 0) return LC_OK;
+    u64* t = lc_scratch(c, ks_words(c, (int)count, (int)level) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    int st = do_relin(c, evk, ct3, (int)count, (int)level, out, t);
+    if (st) return st;
+    return check_launch(c, "lc_relin");
+}
+
+int lc_rescale(lc_ctx* c, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out) {
+    if (!c || !ct || !out || level < 1 || (int)level >= c->nq || deg < 1 || deg > 3)
+        return fail(c, LC_EINVAL, "lc_rescale: bad argument");
+    if (count == 0) return LC_OK;
+    u64* t = lc_scratch(c, rescale_words(c, (int)count, (int)deg, (int)level) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    do_rescale(c, ct, (int)count, (int)deg, (int)level, out, t);
+    return check_launch(c, "lc_rescale");
+}
+
+int lc_rotate(lc_ctx* c, const lc_evk* evk, const uint64_t* ct, uint32_t level, uint32_t n_rot, const int32_t* rots,
+              uint64_t* out) {
+    if (!c || !evk || !ct || !out || (n_rot && !rots) || (int)level >= c->nq)
+        return fail(c, LC_EINVAL, "lc_rotate: bad argument");
+    if (n_rot == 0) return LC_OK;
+    const size_t P = (size_t)(level + 1) * c->N;
+    std::vector<const SwKey*> keys(n_rot);
+    for (uint32_t r = 0; r < n_rot; r++) {
+        keys[r] = rots[r] > 0 ? find_key(evk, rots[r]) : nullptr;
+        if (!keys[r]) return fail(c, LC_EKEY, "rotation key missing");
+    }
+    const size_t kw = ks_words(c, 1, (int)level);
+    u64* t = lc_scratch(c, (kw + 2 * P) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    KsBufs kb = ks_layout(c, t, 1, (int)level);
+    u64* w = t + kw;
+    ks_modup(c, ct + P, 2 * P, 1, (int)level, kb);
+    for (uint32_t r = 0; r < n_rot; r++) {
+        ks_apply(c, ct + P, 2 * P, 1, (int)level, keys[r]->data, kb, ct, nullptr, 2 * P, w, 2 * P);
+        op_gather(c, w, out + (size_t)r * 2 * P, 2, (int)level + 1, keys[r]->galois, false);
+    }
+    return check_launch(c, "lc_rotate");
+}
+
+int lc_rotate_sum(lc_ctx* c, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
+                  const uint32_t* groups) {
+    if (!c || !evk || !cts || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_rotate_sum: bad argument");
+    if (count == 0 || n_groups == 0) return LC_OK;
+    int maxg = 1;
+    for (uint32_t i = 0; i < n_groups; i++) maxg = std::max(maxg, (int)(groups ? groups[i] : 1));
+    if (maxg > 8) return fail(c, LC_EINVAL, "group too large");
+    u64* t = lc_scratch(c, rotsum_words(c, (int)count, (int)level, maxg) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    int st = do_rotate_sum(c, evk, cts, (int)count, (int)level, (int)n_groups, groups, t);
+    if (st) return st;
+    return check_launch(c, "lc_rotate_sum");
+}
+
+int lc_memcpy_h2d(lc_ctx* c, uint64_t* dst, const void* src, size_t bytes) {
+    if (!c || (!dst && bytes) || (!src && bytes)) return fail(c, LC_EINVAL, "lc_memcpy_h2d: null argument");
+    LC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return LC_OK;
+}
+
+int lc_memcpy_d2h(lc_ctx* c, void* dst, const uint64_t* src, size_t bytes) {
+    if (!c || (!dst && bytes) || (!src && bytes)) return fail(c, LC_EINVAL, "lc_memcpy_d2h: null argument");
+    LC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return LC_OK;
+}
+
+int lc_launches(uint64_t* out) {
+    if (!out) return LC_EINVAL;
+    *out = g_lc_launches.load();
+    return LC_OK;
+}
+
+int lc_profile(lc_ctx* c, int start, double* ms, double* bytes, uint64_t* launches) {
+    if (!c) return LC_EINVAL;
+    if (start) {
+        c->prof.clear();
+        c->ev_used = 0;
+        c->prof_on = true;
+        return LC_OK;
+    }
+    c->prof_on = false;
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < PROF_N; k++) {
+        if (ms) ms[k] = 0;
+        if (bytes) bytes[k] = 0;
+        if (launches) launches[k] = 0;
+    }
+    for (const ProfRec& r : c->prof) {
+        float t = 0;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        if (ms) ms[r.cls] += t;
+        if (bytes) bytes[r.cls] += r.bytes;
+        if (launches) launches[r.cls] += 1;
+    }
+    c->prof.clear();
+    c->ev_used = 0;
+    return check_launch(c, "lc_profile");
+}
+
+// ------------------------------------------------------------------------------------ the method
+static int max_batch_for(lc_ctx* c, size_t words_per_item, size_t budget_words) {
+    size_t b = budget_words / std::max<size_t>(1, words_per_item);
+    return (int)std::max<size_t>(1, std::min<size_t>(b, 4096));
+}
+
+int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
+                 uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale) {
+    if (!c || !evk || !cts || !out || n < 2 || chunks == 0) return fail(c, LC_EINVAL, "lc_distances: bad argument");
+    const int L = c->nq - 1;
+    const size_t N = c->N;
+    const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    const int npairs = (int)(n * (n - 1) / 2);
+    std::vector<uint32_t> sched;
+    if (n_groups == 0) {
+        for (int i = 1; i < c->log_n; i++) sched.push_back(1);
+    } else {
+        uint32_t sum = 0;
+        for (uint32_t i = 0; i < n_groups; i++) {
+            sched.push_back(groups ? groups[i] : 1);
+            sum += sched.back();
+        }
+        if ((int)sum != c->log_n - 1) return fail(c, LC_EINVAL, "schedule must sum to log2(slots)");
+    }
+    int maxg = 1;
+    for (uint32_t g : sched) maxg = std::max(maxg, (int)g);
+    if (maxg > 8) return fail(c, LC_EINVAL, "group too large");
+    if (!find_key(evk, -1)) return fail(c, LC_EKEY, "relinearisation key missing");
+    // host buffers are staged through device memory
+    const bool in_host = is_host_ptr(cts), out_host = is_host_ptr(out);
+    const size_t in_words = (size_t)n * chunks * 2 * Pin, out_words = (size_t)npairs * 2 * Pout;
+    const u64* din = cts;
+    u64* dout = out;
+    if (in_host || out_host) {
+        u64* sb = stage_buf(c, ((in_host ? in_words : 0) + (out_host ? out_words : 0)) * 8);
+        if (!sb) return fail(c, LC_ENOMEM, "staging buffer");
+        if (in_host) {
+            LC_CUDA(c, cudaMemcpyAsync(sb, cts, in_words * 8, cudaMemcpyHostToDevice, c->stream));
+            din = sb;
+        }
+        if (out_host) dout = sb + (in_host ? in_words : 0);
+    }
+    // per-item scratch: acc3 + ct2 + key-switch buffers + rotation outputs
+    const size_t per_item = 3 * Pin + 2 * Pin + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
+                            std::max<size_t>(rotsum_words(c, 1, L - 1, maxg), 0);
+    const int B = mode == LC_MODE_PER_OP ? 1 : max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
+    const int Bw = std::min(B, npairs);
+    u64* t = lc_scratch(c, per_item * Bw * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* acc3 = t;
+    u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
+    u64* tmp = ct2 + (size_t)Bw * 2 * Pin;
+    for (int p0 = 0; p0 < npairs; p0 += Bw) {
+        const int b = std::min(Bw, npairs - p0);
+        {
+            // compulsory bytes: every client tile this launch touches, once, plus the outputs
+            const int touched = b == npairs ? (int)n : 2 * b;
+            PROF(c, PROF_TENSOR, ((double)touched * chunks * 2.0 + 3.0 * b) * Pin * 8.0, (uint64_t)b,
+                 op_sq_acc_pairs(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3));
+        }
+        int st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+        if (st) return st;
+        u64* y = dout + (size_t)p0 * 2 * Pout;
+        do_rescale(c, ct2, b, 2, L, y, tmp);
+        st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp);
+        if (st) return st;
+    }
+    if (out_host) LC_CUDA(c, cudaMemcpyAsync(out, dout, out_words * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (out_scale) *out_scale = scale * scale / (double)c->mod[L];
+    if (in_host || out_host) LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_distances");
+}
+
+int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
+                        const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out, double* out_scale) {
+    if (!c || !evk || !cts || !masks || !out || n == 0 || chunks == 0)
+        return fail(c, LC_EINVAL, "lc_masked_aggregate: bad argument");
+    const int L = c->nq - 1;
+    const size_t N = c->N;
+    const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    if (!find_key(evk, -1)) return fail(c, LC_EKEY, "relinearisation key missing");
+    const bool in_host = is_host_ptr(cts), m_host = is_host_ptr(masks), out_host = is_host_ptr(out);
+    const size_t in_words = (size_t)n * chunks * 2 * Pin, m_words = (size_t)n * 2 * Pin,
+                 out_words = (size_t)chunks * 2 * Pout;
+    const u64* din = cts;
+    const u64* dm = masks;
+    u64* dout = out;
+    if (in_host || m_host || out_host) {
+        u64* sb = stage_buf(c, ((in_host ? in_words : 0) + (m_host ? m_words : 0) + (out_host ? out_words : 0)) * 8);
+        if (!sb) return fail(c, LC_ENOMEM, "staging buffer");
+        u64* cur = sb;
+        if (in_host) {
+            LC_CUDA(c, cudaMemcpyAsync(cur, cts, in_words * 8, cudaMemcpyHostToDevice, c->stream));
+            din = cur;
+            cur += in_words;
+        }
+        if (m_host) {
+            LC_CUDA(c, cudaMemcpyAsync(cur, masks, m_words * 8, cudaMemcpyHostToDevice, c->stream));
+            dm = cur;
+            cur += m_words;
+        }
+        if (out_host) dout = cur;
+    }
+    const size_t per_item = 3 * Pin + 2 * Pin + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L));
+    const int B = mode == LC_MODE_PER_OP ? 1 : max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
+    const int Bw = std::min(B, (int)chunks);
+    u64* t = lc_scratch(c, per_item * Bw * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* acc3 = t;
+    u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
+    u64* tmp = ct2 + (size_t)Bw * 2 * Pin;
+    for (int k0 = 0; k0 < (int)chunks; k0 += Bw) {
+        const int b = std::min(Bw, (int)chunks - k0);
+        PROF(c, PROF_TENSOR, ((double)n * b * 2.0 + 2.0 * n + 3.0 * b) * Pin * 8.0, (uint64_t)b,
+             op_mask_acc(c, din, (int)n, (int)chunks, c->nq, dm, k0, b, acc3));
+        int st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+        if (st) return st;
+        do_rescale(c, ct2, b, 2, L, dout + (size_t)k0 * 2 * Pout, tmp);
+    }
+    if (out_host) LC_CUDA(c, cudaMemcpyAsync(out, dout, out_words * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (out_scale) *out_scale = scale * mask_scale / (double)c->mod[L];
+    if (in_host || m_host || out_host) LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_masked_aggregate");
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Device modular arithmetic for word-size RNS primes q < 2^62.
+//
+// Shoup multiplication (V. Shoup, NTL; D. Harvey, "Faster arithmetic for number-theoretic
+// transforms", 2014): with w' = floor(w 2^64 / q), for any a < 2^64
+//   a*w - floor(a w' / 2^64) * q  lies in [0, 2q).
+// 128-bit values are reduced as hi*(2^64 mod q) + lo, each term by a Shoup product.
+#pragma once
+#include <cstdint>
+
+typedef uint64_t u64;
+
+struct ModConst {
+    u64 q;        // the prime
+    u64 two_q;
+    u64 r64;      // 2^64 mod q
+    u64 r64_sh;   // floor(r64 * 2^64 / q)
+    u64 one_sh;   // floor(2^64 / q)
+    u64 n_inv;    // N^-1 mod q
+    u64 n_inv_sh;
+    u64 pad;
+};
+
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 w_sh, u64 q) {
+    u64 hi = __umul64hi(a, w_sh);
+    return a * w - hi * q;  // [0, 2q)
+}
+
+__device__ __forceinline__ u64 csub(u64 a, u64 m) { return a >= m ? a - m : a; }
+
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 w_sh, u64 q) {
+    return csub(mul_shoup_lazy(a, w, w_sh, q), q);
+}
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// 128-bit accumulator helpers
+struct u128v {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(u128v& acc, u64 a, u64 b) {
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+}
+// (hi * 2^64 + lo) mod q in [0, q) for any hi, lo
+__device__ __forceinline__ u64 reduce128(u128v x, const ModConst& m) {
+    u64 a = mul_shoup_lazy(x.hi, m.r64, m.r64_sh, m.q);  // [0, 2q)
+    u64 b = x.lo - __umul64hi(x.lo, m.one_sh) * m.q;     // [0, 2q)
+    u64 s = a + b;                                       // [0, 4q)
+    s = csub(s, m.two_q);
+    return csub(s, m.q);
+}
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const ModConst& m) {
+    u128v t{a * b, __umul64hi(a, b)};
+    return reduce128(t, m);
+}
+// centred lift of a residue of an odd modulus p into another modulus q (as a residue)
+__device__ __forceinline__ u64 lift_centred(u64 v, u64 p, u64 q) {
+    // v in [0, p): if v > (p-1)/2 the integer is v - p < 0
+    if (v > (p >> 1)) {
+        u64 neg = p - v;  // in [1, p/2]
+        neg = neg % q;    // p may exceed q
+        return neg ? q - neg : 0;
+    }
+    return v % q;
+}

@@ -1,0 +1,304 @@
+// Negacyclic NTT kernels; see ntt.cuh for the domain convention and pass structure.
+//
+// Column pass (index bits [8, log_n), C = log_n - 8 "row" bits of a 2^C x 256 view): a CTA of
+// 2^C threads owns 16 columns; every thread loads 16 words straight from global memory (a warp
+// reads two full 128-byte row segments per load), runs the top 4 row-bit stages in registers,
+// exchanges once through shared memory, runs the remaining C-4 stages, and stores straight to
+// global memory.  Row pass (bits [0, 8)): a CTA of 128 threads owns 8 blocks of 256 words; the
+// two radix-16 halves are separated by one swizzled shared-memory exchange, and a second
+// exchange restores a coalesced store (forward) or load (inverse).
+#include <cuda_runtime.h>
+#include "ntt.cuh"
+#include "context.cuh"
+
+namespace {
+
+constexpr int kRowThreads = 128;
+
+__device__ __forceinline__ u64* limb_ptr(u64* base, size_t batch_stride, const RowMap& map, int b, int log_n,
+                                         int& mod_idx) {
+    const int n = map.n;
+    const int bi = b / n, r = b - bi * n;
+    mod_idx = map.mod[r];
+    return base + (size_t)bi * batch_stride + ((size_t)map.row[r] << log_n);
+}
+
+// Cooley-Tukey butterfly, inputs/outputs in [0, 2q)
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
+    u64 t = mul_shoup_lazy(y, w.x, w.y, q);
+    u64 a = x + t;
+    u64 b = x + two_q - t;
+    x = csub(a, two_q);
+    y = csub(b, two_q);
+}
+// Gentleman-Sande butterfly, inputs/outputs in [0, 2q)
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
+    u64 a = x + y;
+    u64 b = x + two_q - y;
+    x = csub(a, two_q);
+    y = mul_shoup_lazy(b, w.x, w.y, q);
+}
+
+// swizzle for the row-pass tile: XOR word bits 0..3 with bits 4..7
+__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 4) & 15); }
+
+__device__ __forceinline__ ulonglong2 ldtw(const ulonglong2* t, int i) { return __ldg(t + i); }
+
+// ------------------------------------------------------------------------------ column pass
+// forward: row bits C-1 .. 0 (global bits log_n-1 .. 8)
+template <int C>
+__global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+    constexpr int LOGN = C + 8;
+    constexpr int T = 1 << C;
+    constexpr int RS = 1 << (C - 4);  // row stride of a thread's 16 words in phase 1
+    constexpr int R2 = C - 4;         // row bits left for phase 2
+    __shared__ u64 s[R2 > 0 ? (16 << C) : 1];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
+    const int col0 = blockIdx.x * 16;
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.fwd + ((size_t)mi << LOGN);
+    const int tid = threadIdx.x;
+    const int c = tid & 15, rg = tid >> 4;
+    u64 x[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = a[((size_t)(rg + RS * u) << 8) + col0 + c];
+#pragma unroll
+    for (int st = 3; st >= 0; st--) {
+        const int b = R2 + st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            const int row = rg + RS * u;
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q, mc.two_q);
+        }
+    }
+    if constexpr (R2 == 0) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) a[((size_t)(rg + RS * u) << 8) + col0 + c] = x[u];
+    } else {
+#pragma unroll
+        for (int u = 0; u < 16; u++) s[((rg + RS * u) << 4) + c] = x[u];
+        __syncthreads();
+        constexpr int V = 1 << R2;
+#pragma unroll
+        for (int k = 0; k < (256 >> C); k++) {
+            const int item = tid + T * k;
+            const int c2 = item & 15, grp = item >> 4;
+            u64 y[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) y[v] = s[(((grp << R2) + v) << 4) + c2];
+#pragma unroll
+            for (int st = R2 - 1; st >= 0; st--) {
+                const int b = st;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    if (v >> st & 1) continue;
+                    const int row = (grp << R2) + v;
+                    ct_bfly(y[v], y[v | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q,
+                            mc.two_q);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) a[((size_t)((grp << R2) + v) << 8) + col0 + c2] = y[v];
+        }
+    }
+}
+
+// inverse: row bits 0 .. C-1; the last stage (t = N/2) folds N^-1
+template <int C>
+__global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+    constexpr int LOGN = C + 8;
+    constexpr int T = 1 << C;
+    constexpr int RS = 1 << (C - 4);
+    constexpr int R2 = C - 4;
+    __shared__ u64 s[R2 > 0 ? (16 << C) : 1];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
+    const int col0 = blockIdx.x * 16;
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.inv + ((size_t)mi << LOGN);
+    const int tid = threadIdx.x;
+    const int c = tid & 15, rg = tid >> 4;
+    u64 x[16];
+    if constexpr (R2 == 0) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) x[u] = a[((size_t)(rg + RS * u) << 8) + col0 + c];
+    } else {
+        constexpr int V = 1 << R2;
+#pragma unroll
+        for (int k = 0; k < (256 >> C); k++) {
+            const int item = tid + T * k;
+            const int c2 = item & 15, grp = item >> 4;
+            u64 y[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) y[v] = a[((size_t)((grp << R2) + v) << 8) + col0 + c2];
+#pragma unroll
+            for (int st = 0; st < R2; st++) {
+                const int b = st;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    if (v >> st & 1) continue;
+                    const int row = (grp << R2) + v;
+                    gs_bfly(y[v], y[v | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q,
+                            mc.two_q);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) s[(((grp << R2) + v) << 4) + c2] = y[v];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 16; u++) x[u] = s[((rg + RS * u) << 4) + c];
+    }
+#pragma unroll
+    for (int st = 0; st < 4; st++) {
+        const int b = R2 + st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            if (st == 3) {
+                // final stage (t = N/2): (x + y) N^-1 and (x - y) psi^{-br(1)} N^-1, fully reduced
+                const u64 xa = x[u] + x[u | 8];
+                const u64 xb = x[u] + mc.two_q - x[u | 8];
+                const ulonglong2 wl = ldtw(tw, 0);
+                x[u] = mul_shoup(xa, mc.n_inv, mc.n_inv_sh, mc.q);
+                x[u | 8] = mul_shoup(xb, wl.x, wl.y, mc.q);
+            } else {
+                const int row = rg + RS * u;
+                gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q, mc.two_q);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) a[((size_t)(rg + RS * u) << 8) + col0 + c] = x[u];
+}
+
+// ------------------------------------------------------------------------------ row pass
+// forward: bits 7 .. 0 inside 256-word blocks; output fully reduced to [0, q)
+__global__ void __launch_bounds__(kRowThreads) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+                                                           NttTables tb) {
+    constexpr int E = 8 * 256;
+    __shared__ u64 s[E];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, log_n, mi) + (size_t)blockIdx.x * E;
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.fwd + ((size_t)mi << log_n);
+    const int tid = threadIdx.x;
+    const int lo = tid & 15, blk = tid >> 4;
+    const int g0 = blockIdx.x * E + (blk << 8);
+    u64 x[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = a[(blk << 8) + lo + 16 * u];
+#pragma unroll
+    for (int st = 3; st >= 0; st--) {
+        const int b = 4 + st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            const int j = g0 + lo + 16 * u;
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) s[swz((blk << 8) + lo + 16 * u)] = x[u];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = s[swz((blk << 8) + 16 * lo + u)];
+#pragma unroll
+    for (int st = 3; st >= 0; st--) {
+        const int b = st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            const int j = g0 + 16 * lo + u;
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) s[swz((blk << 8) + 16 * lo + u)] = csub(x[u], mc.q);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];
+}
+
+// inverse: bits 0 .. 7 inside 256-word blocks; output in [0, 2q) for the column pass
+__global__ void __launch_bounds__(kRowThreads) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+                                                           NttTables tb) {
+    constexpr int E = 8 * 256;
+    __shared__ u64 s[E];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, log_n, mi) + (size_t)blockIdx.x * E;
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.inv + ((size_t)mi << log_n);
+    const int tid = threadIdx.x;
+    const int lo = tid & 15, blk = tid >> 4;
+    const int g0 = blockIdx.x * E + (blk << 8);
+    u64 x[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) s[swz((blk << 8) + lo + 16 * u)] = a[(blk << 8) + lo + 16 * u];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = s[swz((blk << 8) + 16 * lo + u)];
+#pragma unroll
+    for (int st = 0; st < 4; st++) {
+        const int b = st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            const int j = g0 + 16 * lo + u;
+            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) s[swz((blk << 8) + 16 * lo + u)] = x[u];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = s[swz((blk << 8) + lo + 16 * u)];
+#pragma unroll
+    for (int st = 0; st < 4; st++) {
+        const int b = 4 + st;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            if (u >> st & 1) continue;
+            const int j = g0 + lo + 16 * u;
+            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = x[u];
+}
+
+}  // namespace
+
+#define LC_COL_DISPATCH(KERNEL, C_, GRID, S_)                                                       \
+    switch (C_) {                                                                                   \
+        case 4: KERNEL<4><<<GRID, 1 << 4, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        case 5: KERNEL<5><<<GRID, 1 << 5, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        case 6: KERNEL<6><<<GRID, 1 << 6, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        case 7: KERNEL<7><<<GRID, 1 << 7, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        case 8: KERNEL<8><<<GRID, 1 << 8, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        default: break;                                                                             \
+    }
+
+void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n, const NttTables& tb,
+                 cudaStream_t s) {
+    const int limbs = batch * map.n;
+    if (limbs == 0) return;
+    const int C = log_n - 8;
+    dim3 gc(16, limbs), gr((1 << log_n) / 2048, limbs);
+    LC_COL_DISPATCH(ntt_fwd_col, C, gc, s)
+    ntt_fwd_row<<<gr, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb);
+    g_lc_launches += 2;
+}
+
+void ntt_inverse(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n, const NttTables& tb,
+                 cudaStream_t s) {
+    const int limbs = batch * map.n;
+    if (limbs == 0) return;
+    const int C = log_n - 8;
+    dim3 gc(16, limbs), gr((1 << log_n) / 2048, limbs);
+    ntt_inv_row<<<gr, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb);
+    LC_COL_DISPATCH(ntt_inv_col, C, gc, s)
+    g_lc_launches += 2;
+}

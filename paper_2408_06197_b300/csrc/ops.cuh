@@ -1,0 +1,44 @@
+// Launchers of the evaluation kernels (ops.cu).  All pointers are device pointers; all
+// layouts are [count][poly][limb][N] words, evaluation domain unless stated.
+#pragma once
+#include "context.cuh"
+
+// out = a +/- b over n_polys polynomials of nl limbs (limb i mod q_i)
+void op_addsub(lc_ctx* c, const u64* a, const u64* b, u64* out, int n_polys, int nl, bool sub);
+// out[3] = tensor of one pair of degree-1 ciphertexts
+void op_tensor(lc_ctx* c, const u64* a, const u64* b, u64* out, int nl);
+// distances tensor phase: out[p] = sum_k (ct_i[k]-ct_j[k])^2 for pairs p in [p0, p0+np)
+void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p0, int np, u64* out);
+// aggregate tensor phase: out[k] = sum_i ct_i[k] (x) M_i for chunks k in [k0, k0+nk)
+void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64* masks, int k0, int nk, u64* out);
+
+// Hybrid key switching pieces (B polynomials at level `level`):
+//  d: [B] input polys (evaluation domain, nl rows), stride d_stride words
+//  scratch layout is owned by the caller (see capi.cu)
+void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext);
+void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* key, u64* v);
+void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv);
+// W[b][k] = (v_k - conv_k) P^-1 + add_k  (add pointers may be null; add0 stride add_stride)
+void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0,
+                        const u64* add1, size_t add_stride, u64* w, size_t w_stride);
+// rescale: lastc [B*deg][N] coefficient-domain copy of the last limb; r scratch [B*deg][level][N]
+void op_rescale_prep(lc_ctx* c, const u64* lastc, int Bdeg, int level, u64* r);
+void op_rescale_combine(lc_ctx* c, const u64* ct, const u64* r, int B, int deg, int level, u64* out);
+// y[p][i][idx] (+)= w[p][i][perm_g(idx)] over n_polys polys of nl limbs
+void op_gather(lc_ctx* c, const u64* w, u64* y, int n_polys, int nl, uint64_t g, bool accumulate);
+// per-row permutation (any rows, all of length N)
+void op_permute_rows(lc_ctx* c, const u64* in, u64* out, int rows, uint64_t g);
+// signed integers -> residues for rows with modulus indices mods[0..nrows)
+void op_to_rns_i64(lc_ctx* c, const int64_t* x, int B, const int* mods_host, int nrows, u64* out);
+void op_to_rns_i32(lc_ctx* c, const int32_t* x, int B, const int* mods_host, int nrows, u64* out);
+void op_to_rns_i8(lc_ctx* c, const int8_t* x, int B, const int* mods_host, int nrows, u64* out);
+// b = e - a s (+ addmul * st when addmul_host[row] != 0); rows with modulus index mods
+void op_key_combine(lc_ctx* c, const u64* a, const u64* s, const u64* e, const u64* st, const u64* addmul_host,
+                    const int* mods_host, int nrows, u64* b_out);
+// out0 = m + r u0 + e0, out1 = r u1 + e1 over nl limbs, B ciphertexts
+void op_enc_combine(lc_ctx* c, const u64* m, const u64* r, const u64* e0, const u64* e1, const u64* pk, int B,
+                    int nl, u64* out);
+// acc = sum_p ct[p] s^p over nl limbs
+void op_dec_combine(lc_ctx* c, const u64* ct, const u64* s, int deg, int nl, u64* out);
+// elementwise square (evaluation domain), nl rows of modulus index = row
+void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods_host, int nrows);

@@ -1,0 +1,445 @@
+"""Thin Python binding of liblancelot.so (include/lancelot.h).
+
+Argument marshalling only: every step of the evaluation runs in the library's CUDA kernels.
+PyTorch provides device memory (its caching allocator is handed to the library) and the CUDA
+stream.  Ciphertext arrays are torch.int64 tensors on the GPU holding the library's uint64
+words ([count][poly][limb][N], evaluation domain).  The library is loaded on first use; if it
+is missing or cannot be loaded the call raises -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblancelot.so")
+
+LC_OK = 0
+LC_MODE_PER_OP = 0
+LC_MODE_BATCHED = 1
+_ERRS = {-1: "LC_EINVAL", -2: "LC_ELEVEL", -3: "LC_ESCALE", -4: "LC_ENOMEM", -5: "LC_ECUDA",
+         -6: "LC_ETIMEOUT", -7: "LC_EBUSY", -8: "LC_EKEY"}
+
+_lib = None
+vp = ctypes.c_void_p
+u32 = ctypes.c_uint32
+
+
+class LancelotError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("log_n", u32), ("n_q", u32), ("n_p", u32), ("dnum", u32), ("q", vp), ("p", vp)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(vp, ctypes.c_size_t, vp)
+_FREE_FN = ctypes.CFUNCTYPE(None, vp, vp)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", vp)]
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LancelotError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "lc_gen_primes": [u32, u32, u32, u32, vp],
+            "lc_ctx_create": [vp, ctypes.c_int, vp, vp, vp],
+            "lc_ctx_destroy": [vp],
+            "lc_set_stream": [vp, vp],
+            "lc_sync": [vp],
+            "lc_counters": [vp, vp, ctypes.c_int],
+            "lc_pk_gen": [vp, vp, vp, vp, vp],
+            "lc_evk_create": [vp, vp],
+            "lc_evk_free": [vp],
+            "lc_evk_add": [vp, vp, vp, ctypes.c_int32, vp, vp],
+            "lc_evk_export": [vp, vp, ctypes.c_int32, vp],
+            "lc_encode": [vp, vp, ctypes.c_size_t, ctypes.c_double, vp],
+            "lc_decode": [vp, vp, ctypes.c_double, vp],
+            "lc_encrypt": [vp, vp, vp, vp, vp, vp, u32, vp],
+            "lc_decrypt": [vp, vp, vp, u32, u32, vp],
+            "lc_crt_to_double": [vp, vp, u32, vp],
+            "lc_to_coeff": [vp, vp, u32, u32],
+            "lc_to_eval": [vp, vp, u32, u32],
+            "lc_add": [vp, vp, vp, u32, u32, vp],
+            "lc_sub": [vp, vp, vp, u32, u32, vp],
+            "lc_tensor": [vp, vp, vp, u32, vp],
+            "lc_relin": [vp, vp, vp, u32, u32, vp],
+            "lc_rescale": [vp, vp, u32, u32, u32, vp],
+            "lc_rotate": [vp, vp, vp, u32, u32, vp, vp],
+            "lc_rotate_sum": [vp, vp, vp, u32, u32, u32, vp],
+            "lc_distances": [vp, vp, vp, u32, u32, ctypes.c_double, u32, u32, vp, vp, vp],
+            "lc_masked_aggregate": [vp, vp, vp, u32, u32, ctypes.c_double, vp, ctypes.c_double, u32, vp, vp],
+            "lc_memcpy_h2d": [vp, vp, vp, ctypes.c_size_t],
+            "lc_memcpy_d2h": [vp, vp, vp, ctypes.c_size_t],
+            "lc_launches": [vp],
+            "lc_profile": [vp, ctypes.c_int, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name in ("lc_ctx_destroy", "lc_evk_free") else ctypes.c_int
+        L.lc_last_error.argtypes = [vp]
+        L.lc_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _t_ptr(t: torch.Tensor):
+    assert t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def launches() -> int:
+    out = np.zeros(1, dtype=np.uint64)
+    lib().lc_launches(_np_ptr(out))
+    return int(out[0])
+
+
+class PinnedArray(np.ndarray):
+    """numpy view of page-locked torch storage (keeps the storage alive)."""
+    _owner = None
+
+
+def pinned_empty(shape, dtype=np.uint64) -> np.ndarray:
+    """Page-locked host array (torch pinned memory viewed as numpy)."""
+    n = int(np.prod(shape)) * np.dtype(dtype).itemsize
+    t = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    a = t.numpy().view(dtype).reshape(shape).view(PinnedArray)
+    a._owner = t
+    return a
+
+
+def gen_primes(log_n: int, bits: int, skip: int, count: int) -> List[int]:
+    out = np.zeros(max(1, count), dtype=np.uint64)
+    st = lib().lc_gen_primes(log_n, bits, skip, count, _np_ptr(out))
+    if st != LC_OK:
+        raise LancelotError(f"lc_gen_primes: {_ERRS.get(st, st)}")
+    return [int(x) for x in out[:count]]
+
+
+def production_primes():
+    """N = 2^15: q0 = largest 60-bit, p = next four 60-bit, q1..q14 = largest 40-bit (descending)."""
+    q0 = gen_primes(15, 60, 0, 1)
+    p = gen_primes(15, 60, 1, 4)
+    return 15, q0 + gen_primes(15, 40, 0, 14), p, 4, float(2 ** 40)
+
+
+def toy_primes():
+    """N = 2^12: q0 50-bit, q1..q2 30-bit, one 50-bit special prime; dnum = 3 (alpha = 1)."""
+    q0 = gen_primes(12, 50, 0, 1)
+    p = gen_primes(12, 50, 1, 1)
+    return 12, q0 + gen_primes(12, 30, 0, 2), p, 3, float(2 ** 30)
+
+
+def u64_to_torch(a: np.ndarray, device="cuda") -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def torch_to_u64(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+class Context:
+    """One GPU context: parameters, device tables, the torch stream, scratch."""
+
+    def __init__(self, log_n: int, q: Sequence[int], p: Sequence[int], dnum: int, scale: float,
+                 device: int = 0, stream: Optional[torch.cuda.Stream] = None, use_torch_allocator: bool = True):
+        L = lib()
+        self.log_n, self.N = log_n, 1 << log_n
+        self.q, self.p, self.dnum, self.scale = list(q), list(p), dnum, scale
+        self.nq, self.np_ = len(q), len(p)
+        self.alpha = -(-self.nq // dnum)
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        self._qa = np.array(q, dtype=np.uint64)
+        self._pa = np.array(p, dtype=np.uint64)
+        prm = _Params(log_n, len(q), len(p), dnum, self._qa.ctypes.data, self._pa.ctypes.data)
+        self._alloc = None
+        if use_torch_allocator:
+            dev, st = device, self.stream
+
+            def _a(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except RuntimeError:
+                    return None
+
+            def _f(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._afn, self._ffn = _ALLOC_FN(_a), _FREE_FN(_f)
+            self._alloc = _Allocator(self._afn, self._ffn, None)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            st = L.lc_ctx_create(ctypes.byref(prm), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(self._alloc) if self._alloc else None, ctypes.byref(h))
+        if st != LC_OK:
+            raise LancelotError(f"lc_ctx_create: {_ERRS.get(st, st)}")
+        self.h = h
+
+    @classmethod
+    def production(cls, **kw):
+        log_n, q, p, dnum, scale = production_primes()
+        return cls(log_n, q, p, dnum, scale, **kw)
+
+    @classmethod
+    def toy(cls, **kw):
+        log_n, q, p, dnum, scale = toy_primes()
+        return cls(log_n, q, p, dnum, scale, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def L(self) -> int:
+        return self.nq - 1
+
+    @property
+    def slots(self) -> int:
+        return self.N // 2
+
+    def _check(self, st: int, what: str):
+        if st != LC_OK:
+            msg = lib().lc_last_error(self.h)
+            raise LancelotError(f"{what}: {_ERRS.get(st, st)} {msg.decode() if msg else ''}")
+
+    def sync(self):
+        self._check(lib().lc_sync(self.h), "lc_sync")
+
+    def counters(self, reset: bool = False):
+        out = np.zeros(2, dtype=np.uint64)
+        self._check(lib().lc_counters(self.h, _np_ptr(out), int(reset)), "lc_counters")
+        return int(out[0]), int(out[1])
+
+    PROF_CLASSES = ("ntt", "modup", "inner", "moddown", "tensor", "rescale", "automorphism", "other")
+
+    def profile_start(self):
+        self._check(lib().lc_profile(self.h, 1, None, None, None), "lc_profile")
+
+    def profile_stop(self) -> Dict[str, dict]:
+        ms = np.zeros(8)
+        by = np.zeros(8)
+        ln = np.zeros(8, dtype=np.uint64)
+        self._check(lib().lc_profile(self.h, 0, _np_ptr(ms), _np_ptr(by), _np_ptr(ln)), "lc_profile")
+        return {k: {"ms": float(ms[i]), "bytes": float(by[i]), "launches": int(ln[i])}
+                for i, k in enumerate(self.PROF_CLASSES)}
+
+    def h2d(self, dst: torch.Tensor, src: np.ndarray):
+        """Stream-ordered host->device copy through the C ABI (src pinned or pageable)."""
+        self._check(lib().lc_memcpy_h2d(self.h, _t_ptr(dst), ctypes.c_void_p(src.ctypes.data), src.nbytes),
+                    "lc_memcpy_h2d")
+
+    def d2h(self, dst: np.ndarray, src: torch.Tensor):
+        self._check(lib().lc_memcpy_d2h(self.h, ctypes.c_void_p(dst.ctypes.data), _t_ptr(src), dst.nbytes),
+                    "lc_memcpy_d2h")
+
+    def empty(self, *shape) -> torch.Tensor:
+        return torch.empty(shape, dtype=torch.int64, device=f"cuda:{self.device}")
+
+    def ct_shape(self, count: int, deg: int, level: int):
+        return (count, deg, level + 1, self.N)
+
+    # ------------------------------------------------------------------ keys
+    def pk_gen(self, s: np.ndarray, a: np.ndarray, e: np.ndarray) -> torch.Tensor:
+        pk = self.empty(2, self.nq, self.N)
+        self._check(lib().lc_pk_gen(self.h, _np_ptr(np.ascontiguousarray(s, np.int8)),
+                                    _np_ptr(np.ascontiguousarray(a, np.uint64)),
+                                    _np_ptr(np.ascontiguousarray(e, np.int32)), _t_ptr(pk)), "lc_pk_gen")
+        return pk
+
+    def evk(self) -> "EvalKeys":
+        return EvalKeys(self)
+
+    # ------------------------------------------------------------------ encode / encrypt / decrypt
+    def encode(self, z: np.ndarray, scale: float) -> np.ndarray:
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        m = np.zeros(self.N, dtype=np.int64)
+        self._check(lib().lc_encode(self.h, _np_ptr(z), z.shape[0], scale, _np_ptr(m)), "lc_encode")
+        return m
+
+    def decode(self, m: np.ndarray, scale: float) -> np.ndarray:
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        z = np.zeros(self.N // 2, dtype=np.float64)
+        self._check(lib().lc_decode(self.h, _np_ptr(m), scale, _np_ptr(z)), "lc_decode")
+        return z
+
+    def encrypt(self, pk: torch.Tensor, m: np.ndarray, r: np.ndarray, e0: np.ndarray, e1: np.ndarray,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        m = np.ascontiguousarray(m, np.int64).reshape(-1, self.N)
+        count = m.shape[0]
+        if out is None:
+            out = self.empty(count, 2, self.nq, self.N)
+        self._check(lib().lc_encrypt(self.h, _t_ptr(pk), _np_ptr(m), _np_ptr(np.ascontiguousarray(r, np.int8)),
+                                     _np_ptr(np.ascontiguousarray(e0, np.int32)),
+                                     _np_ptr(np.ascontiguousarray(e1, np.int32)), count, _t_ptr(out)), "lc_encrypt")
+        return out
+
+    def decrypt_residues(self, s: np.ndarray, ct: torch.Tensor, level: int) -> np.ndarray:
+        ct = ct.contiguous()
+        deg = ct.shape[-3] if ct.dim() >= 3 else 2
+        res = np.zeros((level + 1, self.N), dtype=np.uint64)
+        self._check(lib().lc_decrypt(self.h, _np_ptr(np.ascontiguousarray(s, np.int8)), _t_ptr(ct), deg, level,
+                                     _np_ptr(res)), "lc_decrypt")
+        return res
+
+    def decrypt(self, s: np.ndarray, ct: torch.Tensor, level: int, scale: float) -> np.ndarray:
+        res = self.decrypt_residues(s, ct, level)
+        m = np.zeros(self.N, dtype=np.float64)
+        self._check(lib().lc_crt_to_double(self.h, _np_ptr(res), level, _np_ptr(m)), "lc_crt_to_double")
+        return self.decode(m, scale)
+
+    # ------------------------------------------------------------------ interchange
+    def to_coeff(self, data: torch.Tensor, level: int) -> torch.Tensor:
+        x = data.clone().contiguous()
+        n_polys = x.numel() // ((level + 1) * self.N)
+        self._check(lib().lc_to_coeff(self.h, _t_ptr(x), n_polys, level), "lc_to_coeff")
+        return x
+
+    def to_eval(self, data: torch.Tensor, level: int) -> torch.Tensor:
+        x = data.clone().contiguous()
+        n_polys = x.numel() // ((level + 1) * self.N)
+        self._check(lib().lc_to_eval(self.h, _t_ptr(x), n_polys, level), "lc_to_eval")
+        return x
+
+    # ------------------------------------------------------------------ primitives
+    def add(self, a, b, level):
+        out = torch.empty_like(a)
+        self._check(lib().lc_add(self.h, _t_ptr(a), _t_ptr(b), a.numel() // ((level + 1) * self.N), level,
+                                 _t_ptr(out)), "lc_add")
+        return out
+
+    def sub(self, a, b, level):
+        out = torch.empty_like(a)
+        self._check(lib().lc_sub(self.h, _t_ptr(a), _t_ptr(b), a.numel() // ((level + 1) * self.N), level,
+                                 _t_ptr(out)), "lc_sub")
+        return out
+
+    def tensor(self, a, b, level):
+        out = self.empty(3, level + 1, self.N)
+        self._check(lib().lc_tensor(self.h, _t_ptr(a), _t_ptr(b), level, _t_ptr(out)), "lc_tensor")
+        return out
+
+    def relin(self, evk: "EvalKeys", ct3: torch.Tensor, level: int) -> torch.Tensor:
+        count = ct3.numel() // (3 * (level + 1) * self.N)
+        out = self.empty(count, 2, level + 1, self.N)
+        self._check(lib().lc_relin(self.h, evk.h, _t_ptr(ct3), count, level, _t_ptr(out)), "lc_relin")
+        return out
+
+    def rescale(self, ct: torch.Tensor, level: int, deg: int = 2) -> torch.Tensor:
+        count = ct.numel() // (deg * (level + 1) * self.N)
+        out = self.empty(count, deg, level, self.N)
+        self._check(lib().lc_rescale(self.h, _t_ptr(ct), count, deg, level, _t_ptr(out)), "lc_rescale")
+        return out
+
+    def rotate(self, evk: "EvalKeys", ct: torch.Tensor, level: int, rots: Sequence[int]) -> torch.Tensor:
+        r = np.array(list(rots), dtype=np.int32)
+        out = self.empty(len(r), 2, level + 1, self.N)
+        self._check(lib().lc_rotate(self.h, evk.h, _t_ptr(ct), level, len(r), _np_ptr(r), _t_ptr(out)), "lc_rotate")
+        return out
+
+    def rotate_sum(self, evk: "EvalKeys", ct: torch.Tensor, level: int, groups: Sequence[int]) -> torch.Tensor:
+        y = ct.clone().contiguous()
+        g = np.array(list(groups), dtype=np.uint32)
+        count = y.numel() // (2 * (level + 1) * self.N)
+        self._check(lib().lc_rotate_sum(self.h, evk.h, _t_ptr(y), count, level, len(g), _np_ptr(g)), "lc_rotate_sum")
+        return y
+
+    # ------------------------------------------------------------------ the method
+    def distances(self, evk: "EvalKeys", cts, n: int, chunks: int, scale: float, mode: int = LC_MODE_BATCHED,
+                  groups: Optional[Sequence[int]] = None, out=None):
+        """cts: [n][chunks][2][nq][N] (torch GPU tensor, or numpy uint64 in host memory)."""
+        npairs = n * (n - 1) // 2
+        host = isinstance(cts, np.ndarray)
+        if out is None:
+            out = (np.empty((npairs, 2, self.L, self.N), dtype=np.uint64) if host
+                   else self.empty(npairs, 2, self.L, self.N))
+        g = np.array(list(groups) if groups else [], dtype=np.uint32)
+        sc = ctypes.c_double()
+        pin = _np_ptr(cts) if host else _t_ptr(cts)
+        pout = _np_ptr(out) if isinstance(out, np.ndarray) else _t_ptr(out)
+        self._check(lib().lc_distances(self.h, evk.h, pin, n, chunks, scale, mode, len(g),
+                                       _np_ptr(g) if len(g) else None, pout, ctypes.byref(sc)), "lc_distances")
+        return out, sc.value
+
+    def masked_aggregate(self, evk: "EvalKeys", cts, n: int, chunks: int, scale: float, masks, mask_scale: float,
+                         mode: int = LC_MODE_BATCHED, out=None):
+        host = isinstance(cts, np.ndarray)
+        if out is None:
+            out = (np.empty((chunks, 2, self.L, self.N), dtype=np.uint64) if host
+                   else self.empty(chunks, 2, self.L, self.N))
+        sc = ctypes.c_double()
+        pin = _np_ptr(cts) if host else _t_ptr(cts)
+        pm = _np_ptr(masks) if isinstance(masks, np.ndarray) else _t_ptr(masks)
+        pout = _np_ptr(out) if isinstance(out, np.ndarray) else _t_ptr(out)
+        self._check(lib().lc_masked_aggregate(self.h, evk.h, pin, n, chunks, scale, pm, mask_scale, mode, pout,
+                                              ctypes.byref(sc)), "lc_masked_aggregate")
+        return out, sc.value
+
+
+class EvalKeys:
+    """Device-resident switching keys (relinearisation + rotations): the server's evk."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(lib().lc_evk_create(ctx.h, ctypes.byref(h)), "lc_evk_create")
+        self.h = h
+        self.rotations: List[int] = []
+
+    def add(self, s: np.ndarray, rotation: Optional[int], a: np.ndarray, e: np.ndarray):
+        rot = -1 if rotation is None else int(rotation)
+        self.ctx._check(lib().lc_evk_add(self.ctx.h, self.h, _np_ptr(np.ascontiguousarray(s, np.int8)), rot,
+                                         _np_ptr(np.ascontiguousarray(a, np.uint64)),
+                                         _np_ptr(np.ascontiguousarray(e, np.int32))), "lc_evk_add")
+        if rotation is not None:
+            self.rotations.append(int(rotation))
+
+    def export(self, rotation: Optional[int]) -> np.ndarray:
+        c = self.ctx
+        out = np.zeros((c.dnum, 2, c.nq + c.np_, c.N), dtype=np.uint64)
+        rot = -1 if rotation is None else int(rotation)
+        c._check(lib().lc_evk_export(c.h, self.h, rot, _np_ptr(out)), "lc_evk_export")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lc_evk_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rotations_of_schedule(groups: Sequence[int]) -> List[int]:
+    out, stride = [], 1
+    for g in groups:
+        for t in range(1, 1 << g):
+            out.append(t * stride)
+        stride <<= g
+    return out

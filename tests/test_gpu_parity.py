@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle, bit for bit in the
+coefficient domain, plus decrypted accuracy against FP64.  Every oracle input is built from
+the shared seeded generators and the oracle's own encoder/encryptor."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from common import KeySet, plaintexts
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(kind):
+    from paper_2408_06197_b300 import lancelot as LC
+    return LC.Context.toy() if kind == "toy" else LC.Context.production()
+
+
+class Env:
+    def __init__(self, kind, seed, config, extra_rot=()):
+        from paper_2408_06197_b300 import lancelot as LC
+        self.LC = LC
+        self.kind = kind
+        self.prm = O.params_toy() if kind == "toy" else O.params_production()
+        self.o = O.Context(self.prm)
+        self.g = _ctx(kind)
+        self.sched = O.default_schedule(self.prm.slots)
+        rots = sorted(set(O.rotations_of_schedule(self.sched)) | set(extra_rot))
+        self.keys = KeySet(self.prm, seed, config, rots)
+        self.opk, self.orlk, self.ork = self.keys.oracle_keys(self.o)
+        self.gpk, self.gevk = self.keys.gpu_keys(self.g)
+        self.seed, self.config = seed, config
+        self.N, self.L = self.prm.N, self.prm.L
+
+    def g_coeff(self, t, level):
+        return self.LC.torch_to_u64(self.g.to_coeff(t, level))
+
+    def o_coeff(self, a):
+        return self.o.to_coeff(a)
+
+    def encrypt_both(self, X, clients, chunks):
+        """X [n][chunks][slots] -> (oracle cts, gpu cts) of the same integer plaintexts."""
+        m = plaintexts(self.o, self.prm, X)
+        r, e0, e1 = S.enc_rand_batch(self.seed, self.config, clients, chunks, self.N)
+        flat_m = m.reshape(-1, self.N)
+        ocs = np.stack([self.o.encrypt(self.opk, flat_m[k], r[k], e0[k], e1[k]) for k in range(flat_m.shape[0])])
+        gcs = self.g.encrypt(self.gpk, flat_m, r, e0, e1)
+        shape = X.shape[:-1] + (2, self.prm.L + 1, self.N)
+        return ocs.reshape(shape), gcs.reshape(shape)
+
+
+@pytest.fixture(scope="module")
+def toy():
+    return Env("toy", S.TOY.seed, S.TOY.config, extra_rot=(3, 6, 12))
+
+
+@pytest.fixture(scope="module")
+def prod():
+    return Env("prod", 0, S.CFG_PLAIN)
+
+
+@pytest.fixture(params=["toy", "prod"])
+def env(request, toy, prod):
+    return toy if request.param == "toy" else prod
+
+
+# ------------------------------------------------------------------------------- transforms
+
+def test_ntt_roundtrip_and_negacyclic_product(env):
+    rng = np.random.default_rng(1)
+    nl = env.L + 1
+    a = np.stack([rng.integers(0, q, size=env.N, dtype=np.uint64) for q in env.prm.q])
+    b = np.stack([rng.integers(0, q, size=env.N, dtype=np.uint64) for q in env.prm.q])
+    ga, gb = env.LC.u64_to_torch(a), env.LC.u64_to_torch(b)
+    ea, eb = env.g.to_eval(ga, env.L), env.g.to_eval(gb, env.L)
+    assert np.array_equal(env.g_coeff(ea, env.L), a)
+    # tensor of (a, 0) and (b, 0): first output is a*b in Z_q[X]/(X^N+1)
+    z = torch.zeros_like(ea)
+    t = env.g.tensor(torch.stack([ea, z]).contiguous(), torch.stack([eb, z]).contiguous(), env.L)
+    prod_coef = env.g_coeff(t[0].contiguous(), env.L)
+    for i in (0, nl - 1):
+        assert np.array_equal(prod_coef[i], env.o.poly_mul(i, a[i], b[i]))
+
+
+def test_encoder_matches_oracle(env):
+    z = np.random.default_rng(2).normal(0, 0.01, env.prm.slots)
+    mg = env.g.encode(z, env.prm.scale)
+    mo = env.o.encode(z, env.prm.scale)
+    diff = np.abs(mg - mo)
+    assert diff.max() <= 1 and np.count_nonzero(diff) <= 2
+    back = env.g.decode(mo.astype(np.float64), env.prm.scale)
+    assert np.abs(back - z).max() <= 0.5 * env.N / env.prm.scale
+
+
+# ------------------------------------------------------------------------------- keys, enc, dec
+
+def test_keys_bit_exact(env):
+    assert np.array_equal(env.g_coeff(env.gpk, env.L), env.o_coeff(env.opk))
+    assert np.array_equal(env.gevk.export(None), env.o.key_to_coeff(env.orlk))
+    r = env.sched and O.rotations_of_schedule(env.sched)[3]
+    assert np.array_equal(env.gevk.export(r), env.o.key_to_coeff(env.ork[r]))
+
+
+def test_encrypt_decrypt_bit_exact(env):
+    X = np.random.default_rng(3).normal(0, 0.01, (2, 1, env.prm.slots))
+    ocs, gcs = env.encrypt_both(X, [0, 1], [0])
+    for i in range(2):
+        assert np.array_equal(env.g_coeff(gcs[i, 0].contiguous(), env.L), env.o_coeff(ocs[i, 0]))
+    res_g = env.g.decrypt_residues(env.keys.s, gcs[0, 0].contiguous(), env.L)
+    res_o = env.o.decrypt_residues(env.keys.s, ocs[0, 0], env.L)
+    assert np.array_equal(res_g, res_o)
+    zg = env.g.decrypt(env.keys.s, gcs[0, 0].contiguous(), env.L, env.prm.scale)
+    # fresh noise: about 1e-7 per slot (production), 1e-5 (toy); max over all slots ~5 sigma
+    assert np.abs(zg - X[0, 0]).max() < (1e-4 if env.kind == "toy" else 1e-6)
+
+
+# ------------------------------------------------------------------------------- primitives
+
+def test_sub_tensor_relin_rescale_bit_exact(env):
+    X = np.random.default_rng(4).normal(0, 0.01, (2, 1, env.prm.slots))
+    ocs, gcs = env.encrypt_both(X, [0, 1], [0])
+    L = env.L
+    od = env.o.sub(ocs[0, 0], ocs[1, 0], L)
+    gd = env.g.sub(gcs[0, 0].contiguous(), gcs[1, 0].contiguous(), L)
+    assert np.array_equal(env.g_coeff(gd, L), env.o_coeff(od))
+    o3 = env.o.tensor(od, od, L)
+    g3 = env.g.tensor(gd, gd, L)
+    assert np.array_equal(env.g_coeff(g3, L), env.o_coeff(o3))
+    o2 = env.o.relin(o3, L, env.orlk)
+    g2 = env.g.relin(env.gevk, g3, L)[0]
+    assert np.array_equal(env.g_coeff(g2, L), env.o_coeff(o2))
+    orr = env.o.rescale(o2, L)
+    grr = env.g.rescale(g2.contiguous(), L)[0]
+    assert np.array_equal(env.g_coeff(grr, L - 1), env.o_coeff(orr))
+    sc = env.prm.scale ** 2 / env.prm.q[L]
+    dz = X[0, 0] - X[1, 0]
+    assert np.abs(env.g.decrypt(env.keys.s, grr, L - 1, sc) - dz * dz).max() < (1e-4 if env.kind == "toy" else 5e-7)
+
+
+def test_hoisted_rotations_and_rotate_sum_bit_exact(env):
+    X = np.random.default_rng(5).normal(0, 0.01, (1, 1, env.prm.slots))
+    ocs, gcs = env.encrypt_both(X, [0], [0])
+    L = env.L
+    rots = [1, 2, 4] if env.kind == "prod" else [1, 3, 6, 12]
+    outs_o = env.o.rotate_hoisted(ocs[0, 0], L, rots, [env.ork[r] for r in rots])
+    outs_g = env.g.rotate(env.gevk, gcs[0, 0].contiguous(), L, rots)
+    for k, r in enumerate(rots):
+        assert np.array_equal(env.g_coeff(outs_g[k].contiguous(), L), env.o_coeff(outs_o[k]))
+    z = env.g.decrypt(env.keys.s, outs_g[0].contiguous(), L, env.prm.scale)
+    assert np.abs(z - np.roll(X[0, 0], -rots[0])).max() < (2e-4 if env.kind == "toy" else 2e-6)
+    # rotate-and-sum: log-step, and (toy) a hoisted group of size 2
+    scheds = [env.sched] + ([[2] + [1] * (len(env.sched) - 2)] if env.kind == "toy" else [])
+    for sched in scheds:
+        need = O.rotations_of_schedule(sched)
+        yo = env.o.rotate_sum(ocs[0, 0], L, sched, {r: env.ork[r] for r in need})
+        yg = env.g.rotate_sum(env.gevk, gcs[0, 0].contiguous(), L, sched)
+        assert np.array_equal(env.g_coeff(yg, L), env.o_coeff(yo))
+
+
+# ------------------------------------------------------------------------------- the method (toy)
+
+def _toy_inputs(toy):
+    w = S.TOY
+    W = S.client_updates(w)
+    X = S.split_chunks(W, toy.prm.slots)
+    ocs, gcs = toy.encrypt_both(X, range(w.n_clients), range(w.chunks))
+    return w, W, X, ocs, gcs
+
+
+def test_toy_distances_bit_exact_both_modes_and_fp64(toy):
+    from paper_2408_06197_b300 import kgc
+    from test_oracle_pins import toy_distance_tolerance
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    toy.g.counters(reset=True)
+    Dg, sc = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale, mode=toy.LC.LC_MODE_BATCHED)
+    ks, mu = toy.g.counters(reset=True)
+    assert ks == w.n_pairs * (1 + len(toy.sched)) and mu == ks
+    Dp, _ = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale, mode=toy.LC.LC_MODE_PER_OP)
+    assert torch.equal(Dg, Dp)
+    Do = toy.o.distances(ocs, toy.orlk, toy.sched, toy.ork)
+    assert np.array_equal(toy.g_coeff(Dg, toy.L - 1), toy.o_coeff(Do))
+    tol = toy_distance_tolerance(toy.prm)
+    dist = np.zeros((w.n_clients, w.n_clients))
+    k = 0
+    for i in range(w.n_clients):
+        for j in range(i + 1, w.n_clients):
+            v = toy.g.decrypt(toy.keys.s, Dg[k].contiguous(), toy.L - 1, sc)
+            assert np.abs(v - np.sum((W[i] - W[j]) ** 2)).max() <= tol
+            dist[i, j] = dist[j, i] = v[0]
+            k += 1
+    ref = np.array([[np.sum((W[i] - W[j]) ** 2) for j in range(w.n_clients)] for i in range(w.n_clients)])
+    assert kgc.krum_select(dist, w.f, w.n_select) == kgc.krum_select(ref, w.f, w.n_select)
+
+
+def test_toy_masked_aggregate_bit_exact(toy):
+    from paper_2408_06197_b300 import kgc
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    sel = [0]
+    wts = kgc.mask_weights(w.n_clients, sel, average=False)
+    MX = np.stack([np.full((1, toy.prm.slots), wts[i]) for i in range(w.n_clients)])
+    m = plaintexts(toy.o, toy.prm, MX)[:, 0]
+    r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), [S.MASK_CHUNK], toy.N)
+    om = np.stack([toy.o.encrypt(toy.opk, m[i], r[i], e0[i], e1[i]) for i in range(w.n_clients)])
+    gm = toy.g.encrypt(toy.gpk, m, r, e0, e1)
+    for mode in (toy.LC.LC_MODE_BATCHED, toy.LC.LC_MODE_PER_OP):
+        ag, sc = toy.g.masked_aggregate(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale, gm, toy.prm.scale,
+                                        mode=mode)
+        ao = toy.o.masked_aggregate(ocs, om, toy.orlk)
+        assert np.array_equal(toy.g_coeff(ag, toy.L - 1), toy.o_coeff(ao))
+    got = toy.g.decrypt(toy.keys.s, ag[0].contiguous(), toy.L - 1, sc)
+    assert np.linalg.norm(got - X[0, 0]) / np.linalg.norm(X[0, 0]) < 1e-3
+
+
+def test_host_buffers_match_device_buffers(toy):
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    host = toy.LC.torch_to_u64(gcs.contiguous())
+    Dh, _ = toy.g.distances(toy.gevk, host, w.n_clients, w.chunks, toy.prm.scale)
+    Dd, _ = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale)
+    assert np.array_equal(Dh, toy.LC.torch_to_u64(Dd))
+
+
+def test_edge_cases(toy):
+    LC = toy.LC
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    # two clients: exactly one pair
+    D2, _ = toy.g.distances(toy.gevk, gcs[:2].contiguous(), 2, 1, toy.prm.scale)
+    D4, _ = toy.g.distances(toy.gevk, gcs, 4, 1, toy.prm.scale)
+    assert torch.equal(D2[0], D4[0])
+    with pytest.raises(LC.LancelotError):
+        toy.g.distances(toy.gevk, gcs[:1].contiguous(), 1, 1, toy.prm.scale)
+    empty = toy.g.evk()
+    with pytest.raises(LC.LancelotError, match="LC_EKEY"):
+        toy.g.distances(empty, gcs, 4, 1, toy.prm.scale)
+    with pytest.raises(LC.LancelotError):
+        toy.g.distances(toy.gevk, gcs, 4, 1, toy.prm.scale, groups=[1, 1])  # does not cover all slots
+
+
+# ------------------------------------------------------------------------------- production sizes
+
+def test_production_distances_small_bit_exact(prod):
+    w = S.Workload("p3", S.CFG_PLAIN, 15, 3, 2 * prod.prm.slots - 100, 0, (2,), "flip5", 1, 0)
+    W = S.client_updates(w)
+    X = S.split_chunks(W, prod.prm.slots)   # ragged: the last chunk is zero padded
+    ocs, gcs = prod.encrypt_both(X, range(3), range(w.chunks))
+    Dg, sc = prod.g.distances(prod.gevk, gcs, 3, w.chunks, prod.prm.scale)
+    Do = prod.o.distances(ocs, prod.orlk, prod.sched, prod.ork)
+    assert np.array_equal(prod.g_coeff(Dg, prod.L - 1), prod.o_coeff(Do))
+    k = 0
+    for i in range(3):
+        for j in range(i + 1, 3):
+            ref = np.sum((W[i] - W[j]) ** 2)
+            v = prod.g.decrypt(prod.keys.s, Dg[k].contiguous(), prod.L - 1, sc)
+            assert abs(v[0] - ref) / ref < 1e-5
+            k += 1
+
+
+@pytest.mark.slow
+def test_production_full_size_sampled(prod):
+    """Config of the benchmark (n=10, d=2^20, 64 chunks, batched launches): every pair against
+    FP64 and two sampled pairs + two sampled aggregate chunks bit-exact against the oracle."""
+    from paper_2408_06197_b300 import kgc
+    w = S.PLAIN
+    W = S.client_updates(w)
+    X = S.split_chunks(W, prod.prm.slots)
+    m = plaintexts(prod.o, prod.prm, X)
+    r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), range(w.chunks), prod.N)
+    gcs = prod.g.encrypt(prod.gpk, m.reshape(-1, prod.N), r, e0, e1).reshape(w.n_clients, w.chunks, 2, prod.L + 1,
+                                                                               prod.N)
+    Dg, sc = prod.g.distances(prod.gevk, gcs, w.n_clients, w.chunks, prod.prm.scale)
+    dist = np.zeros((w.n_clients, w.n_clients))
+    ref = np.zeros_like(dist)
+    k = 0
+    for i in range(w.n_clients):
+        for j in range(i + 1, w.n_clients):
+            v = prod.g.decrypt(prod.keys.s, Dg[k].contiguous(), prod.L - 1, sc)
+            ref[i, j] = ref[j, i] = np.sum((W[i] - W[j]) ** 2)
+            assert abs(v[0] - ref[i, j]) / ref[i, j] < 1e-5
+            dist[i, j] = dist[j, i] = v[0]
+            k += 1
+    sel = kgc.krum_select(dist, w.f, w.n_select)
+    assert sel == kgc.krum_select(ref, w.f, w.n_select) and not (set(sel) & set(w.byzantine))
+    # sampled pairs bit-exact: (0,1) and (7,9) -> local clients
+    clients = [0, 1, 7, 9]
+    idx = {c: k for k, c in enumerate(clients)}
+    ocs = np.stack([np.stack([prod.o.encrypt(prod.opk, m[c, k], r[c * w.chunks + k], e0[c * w.chunks + k],
+                                             e1[c * w.chunks + k]) for k in range(w.chunks)]) for c in clients])
+    pairs = [(0, 1), (7, 9)]
+    Do = prod.o.distances(ocs, prod.orlk, prod.sched, prod.ork, pairs=[(idx[i], idx[j]) for i, j in pairs])
+
+    def pidx(i, j):
+        return i * w.n_clients - i * (i + 1) // 2 + (j - i - 1)
+
+    for t, (i, j) in enumerate(pairs):
+        assert np.array_equal(prod.g_coeff(Dg[pidx(i, j)].contiguous(), prod.L - 1), prod.o_coeff(Do[t]))
+    # masked aggregate of the selected clients, weights 1/l
+    wts = kgc.mask_weights(w.n_clients, sel, average=True)
+    mm = plaintexts(prod.o, prod.prm, np.stack([np.full((1, prod.prm.slots), wts[i]) for i in range(w.n_clients)]))[:, 0]
+    rm, e0m, e1m = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), [S.MASK_CHUNK], prod.N)
+    gm = prod.g.encrypt(prod.gpk, mm, rm, e0m, e1m)
+    Ag, asc = prod.g.masked_aggregate(prod.gevk, gcs, w.n_clients, w.chunks, prod.prm.scale, gm, prod.prm.scale)
+    agg_ref = sum(wts[i] * W[i] for i in range(w.n_clients))
+    got = np.concatenate([prod.g.decrypt(prod.keys.s, Ag[k].contiguous(), prod.L - 1, asc) for k in range(w.chunks)])
+    assert np.linalg.norm(got - agg_ref) / np.linalg.norm(agg_ref) < 1e-5
+    om = np.stack([prod.o.encrypt(prod.opk, mm[i], rm[i], e0m[i], e1m[i]) for i in range(w.n_clients)])
+    for k in (0, w.chunks - 1):
+        ock = np.stack([prod.o.encrypt(prod.opk, m[c, k], r[c * w.chunks + k], e0[c * w.chunks + k],
+                                       e1[c * w.chunks + k]) for c in range(w.n_clients)])[:, None]
+        Ao = prod.o.masked_aggregate(np.ascontiguousarray(ock), om, prod.orlk)
+        assert np.array_equal(prod.g_coeff(Ag[k].contiguous(), prod.L - 1), prod.o_coeff(Ao[0]))
