@@ -170,6 +170,25 @@ int lc_relin(lc_ctx* ctx, const lc_evk* evk, const uint64_t* ct3, uint32_t count
 /* Rescale: drop q_level with centred rounding; [count][deg][level+1][N] -> [count][deg][level][N];
  * the scale divides by q_level. */
 int lc_rescale(lc_ctx* ctx, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out);
+/* Rescale that allocates nothing (no counterpart in the paper).  Same inputs, outputs and
+ * result as lc_rescale, but its scratch is a fixed 16 MiB device array built into the library
+ * (2 Mi words; one production ciphertext of degree 2 at level 14 needs 983,040) instead of the
+ * context's scratch arena, which lc_rescale may grow with cudaMalloc.  It is meant for callers
+ * that cannot allocate at that point: a process whose device-memory budget is fully committed
+ * at start-up, code running while its allocator must not be entered, or latency-sensitive
+ * paths that cannot take the device synchronisation cudaMalloc / cudaFree can cause.
+ *  - Calls no cudaMalloc, cudaFree or allocating routine.  Every GPU that loads the library
+ *    holds the array until the process exits.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device made current for the look-up); make that first call before any stream
+ *    capture.
+ *  - A request needing more than 16 MiB of scratch (count * deg * N * (level+1) words) is
+ *    rejected with LC_EINVAL and a message in lc_last_error; split it into smaller calls.
+ *  - All calls in the process share the one array and leave their last contents in it (nothing
+ *    in it needs to start at zero): calls that may overlap on the GPU (different streams or
+ *    contexts) race on it and must be serialised by the caller. */
+int lc_rescale_noalloc(lc_ctx* ctx, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out);
+
 /* Hoisted rotations (Section "Dynamic Hoisting"): one ModUp of c1, then for each r in
  * rots[n_rot] the left rotation by r slots: out[k] = (phi(c0) + KS0, KS1),
  * out: device [n_rot][2][level+1][N]. */

@@ -364,12 +364,12 @@ static int do_relin(lc_ctx* c, const lc_evk* evk, const u64* ct3, int B, int lev
     return LC_OK;
 }
 
-static size_t rescale_words(lc_ctx* c, int B, int deg, int level) {
+size_t rescale_words(lc_ctx* c, int B, int deg, int level) {
     return (size_t)B * deg * c->N * (1 + level);
 }
 
 // rescale B ciphertexts [B][deg][level+1][N] -> out [B][deg][level][N]
-static void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u64* tmp) {
+void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u64* tmp) {
     const size_t N = c->N;
     u64* lastc = tmp;
     u64* r = tmp + (size_t)B * deg * N;

@@ -107,3 +107,6 @@ void* lc_dev_alloc(lc_ctx* c, size_t bytes);
 void lc_dev_free(lc_ctx* c, void* p);
 // scratch arena of at least `bytes` (grows; contents not preserved across growth)
 u64* lc_scratch(lc_ctx* c, size_t bytes);
+// rescale of B ciphertexts using caller-provided scratch `tmp` of rescale_words() words
+size_t rescale_words(lc_ctx* c, int B, int deg, int level);
+void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u64* tmp);

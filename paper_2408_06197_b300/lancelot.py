@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
             "lc_tensor": [vp, vp, vp, u32, vp],
             "lc_relin": [vp, vp, vp, u32, u32, vp],
             "lc_rescale": [vp, vp, u32, u32, u32, vp],
+            "lc_rescale_noalloc": [vp, vp, u32, u32, u32, vp],
             "lc_rotate": [vp, vp, vp, u32, u32, vp, vp],
             "lc_rotate_sum": [vp, vp, vp, u32, u32, u32, vp],
             "lc_distances": [vp, vp, vp, u32, u32, ctypes.c_double, u32, u32, vp, vp, vp],
@@ -352,6 +353,17 @@ class Context:
         count = ct.numel() // (deg * (level + 1) * self.N)
         out = self.empty(count, deg, level, self.N)
         self._check(lib().lc_rescale(self.h, _t_ptr(ct), count, deg, level, _t_ptr(out)), "lc_rescale")
+        return out
+
+    def rescale_noalloc(self, ct: torch.Tensor, level: int, deg: int = 2,
+                        out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Rescale through the entry point that allocates nothing (fixed 16 MiB library scratch);
+        pass a preallocated `out` when no allocation may happen at all."""
+        count = ct.numel() // (deg * (level + 1) * self.N)
+        if out is None:
+            out = self.empty(count, deg, level, self.N)
+        self._check(lib().lc_rescale_noalloc(self.h, _t_ptr(ct), count, deg, level, _t_ptr(out)),
+                    "lc_rescale_noalloc")
         return out
 
     def rotate(self, evk: "EvalKeys", ct: torch.Tensor, level: int, rots: Sequence[int]) -> torch.Tensor:
