@@ -199,9 +199,10 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- kernel micro case
 def run_micro(args):
-    """Small isolated case for profiler captures (a few hundred MB on the device, inputs larger
-    than L2): 16 degree-2 triples relinearised and rescaled at level 14, 16 ciphertexts rotated at
-    level 13, and 960 limbs transformed forward and back.  Prints per-class timings."""
+    """Small isolated case for profiler captures (about 3 GB on the device, inputs larger than
+    L2): batched distances of 10 clients x 8 chunks (45 pairs), 960 limbs transformed forward and
+    back, 16 degree-2 triples relinearised and rescaled at level 14, and 16 ciphertexts rotated
+    at level 13.  Prints per-class timings."""
     import torch
     from paper_2408_06197_b300 import lancelot as LC
     w = S.PLAIN
@@ -217,9 +218,21 @@ def run_micro(args):
     ct3 = torch.randint(0, 1 << 40, (B, 3, g.nq, N), device="cuda", generator=gen)
     cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
     limbs = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
+    # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input)
+    for r in LC.rotations_of_schedule([1] * (g.log_n - 1)):
+        if r != 1:
+            evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
+    rng = np.random.default_rng(5)
+    dc = np.empty((10, 8, 2, g.nq, N), dtype=np.uint64)
+    for i, q in enumerate(g.q):
+        dc[:, :, :, i] = rng.integers(0, q, size=(10, 8, 2, N), dtype=np.uint64)
+    dcts = LC.u64_to_torch(dc)
+    del dc
+    dout = g.empty(45, 2, g.L, N)
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             g.profile_start()
+        g.distances(evk, dcts, 10, 8, g.scale, out=dout)
         x = g.to_eval(limbs, g.L)
         g.to_coeff(x, g.L)
         r2 = g.relin(evk, ct3, g.L)
@@ -288,13 +301,14 @@ def main():
         time.sleep(0.3)
         l0 = LC.launches()
         g.profile_start()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev0, ev1 = evs[0], evs[-1]
         ev0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[k + 1].record(stream)
         torch.cuda.synchronize()
+        step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
         prof = g.profile_stop()
         launches = LC.launches() - l0
         barrier()
@@ -363,7 +377,10 @@ def main():
                        "chunks": w.chunks, "pairs": w.n_pairs, "log_n": 15, "limbs_q": 15, "limbs_p": 4, "dnum": 4,
                        "rotations": 14, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},
-            "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e}
+            "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e,
+            "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                                 "definition": "one round = 45 pair distances + masked aggregate of 64 chunks, "
+                                               "device time per step (rank 0)"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, per, threads, step_s = oracle_sample(w, reps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",

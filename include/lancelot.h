@@ -105,6 +105,11 @@ int lc_launches(uint64_t* out);
  * 6 automorphism, 7 other) the summed milliseconds, algorithmic bytes and launches [8]. */
 int lc_profile(lc_ctx* ctx, int start, double* ms, double* bytes, uint64_t* launches);
 
+/* Caps how many pairs / chunks one batched wave of lc_distances / lc_masked_aggregate
+ * processes (0 = only the 8 GiB scratch budget limits it).  Smaller waves use less scratch;
+ * results are identical for every setting. */
+int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
+
 /* ---------------------------------------------------------------- keys (KGC side) */
 
 /* Public key pk = ([-a s + e]_Q, a) (Section "CKKS Scheme Description", Key generation).

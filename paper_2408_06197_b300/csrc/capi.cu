@@ -186,6 +186,10 @@ static int build_tables(lc_ctx* c) {
                 const u64 mt = c->mod[mi];
                 t.dst_row[nd] = r;
                 t.dst_mod[nd] = mi;
+                t.dq[nd] = c->mc_host[mi].q;
+                t.dr64[nd] = c->mc_host[mi].r64;
+                t.dr64sh[nd] = c->mc_host[mi].r64_sh;
+                t.donesh[nd] = c->mc_host[mi].one_sh;
                 for (int i = lo; i < hi; i++) {
                     u64 prod = 1 % mt;
                     for (int k = lo; k < hi; k++)
@@ -228,6 +232,10 @@ static int build_tables(lc_ctx* c) {
         for (int k = 0; k < c->np; k++) P = hmul(P, c->mod[c->nq + k] % qi, qi);
         md.pinv[i] = hinv(P, qi);
         md.pinv_sh[i] = shoup_of(md.pinv[i], qi);
+        md.qq[i] = c->mc_host[i].q;
+        md.qr64[i] = c->mc_host[i].r64;
+        md.qr64sh[i] = c->mc_host[i].r64_sh;
+        md.qonesh[i] = c->mc_host[i].one_sh;
     }
     // rescale tables
     std::vector<RescaleTab> rs(c->nq);
@@ -976,7 +984,15 @@ int lc_profile(lc_ctx* c, int start, double* ms, double* bytes, uint64_t* launch
 // ------------------------------------------------------------------------------------ the method
 static int max_batch_for(lc_ctx* c, size_t words_per_item, size_t budget_words) {
     size_t b = budget_words / std::max<size_t>(1, words_per_item);
-    return (int)std::max<size_t>(1, std::min<size_t>(b, 4096));
+    b = std::max<size_t>(1, std::min<size_t>(b, 4096));
+    if (c->max_batch) b = std::min<size_t>(b, c->max_batch);
+    return (int)b;
+}
+
+int lc_set_max_batch(lc_ctx* c, uint32_t max_items) {
+    if (!c) return LC_EINVAL;
+    c->max_batch = max_items;
+    return LC_OK;
 }
 
 int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
@@ -1029,9 +1045,10 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         const int b = std::min(Bw, npairs - p0);
         {
             // compulsory bytes: every client tile this launch touches, once, plus the outputs
-            const int touched = b == npairs ? (int)n : 2 * b;
+            const int touched = mode == LC_MODE_PER_OP ? 2 * b : std::min((int)n, 2 * b);
             PROF(c, PROF_TENSOR, ((double)touched * chunks * 2.0 + 3.0 * b) * Pin * 8.0, (uint64_t)b,
-                 op_sq_acc_pairs(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3));
+                 mode == LC_MODE_PER_OP ? op_sq_acc_pairs(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3)
+                                        : op_sq_acc_tiled(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3));
         }
         int st = do_relin(c, evk, acc3, b, L, ct2, tmp);
         if (st) return st;

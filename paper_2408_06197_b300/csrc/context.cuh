@@ -25,6 +25,8 @@ struct ModUpTab {
     int dst_mod[LC_MAX_DST];
     u64 hat[LC_MAX_SRC][LC_MAX_DST];   // D/q_i mod m_t
     u64 corr[LC_MAX_SRC][LC_MAX_DST];  // (-q_i * hat) mod m_t, added when y_i is negative
+    // reduction constants of each destination modulus m_t (see ModConst)
+    u64 dq[LC_MAX_DST], dr64[LC_MAX_DST], dr64sh[LC_MAX_DST], donesh[LC_MAX_DST];
 };
 
 // ModDown from Q_l U P to Q_l: y_k = [v_pk (P/p_k)^-1]_{p_k} (centred),
@@ -36,6 +38,8 @@ struct ModDownTab {
     u64 phat[LC_MAX_P][LC_MAX_DST];
     u64 corr[LC_MAX_P][LC_MAX_DST];
     u64 pinv[LC_MAX_DST], pinv_sh[LC_MAX_DST];
+    // reduction constants of each q_i (see ModConst)
+    u64 qq[LC_MAX_DST], qr64[LC_MAX_DST], qr64sh[LC_MAX_DST], qonesh[LC_MAX_DST];
 };
 
 // Rescale at level l: out_i = (x_i - [r]_{q_i}) q_l^-1 for i < l, r the centred last residue.
@@ -91,6 +95,7 @@ struct lc_ctx {
     size_t stage_bytes = 0;
     std::string err;
     uint64_t n_keyswitch = 0, n_modup = 0;
+    uint32_t max_batch = 0;  // 0 = limited only by the scratch budget
     // profiling
     bool prof_on = false;
     std::vector<ProfRec> prof;

@@ -38,11 +38,19 @@ __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a 
 struct u128v {
     u64 lo, hi;
 };
+// acc += a * b (128-bit), one carry chain
 __device__ __forceinline__ void mac128(u128v& acc, u64 a, u64 b) {
-    u64 lo = a * b;
-    u64 hi = __umul64hi(a, b);
-    acc.lo += lo;
-    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(a), "l"(b));
+}
+// acc += v (64-bit addend)
+__device__ __forceinline__ void add128(u128v& acc, u64 v) {
+    asm("add.cc.u64 %0, %0, %2;\n\t"
+        "addc.u64 %1, %1, 0;"
+        : "+l"(acc.lo), "+l"(acc.hi)
+        : "l"(v));
 }
 // (hi * 2^64 + lo) mod q in [0, q) for any hi, lo
 __device__ __forceinline__ u64 reduce128(u128v x, const ModConst& m) {
@@ -65,4 +73,13 @@ __device__ __forceinline__ u64 lift_centred(u64 v, u64 p, u64 q) {
         return neg ? q - neg : 0;
     }
     return v % q;
+}
+
+// (hi * 2^64 + lo) mod q in [0, q), constants given explicitly (q < 2^62)
+__device__ __forceinline__ u64 reduce128c(u128v x, u64 q, u64 r64, u64 r64_sh, u64 one_sh) {
+    u64 a = mul_shoup_lazy(x.hi, r64, r64_sh, q);
+    u64 b = x.lo - __umul64hi(x.lo, one_sh) * q;
+    u64 s = a + b;
+    s = csub(s, 2 * q);
+    return csub(s, q);
 }

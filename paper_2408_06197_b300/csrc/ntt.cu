@@ -23,13 +23,12 @@ __device__ __forceinline__ u64* limb_ptr(u64* base, size_t batch_stride, const R
     return base + (size_t)bi * batch_stride + ((size_t)map.row[r] << log_n);
 }
 
-// Cooley-Tukey butterfly, inputs/outputs in [0, 2q)
+// Cooley-Tukey butterfly (Harvey): inputs and outputs in [0, 4q), one conditional subtraction
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
-    u64 t = mul_shoup_lazy(y, w.x, w.y, q);
-    u64 a = x + t;
-    u64 b = x + two_q - t;
-    x = csub(a, two_q);
-    y = csub(b, two_q);
+    const u64 xr = csub(x, two_q);                   // [0, 2q)
+    const u64 t = mul_shoup_lazy(y, w.x, w.y, q);    // [0, 2q) for any y < 2^64
+    x = xr + t;
+    y = xr + two_q - t;
 }
 // Gentleman-Sande butterfly, inputs/outputs in [0, 2q)
 __device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
@@ -69,8 +68,8 @@ __global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_st
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            const int row = rg + RS * u;
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q, mc.two_q);
+            // row = rg + RS*u with rg < RS <= 2^b: row >> (b+1) = u >> (b+1-R2), a compile-time offset
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q, mc.two_q);
         }
     }
     if constexpr (R2 == 0) {
@@ -94,8 +93,8 @@ __global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_st
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     if (v >> st & 1) continue;
-                    const int row = (grp << R2) + v;
-                    ct_bfly(y[v], y[v | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q,
+                    ct_bfly(y[v], y[v | (1 << st)],
+                            ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
                             mc.two_q);
                 }
             }
@@ -139,8 +138,8 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     if (v >> st & 1) continue;
-                    const int row = (grp << R2) + v;
-                    gs_bfly(y[v], y[v | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q,
+                    gs_bfly(y[v], y[v | (1 << st)],
+                            ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
                             mc.two_q);
                 }
             }
@@ -165,8 +164,8 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
                 x[u] = mul_shoup(xa, mc.n_inv, mc.n_inv_sh, mc.q);
                 x[u | 8] = mul_shoup(xb, wl.x, wl.y, mc.q);
             } else {
-                const int row = rg + RS * u;
-                gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (row >> (b + 1))), mc.q, mc.two_q);
+                gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q,
+                        mc.two_q);
             }
         }
     }
@@ -175,8 +174,8 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
 }
 
 // ------------------------------------------------------------------------------ row pass
-// forward: bits 7 .. 0 inside 256-word blocks; output fully reduced to [0, q)
-__global__ void __launch_bounds__(kRowThreads) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+// forward: bits 7 .. 0 inside 256-word blocks; input in [0, 4q), output fully reduced to [0, q)
+__global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
                                                            NttTables tb) {
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
@@ -196,8 +195,9 @@ __global__ void __launch_bounds__(kRowThreads) ntt_fwd_row(u64* base, size_t bat
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            const int j = g0 + lo + 16 * u;
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+            // j = g0 + lo + 16u, g0 a multiple of 256, lo < 16: j >> (b+1) = (g0 >> (b+1)) + (u >> (b-3))
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))), mc.q,
+                    mc.two_q);
         }
     }
 #pragma unroll
@@ -211,19 +211,20 @@ __global__ void __launch_bounds__(kRowThreads) ntt_fwd_row(u64* base, size_t bat
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            const int j = g0 + 16 * lo + u;
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+            // j = (g0 + 16 lo) + u with the bracket a multiple of 16: offset u >> (b+1)
+            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))),
+                    mc.q, mc.two_q);
         }
     }
 #pragma unroll
-    for (int u = 0; u < 16; u++) s[swz((blk << 8) + 16 * lo + u)] = csub(x[u], mc.q);
+    for (int u = 0; u < 16; u++) s[swz((blk << 8) + 16 * lo + u)] = csub(csub(x[u], mc.two_q), mc.q);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];
 }
 
 // inverse: bits 0 .. 7 inside 256-word blocks; output in [0, 2q) for the column pass
-__global__ void __launch_bounds__(kRowThreads) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+__global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
                                                            NttTables tb) {
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
@@ -246,8 +247,8 @@ __global__ void __launch_bounds__(kRowThreads) ntt_inv_row(u64* base, size_t bat
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            const int j = g0 + 16 * lo + u;
-            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))),
+                    mc.q, mc.two_q);
         }
     }
 #pragma unroll
@@ -261,8 +262,8 @@ __global__ void __launch_bounds__(kRowThreads) ntt_inv_row(u64* base, size_t bat
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            const int j = g0 + lo + 16 * u;
-            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (j >> (b + 1))), mc.q, mc.two_q);
+            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))), mc.q,
+                    mc.two_q);
         }
     }
 #pragma unroll

@@ -11,7 +11,7 @@
 //                   a CTA owns a 2^C x 16 tile (rows strided by 256 words, 16 columns)
 //   row pass     -- stages with t < 256; a CTA owns 8 contiguous blocks of 256 words.
 // Inside a pass, each thread runs up to 4 stages (radix 16) in registers between shared
-// memory exchanges.  Butterflies are Harvey-lazy: values stay in [0, 2q) between stages.
+// memory exchanges.  Butterflies are Harvey-lazy: forward values stay in [0, 4q), inverse values in [0, 2q).
 #pragma once
 #include <cstdint>
 #include "modarith.cuh"

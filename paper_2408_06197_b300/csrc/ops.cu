@@ -123,6 +123,151 @@ __global__ void __launch_bounds__(kT) k_sq_acc_pairs(const u64* __restrict__ cts
     o[2 * P] = reduce128(s11, m);
 }
 
+// Batched distances tensor phase with client-block tiling.  Clients are grouped in blocks of
+// `cb` (all clients when n <= 11, else 8); a CTA owns one pair of client blocks (I <= J), one
+// 32-coefficient tile and one limb.  Chunk tiles of all its clients stream through a
+// kStages-deep shared-memory ring filled with cp.async (kStages-1 chunks in flight); each warp
+// owns a set of pairs and one lane per coefficient, and accumulates (a-b)^2 for every chunk.
+// Each client tile is read from HBM about n/cb times instead of n-1 times.  Pairs outside
+// [p0, p0+np) are skipped (waves).
+constexpr int kTX = 32;
+constexpr int kStages = 4;
+constexpr int kMaxSlots = 16;                  // client slots staged per chunk (2 blocks of 8, or 11)
+constexpr int kWarps = kT / 32;                // 8 pair slots
+constexpr int kPPT = 8;                        // pairs per thread: 64 / 8 (and ceil(55 / 8) = 7)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_)); }
+
+__global__ void __launch_bounds__(kT, 2) k_sq_acc_tiled(const u64* __restrict__ cts, int n, int chunks, int nl,
+                                                        int log_n, int cb, int p0, int np,
+                                                        const ModConst* __restrict__ mc, u64* __restrict__ out) {
+    __shared__ __align__(16) u64 sh[kStages][kMaxSlots][2][kTX];
+    const int nb = (n + cb - 1) / cb;
+    int bp = blockIdx.x, I = 0;
+    while (bp >= nb - I) {
+        bp -= nb - I;
+        I++;
+    }
+    const int J = I + bp;
+    const int cI0 = I * cb, cJ0 = J * cb;
+    const int cntI = min(cb, n - cI0), cntJ = min(cb, n - cJ0);
+    const bool diag = I == J;
+    const int total = diag ? cntI * (cntI - 1) / 2 : cntI * cntJ;
+    const int nslots = diag ? cntI : cntI + cntJ;
+    const int limb = blockIdx.z;
+    const size_t N = (size_t)1 << log_n;
+    const int tid = threadIdx.x, x = tid & 31, warp = tid >> 5;
+    const size_t x0 = (size_t)blockIdx.y * kTX;
+    const ModConst m = mc[limb];
+    const size_t P = (size_t)nl * N;
+    // per pair: (output index << 8) | (slot a << 4) | slot b, or -1 when the pair is not owned
+    int pk[kPPT];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kPPT; k++) {
+        const int pi = warp + kWarps * k;
+        pk[k] = -1;
+        int sa = 0, sb = 0;
+        if (pi < total) {
+            int a, b;
+            if (diag) {
+                a = 0;
+                int r = pi;
+                while (r >= cntI - 1 - a) {
+                    r -= cntI - 1 - a;
+                    a++;
+                }
+                b = a + 1 + r;
+                sa = a;
+                sb = b;
+            } else {
+                a = pi / cntJ;
+                b = pi - a * cntJ;
+                sa = a;
+                sb = cntI + b;
+            }
+            const int i = cI0 + a, j = (diag ? cI0 : cJ0) + b;
+            const int g = i * n - i * (i + 1) / 2 + (j - i - 1);
+            if (g >= p0 && g < p0 + np) {
+                pk[k] = ((g - p0) << 8) | (sa << 4) | sb;
+                any = true;
+            }
+        }
+    }
+    if (!__syncthreads_or(any)) return;
+    // 16-byte copy units: (client slot, poly, coefficient pair): 32 per slot, <= 512 -> 2 per thread
+    const int units = nslots * 2 * (kTX / 2);
+    const u64* gsrc[2];
+    int ucs[2], upp[2], uxx[2];
+    bool ucopy[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int u = tid + h * kT;
+        ucopy[h] = u < units;
+        ucs[h] = u / kTX;
+        upp[h] = (u / (kTX / 2)) & 1;
+        uxx[h] = (u % (kTX / 2)) * 2;
+        const int c = ucs[h] < cntI ? cI0 + ucs[h] : cJ0 + (ucs[h] - cntI);
+        gsrc[h] = cts + ((size_t)(ucopy[h] ? c : 0) * chunks * 2 + upp[h]) * P + (size_t)limb * N + x0 + uxx[h];
+    }
+    const size_t chunk_stride = 2 * P;
+#pragma unroll
+    for (int st = 0; st < kStages - 1; st++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+            if (ucopy[h] && st < chunks) cp_async16(&sh[st][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)st * chunk_stride);
+        cp_async_commit();
+    }
+    u128v s00[kPPT], s01[kPPT], s11[kPPT];
+#pragma unroll
+    for (int k = 0; k < kPPT; k++) s00[k] = s01[k] = s11[k] = u128v{0, 0};
+    for (int k = 0; k < chunks; k++) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        {
+            const int nk = k + kStages - 1;
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+                if (ucopy[h] && nk < chunks)
+                    cp_async16(&sh[nk % kStages][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)nk * chunk_stride);
+            cp_async_commit();
+        }
+        const int cur = k % kStages;
+#pragma unroll
+        for (int t = 0; t < kPPT; t++) {
+            if (pk[t] < 0) continue;
+            const int sa = (pk[t] >> 4) & 15, sb = pk[t] & 15;
+            const u64 a0 = sh[cur][sa][0][x], a1 = sh[cur][sa][1][x];
+            const u64 b0 = sh[cur][sb][0][x], b1 = sh[cur][sb][1][x];
+            const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
+            mac128(s00[t], d0, d0);
+            mac128(s01[t], d0, d1);
+            mac128(s11[t], d1, d1);
+            if ((k & 7) == 7) {
+                fold(s00[t], m);
+                fold(s01[t], m);
+                fold(s11[t], m);
+            }
+        }
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int t = 0; t < kPPT; t++) {
+        if (pk[t] < 0) continue;
+        u64* o = out + (size_t)(pk[t] >> 8) * 3 * P + (size_t)limb * N + x0 + x;
+        o[0] = reduce128(s00[t], m);
+        const u64 d1 = reduce128(s01[t], m);
+        o[P] = add_mod(d1, d1, m.q);
+        o[2 * P] = reduce128(s11[t], m);
+    }
+}
+
 // grid: x = chunk (fastest; the masks are shared by every chunk), y = tile, z = limb
 __global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, int n, int chunks, int nl, int log_n,
                                                  int k0, const u64* __restrict__ masks,
@@ -155,145 +300,164 @@ __global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, in
 }
 
 // ---------------------------------------------------------------------------- base conversion
-// grid: x = coefficient tile, y = b * beta + j
-__global__ void __launch_bounds__(kT) k_modup(const u64* __restrict__ coef, size_t coef_stride, int beta, int rows,
-                                              int log_n, const ModUpTab* __restrict__ tabs,
-                                              const ModConst* __restrict__ mc, u64* __restrict__ ext) {
-    __shared__ ModUpTab tab;
-    const int b = blockIdx.y / beta, j = blockIdx.y - b * beta;
-    {
-        const int words = sizeof(ModUpTab) / 8;
-        const u64* src = reinterpret_cast<const u64*>(tabs + j);
-        u64* dst = reinterpret_cast<u64*>(&tab);
-        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
-    }
+// All four kernels handle VEC consecutive coefficients per thread with 16-byte accesses; the
+// per-destination reduction constants come from the shared-memory copy of the table.
+
+template <typename Tab>
+__device__ __forceinline__ void load_tab(Tab& dst, const Tab* src) {
+    const int words = sizeof(Tab) / 8;
+    const u64* s = reinterpret_cast<const u64*>(src);
+    u64* d = reinterpret_cast<u64*>(&dst);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) d[w] = s[w];
     __syncthreads();
+}
+
+__device__ __forceinline__ ulonglong2 ld2(const u64* p) { return __ldg(reinterpret_cast<const ulonglong2*>(p)); }
+__device__ __forceinline__ void st2(u64* p, u64 a, u64 b) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b); }
+
+// ModUp of NS-prime digits j0 .. j0+nj-1.  grid: x = tile of 2*kT coefficients, y = b * nj + (j - j0)
+template <int NS>
+__global__ void __launch_bounds__(kT) k_modup(const u64* __restrict__ coef, size_t coef_stride, int beta, int j0,
+                                              int nj, int rows, int log_n, const ModUpTab* __restrict__ tabs,
+                                              u64* __restrict__ ext) {
+    __shared__ ModUpTab tab;
+    const int b = blockIdx.y / nj, j = j0 + (blockIdx.y - (blockIdx.y / nj) * nj);
+    load_tab(tab, tabs + j);
     const size_t N = (size_t)1 << log_n;
-    const size_t x = (size_t)blockIdx.x * kT + threadIdx.x;
+    const size_t x = ((size_t)blockIdx.x * kT + threadIdx.x) * 2;
     const u64* cb = coef + (size_t)b * coef_stride + x;
-    u64 y[LC_MAX_SRC];
-    bool neg[LC_MAX_SRC];
-    const int ns = tab.n_src;
+    u64 y0[NS], y1[NS];
+    unsigned negm = 0;
 #pragma unroll
-    for (int i = 0; i < LC_MAX_SRC; i++) {
-        if (i < ns) {
-            const u64 q = tab.src_q[i];
-            const u64 v = __ldg(cb + ((size_t)tab.src_row[i] << log_n));
-            y[i] = csub(mul_shoup_lazy(v, tab.hinv[i], tab.hinv_sh[i], q), q);
-            neg[i] = y[i] > (q >> 1);
-        }
+    for (int i = 0; i < NS; i++) {
+        const u64 q = tab.src_q[i];
+        const ulonglong2 v = ld2(cb + ((size_t)tab.src_row[i] << log_n));
+        y0[i] = csub(mul_shoup_lazy(v.x, tab.hinv[i], tab.hinv_sh[i], q), q);
+        y1[i] = csub(mul_shoup_lazy(v.y, tab.hinv[i], tab.hinv_sh[i], q), q);
+        negm |= (y0[i] > (q >> 1) ? 1u : 0u) << (2 * i);
+        negm |= (y1[i] > (q >> 1) ? 2u : 0u) << (2 * i);
     }
     u64* eb = ext + ((size_t)b * beta + j) * rows * N + x;
-    for (int t = 0; t < tab.n_dst; t++) {
-        const ModConst m = mc[tab.dst_mod[t]];
-        u128v acc{0, 0};
+    const int nd = tab.n_dst;
+    for (int t = 0; t < nd; t++) {
+        u128v a0{0, 0}, a1{0, 0};
 #pragma unroll
-        for (int i = 0; i < LC_MAX_SRC; i++) {
-            if (i < ns) {
-                mac128(acc, y[i], tab.hat[i][t]);
-                if (neg[i]) {
-                    const u64 cr = tab.corr[i][t];
-                    acc.lo += cr;
-                    acc.hi += acc.lo < cr ? 1 : 0;
-                }
-            }
+        for (int i = 0; i < NS; i++) {
+            const u64 h = tab.hat[i][t], cr = tab.corr[i][t];
+            mac128(a0, y0[i], h);
+            mac128(a1, y1[i], h);
+            if (negm >> (2 * i) & 1) add128(a0, cr);
+            if (negm >> (2 * i) & 2) add128(a1, cr);
         }
-        eb[(size_t)tab.dst_row[t] << log_n] = reduce128(acc, m);
+        const u64 q = tab.dq[t], r64 = tab.dr64[t], r64sh = tab.dr64sh[t], osh = tab.donesh[t];
+        st2(eb + ((size_t)tab.dst_row[t] << log_n), reduce128c(a0, q, r64, r64sh, osh),
+            reduce128c(a1, q, r64, r64sh, osh));
     }
 }
 
-// grid: x = batch item (fastest, so one key tile serves every item through L2), y = tile, z = row
+// key inner product.  grid: x = batch item (fastest: one key tile serves every item through L2),
+// y = tile of 4*kT coefficients, z = row t of Q_l U P
 __global__ void __launch_bounds__(kT) k_inner(const u64* __restrict__ ext, const u64* __restrict__ d, size_t d_stride,
                                               int beta, int nl, int rows, int alpha, int nq, int nqp, int log_n,
                                               const u64* __restrict__ key, const ModConst* __restrict__ mc,
-                                              int mod_of_p0, u64* __restrict__ v) {
+                                              u64* __restrict__ v) {
     const int b = blockIdx.x, t = blockIdx.z;
     const size_t N = (size_t)1 << log_n;
-    const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
+    const size_t x = ((size_t)blockIdx.y * kT + threadIdx.x) * 4;
     const int kt = t < nl ? t : nq + (t - nl);
-    const ModConst m = mc[t < nl ? t : mod_of_p0 + (t - nl)];
-    u128v a0{0, 0}, a1{0, 0};
+    const ModConst& mcr = mc[kt];
+    const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
+    u128v a[4], c[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) a[k] = c[k] = u128v{0, 0};
     for (int j = 0; j < beta; j++) {
-        u64 e;
-        if (t < nl && t / alpha == j) e = __ldg(d + (size_t)b * d_stride + ((size_t)t << log_n) + x);
-        else e = __ldg(ext + (((size_t)b * beta + j) * rows + t) * N + x);
-        const u64 kb = __ldg(key + (((size_t)j * 2 + 0) * nqp + kt) * N + x);
-        const u64 ka = __ldg(key + (((size_t)j * 2 + 1) * nqp + kt) * N + x);
-        mac128(a0, e, kb);
-        mac128(a1, e, ka);
+        const u64* src = (t < nl && t / alpha == j) ? d + (size_t)b * d_stride + ((size_t)t << log_n)
+                                                     : ext + (((size_t)b * beta + j) * rows + t) * N;
+        const u64* kb = key + (((size_t)j * 2 + 0) * nqp + kt) * N + x;
+        const u64* ka = key + (((size_t)j * 2 + 1) * nqp + kt) * N + x;
+        const ulonglong2 e01 = ld2(src + x), e23 = ld2(src + x + 2);
+        const ulonglong2 b01 = ld2(kb), b23 = ld2(kb + 2), a01 = ld2(ka), a23 = ld2(ka + 2);
+        mac128(a[0], e01.x, b01.x);
+        mac128(a[1], e01.y, b01.y);
+        mac128(a[2], e23.x, b23.x);
+        mac128(a[3], e23.y, b23.y);
+        mac128(c[0], e01.x, a01.x);
+        mac128(c[1], e01.y, a01.y);
+        mac128(c[2], e23.x, a23.x);
+        mac128(c[3], e23.y, a23.y);
     }
     u64* vb = v + (size_t)b * 2 * rows * N + (size_t)t * N + x;
-    vb[0] = reduce128(a0, m);
-    vb[(size_t)rows * N] = reduce128(a1, m);
+    st2(vb, reduce128c(a[0], q, r64, r64sh, osh), reduce128c(a[1], q, r64, r64sh, osh));
+    st2(vb + 2, reduce128c(a[2], q, r64, r64sh, osh), reduce128c(a[3], q, r64, r64sh, osh));
+    u64* vc = vb + (size_t)rows * N;
+    st2(vc, reduce128c(c[0], q, r64, r64sh, osh), reduce128c(c[1], q, r64, r64sh, osh));
+    st2(vc + 2, reduce128c(c[2], q, r64, r64sh, osh), reduce128c(c[3], q, r64, r64sh, osh));
 }
 
-// grid: x = tile, y = b * 2 + k
+// ModDown conversion of the K special-prime rows.  grid: x = tile of 2*kT coefficients, y = b*2 + k
+template <int K>
 __global__ void __launch_bounds__(kT) k_moddown_bconv(const u64* __restrict__ v, int nl, int rows, int log_n,
-                                                      const ModDownTab* __restrict__ tabp,
-                                                      const ModConst* __restrict__ mc, u64* __restrict__ conv) {
+                                                      const ModDownTab* __restrict__ tabp, u64* __restrict__ conv) {
     __shared__ ModDownTab tab;
-    {
-        const int words = sizeof(ModDownTab) / 8;
-        const u64* src = reinterpret_cast<const u64*>(tabp);
-        u64* dst = reinterpret_cast<u64*>(&tab);
-        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
-    }
-    __syncthreads();
+    load_tab(tab, tabp);
     const size_t N = (size_t)1 << log_n;
-    const size_t x = (size_t)blockIdx.x * kT + threadIdx.x;
+    const size_t x = ((size_t)blockIdx.x * kT + threadIdx.x) * 2;
     const int bk = blockIdx.y;
     const u64* vb = v + (size_t)bk * rows * N + x;
-    const int K = tab.K;
-    u64 y[LC_MAX_P];
-    bool neg[LC_MAX_P];
+    u64 y0[K], y1[K];
+    unsigned negm = 0;
 #pragma unroll
-    for (int k = 0; k < LC_MAX_P; k++) {
-        if (k < K) {
-            const u64 p = tab.p[k];
-            const u64 val = __ldg(vb + ((size_t)(nl + k) << log_n));
-            y[k] = csub(mul_shoup_lazy(val, tab.phinv[k], tab.phinv_sh[k], p), p);
-            neg[k] = y[k] > (p >> 1);
-        }
+    for (int k = 0; k < K; k++) {
+        const u64 p = tab.p[k];
+        const ulonglong2 val = ld2(vb + ((size_t)(nl + k) << log_n));
+        y0[k] = csub(mul_shoup_lazy(val.x, tab.phinv[k], tab.phinv_sh[k], p), p);
+        y1[k] = csub(mul_shoup_lazy(val.y, tab.phinv[k], tab.phinv_sh[k], p), p);
+        negm |= (y0[k] > (p >> 1) ? 1u : 0u) << (2 * k);
+        negm |= (y1[k] > (p >> 1) ? 2u : 0u) << (2 * k);
     }
     u64* cb = conv + (size_t)bk * nl * N + x;
     for (int i = 0; i < nl; i++) {
-        const ModConst m = mc[i];
-        u128v acc{0, 0};
+        u128v a0{0, 0}, a1{0, 0};
 #pragma unroll
-        for (int k = 0; k < LC_MAX_P; k++) {
-            if (k < K) {
-                mac128(acc, y[k], tab.phat[k][i]);
-                if (neg[k]) {
-                    const u64 cr = tab.corr[k][i];
-                    acc.lo += cr;
-                    acc.hi += acc.lo < cr ? 1 : 0;
-                }
-            }
+        for (int k = 0; k < K; k++) {
+            const u64 h = tab.phat[k][i], cr = tab.corr[k][i];
+            mac128(a0, y0[k], h);
+            mac128(a1, y1[k], h);
+            if (negm >> (2 * k) & 1) add128(a0, cr);
+            if (negm >> (2 * k) & 2) add128(a1, cr);
         }
-        cb[(size_t)i << log_n] = reduce128(acc, m);
+        const u64 q = tab.qq[i], r64 = tab.qr64[i], r64sh = tab.qr64sh[i], osh = tab.qonesh[i];
+        st2(cb + ((size_t)i << log_n), reduce128c(a0, q, r64, r64sh, osh), reduce128c(a1, q, r64, r64sh, osh));
     }
 }
 
+// W[b][k] = (v_k - conv_k) P^-1 + add_k over 2 coefficients per thread; grid-stride over B*2*nl*N/2
 __global__ void k_moddown_combine(const u64* __restrict__ v, const u64* __restrict__ conv, int B, int nl, int rows,
                                   int log_n, const ModDownTab* __restrict__ tab, const ModConst* __restrict__ mc,
                                   const u64* __restrict__ add0, const u64* __restrict__ add1, size_t add_stride,
                                   u64* __restrict__ w, size_t w_stride) {
     const size_t N = (size_t)1 << log_n;
-    const size_t total = (size_t)B * 2 * nl * N;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t total = (size_t)B * 2 * nl * N / 2;
+    for (size_t h = (size_t)blockIdx.x * blockDim.x + threadIdx.x; h < total; h += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = h * 2;
         const size_t x = idx & (N - 1);
         const size_t r = idx >> log_n;  // (b*2 + k)*nl + i
         const int i = (int)(r % nl);
         const size_t bk = r / nl;
         const int k = (int)(bk & 1);
         const size_t b = bk >> 1;
-        const ModConst m = mc[i];
-        const u64 vv = v[(bk * rows + i) * N + x];
-        const u64 cc = conv[(bk * nl + i) * N + x];
-        u64 o = mul_shoup(sub_mod(vv, cc, m.q), tab->pinv[i], tab->pinv_sh[i], m.q);
+        const u64 q = __ldg(&tab->qq[i]), pinv = __ldg(&tab->pinv[i]), pinvsh = __ldg(&tab->pinv_sh[i]);
+        const ulonglong2 vv = ld2(v + (bk * rows + i) * N + x);
+        const ulonglong2 cc = ld2(conv + (bk * nl + i) * N + x);
+        u64 o0 = mul_shoup(sub_mod(vv.x, cc.x, q), pinv, pinvsh, q);
+        u64 o1 = mul_shoup(sub_mod(vv.y, cc.y, q), pinv, pinvsh, q);
         const u64* add = k == 0 ? add0 : add1;
-        if (add) o = add_mod(o, add[b * add_stride + ((size_t)i << log_n) + x], m.q);
-        w[b * w_stride + ((size_t)(k * nl + i) << log_n) + x] = o;
+        if (add) {
+            const ulonglong2 aa = ld2(add + b * add_stride + ((size_t)i << log_n) + x);
+            o0 = add_mod(o0, aa.x, q);
+            o1 = add_mod(o1, aa.y, q);
+        }
+        st2(w + b * w_stride + ((size_t)(k * nl + i) << log_n) + x, o0, o1);
     }
 }
 
@@ -461,6 +625,14 @@ void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     g_lc_launches += 1;
 }
 
+void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p0, int np, u64* out) {
+    const int cb = n <= 11 ? n : 8;  // one diagonal block up to 11 clients (55 pairs), else blocks of 8
+    const int nb = (n + cb - 1) / cb;
+    dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), nl);
+    k_sq_acc_tiled<<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, c->log_n, cb, p0, np, c->mc, out);
+    g_lc_launches += 1;
+}
+
 void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64* masks, int k0, int nk, u64* out) {
     dim3 grid(nk, (unsigned)(c->N / kT), nl);
     k_mask_acc<<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, c->log_n, k0, masks, c->mc, out);
@@ -470,32 +642,63 @@ void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64
 void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext) {
     const int beta = c->digits(level);
     const int rows = level + 1 + c->np;
-    dim3 grid((unsigned)(c->N / kT), B * beta);
-    k_modup<<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, rows, c->log_n, c->modup + (size_t)level * c->dnum,
-                                        c->mc, ext);
-    g_lc_launches += 1;
+    const int nl = level + 1;
+    const ModUpTab* tabs = c->modup + (size_t)level * c->dnum;
+    // digits 0..beta-2 have alpha primes; the last one has the remainder
+    const int last = nl - (beta - 1) * c->alpha;
+    auto launch = [&](int ns, int j0, int nj) {
+        dim3 grid((unsigned)(c->N / (2 * kT)), B * nj);
+        switch (ns) {
+            case 1: k_modup<1><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 2: k_modup<2><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 3: k_modup<3><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 4: k_modup<4><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 5: k_modup<5><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 6: k_modup<6><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 7: k_modup<7><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            case 8: k_modup<8><<<grid, kT, 0, c->stream>>>(coef, coef_stride, beta, j0, nj, rows, c->log_n, tabs, ext); break;
+            default: break;
+        }
+        g_lc_launches += 1;
+    };
+    if (last == c->alpha) {
+        launch(c->alpha, 0, beta);
+    } else {
+        if (beta > 1) launch(c->alpha, 0, beta - 1);
+        launch(last, beta - 1, 1);
+    }
 }
 
 void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* key, u64* v) {
     const int beta = c->digits(level);
     const int nl = level + 1, rows = nl + c->np;
-    dim3 grid(B, (unsigned)(c->N / kT), rows);
+    dim3 grid(B, (unsigned)(c->N / (4 * kT)), rows);
     k_inner<<<grid, kT, 0, c->stream>>>(ext, d, d_stride, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n,
-                                        key, c->mc, c->nq, v);
+                                        key, c->mc, v);
     g_lc_launches += 1;
 }
 
 void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv) {
     const int nl = level + 1, rows = nl + c->np;
-    dim3 grid((unsigned)(c->N / kT), B * 2);
-    k_moddown_bconv<<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, c->mc, conv);
+    dim3 grid((unsigned)(c->N / (2 * kT)), B * 2);
+    switch (c->np) {
+        case 1: k_moddown_bconv<1><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 2: k_moddown_bconv<2><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 3: k_moddown_bconv<3><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 4: k_moddown_bconv<4><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 5: k_moddown_bconv<5><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 6: k_moddown_bconv<6><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 7: k_moddown_bconv<7><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        case 8: k_moddown_bconv<8><<<grid, kT, 0, c->stream>>>(v, nl, rows, c->log_n, c->moddown, conv); break;
+        default: break;
+    }
     g_lc_launches += 1;
 }
 
 void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0, const u64* add1,
                         size_t add_stride, u64* w, size_t w_stride) {
     const int nl = level + 1, rows = nl + c->np;
-    const size_t total = (size_t)B * 2 * nl * c->N;
+    const size_t total = (size_t)B * 2 * nl * c->N / 2;
     k_moddown_combine<<<grid_for(total), kT, 0, c->stream>>>(v, conv, B, nl, rows, c->log_n, c->moddown, c->mc, add0,
                                                              add1, add_stride, w, w_stride);
     g_lc_launches += 1;

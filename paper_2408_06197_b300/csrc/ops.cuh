@@ -9,6 +9,8 @@ void op_addsub(lc_ctx* c, const u64* a, const u64* b, u64* out, int n_polys, int
 void op_tensor(lc_ctx* c, const u64* a, const u64* b, u64* out, int nl);
 // distances tensor phase: out[p] = sum_k (ct_i[k]-ct_j[k])^2 for pairs p in [p0, p0+np)
 void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p0, int np, u64* out);
+// same as op_sq_acc_pairs with client-block tiling (batched form): all pairs in [p0, p0+np)
+void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p0, int np, u64* out);
 // aggregate tensor phase: out[k] = sum_i ct_i[k] (x) M_i for chunks k in [k0, k0+nk)
 void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64* masks, int k0, int nk, u64* out);
 

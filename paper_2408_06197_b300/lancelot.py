@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "lc_memcpy_d2h": [vp, vp, vp, ctypes.c_size_t],
             "lc_launches": [vp],
             "lc_profile": [vp, ctypes.c_int, vp, vp, vp],
+            "lc_set_max_batch": [vp, u32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -226,6 +227,9 @@ class Context:
         if st != LC_OK:
             msg = lib().lc_last_error(self.h)
             raise LancelotError(f"{what}: {_ERRS.get(st, st)} {msg.decode() if msg else ''}")
+
+    def set_max_batch(self, max_items: int):
+        self._check(lib().lc_set_max_batch(self.h, int(max_items)), "lc_set_max_batch")
 
     def sync(self):
         self._check(lib().lc_sync(self.h), "lc_sync")

@@ -214,6 +214,17 @@ def test_toy_masked_aggregate_bit_exact(toy):
     assert np.linalg.norm(got - X[0, 0]) / np.linalg.norm(X[0, 0]) < 1e-3
 
 
+def test_batched_waves_match_single_wave(toy):
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    D1, _ = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale)
+    toy.g.set_max_batch(4)  # 6 pairs -> waves of 4 and 2
+    try:
+        D2, _ = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale)
+    finally:
+        toy.g.set_max_batch(0)
+    assert torch.equal(D1, D2)
+
+
 def test_host_buffers_match_device_buffers(toy):
     w, W, X, ocs, gcs = _toy_inputs(toy)
     host = toy.LC.torch_to_u64(gcs.contiguous())
