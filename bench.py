@@ -96,10 +96,14 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- workload (GPU)
-def build_workload(LC, g, w: S.Workload):
+SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7}
+
+
+def build_workload(LC, g, w: S.Workload, sched_name: str = "g2qp"):
     N = g.N
-    sched = [1] * (g.log_n - 1)
-    rots = LC.rotations_of_schedule(sched)
+    sched = SCHEDULES[sched_name]
+    # keys of the schedule plus the 14 log-step keys of the plain form
+    rots = sorted(set(LC.rotations_of_schedule(sched)) | set(LC.rotations_of_schedule([1] * (g.log_n - 1))))
     s = S.secret_key(w.seed, w.config, N)
     pa, pe = S.pk_rand(w.seed, w.config, g.q, N)
     pk = g.pk_gen(s, pa, pe)
@@ -252,9 +256,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mode", choices=["batched", "perop"], default="batched")
+    ap.add_argument("--schedule", choices=sorted(SCHEDULES), default="g2qp",
+                    help="rotate-and-sum hoisting: log = 14 single rotations; g2qp = 7 groups of 3 rotations "
+                         "with one ModDown per group (21 rotation keys)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-operation reference measurement")
     ap.add_argument("--micro", action="store_true", help="small isolated kernel case for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -278,14 +286,20 @@ def main():
     w = S.PLAIN
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=local, stream=stream)
-        evk, cts, masks, sched, s = build_workload(LC, g, w)
+        evk, cts, masks, sched, s = build_workload(LC, g, w, args.schedule)
         mode = LC.LC_MODE_BATCHED if args.mode == "batched" else LC.LC_MODE_PER_OP
+        dmode = mode | (LC.LC_HOIST_QP_SUM if args.schedule == "g2qp" else 0)
         out_d = g.empty(w.n_pairs, 2, g.L, g.N)
         out_a = g.empty(w.chunks, 2, g.L, g.N)
 
         def step():
-            g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=mode, out=out_d)
+            g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d)
             g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, mode=mode, out=out_a)
+
+        def plain_step():  # the plain per-operation form: one pair / chunk per launch sequence, 14 keys
+            g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=LC.LC_MODE_PER_OP, out=out_d)
+            g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, mode=LC.LC_MODE_PER_OP,
+                               out=out_a)
 
         def barrier():
             if world > 1:
@@ -336,7 +350,7 @@ def main():
             def e2e_step():
                 g.h2d(d_cts, h_cts)
                 g.h2d(d_masks, h_masks)
-                g.distances(evk, d_cts, w.n_clients, w.chunks, g.scale, mode=mode, out=out_d)
+                g.distances(evk, d_cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d)
                 g.masked_aggregate(evk, d_cts, w.n_clients, w.chunks, g.scale, d_masks, g.scale, mode=mode,
                                    out=out_a)
                 g.d2h(h_out_d, out_d)
@@ -358,6 +372,24 @@ def main():
                    "d2h_bytes_per_step": int(h_out_d.nbytes + h_out_a.nbytes)}
             del d_cts, d_masks
 
+    # the plain per-operation form on the same inputs (reference point of the batched form)
+    plain = None
+    if args.mode == "batched" and not args.no_plain:
+        with torch.cuda.stream(stream):
+            plain_step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                plain_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms = e0.elapsed_time(e1) / 2
+        plain = {"value": w.n_pairs / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                 "form": "per-operation launches (one pair / chunk at a time), log-step rotations, 14 keys",
+                 "batched_over_plain": (w.n_pairs / (ms_per_step / 1e3)) / (w.n_pairs / (pms / 1e3))}
+
     # roofline of the dominant kernel class
     hbm, peak_kind = peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -375,9 +407,10 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "n_clients": w.n_clients, "d": w.d,
                        "chunks": w.chunks, "pairs": w.n_pairs, "log_n": 15, "limbs_q": 15, "limbs_p": 4, "dnum": 4,
-                       "rotations": 14, "parallelism": f"replicas{world}",
+                       "rotation_schedule": args.schedule, "rotation_keys": len(evk.rotations),
+                       "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},
-            "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e,
+            "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e, "plain_form": plain,
             "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                  "definition": "one round = 45 pair distances + masked aggregate of 64 chunks, "
                                                "device time per step (rank 0)"}}

@@ -73,6 +73,12 @@ typedef struct {
 /* Evaluation modes of lc_distances / lc_masked_aggregate. */
 #define LC_MODE_PER_OP 0  /* one kernel sequence per HE operation, one pair / chunk at a time */
 #define LC_MODE_BATCHED 1 /* every pair / chunk in each launch, keys read once per launch */
+/* Hoisting variant flag (or-ed into the mode of lc_distances, flags of lc_rotate_sum): a
+ * hoisted group of rotations sums its inner products over Q_l U P and switches down once,
+ * instead of once per rotation (Section "Dynamic Hoisting": the rotations of one unfolded
+ * group are summed after the key switching).  Identical results for groups of size 1;
+ * a different rounding (not the same bits) for larger groups. */
+#define LC_HOIST_QP_SUM 2
 
 /* ---------------------------------------------------------------- parameters / context */
 
@@ -202,9 +208,10 @@ int lc_rotate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* ct, uint32_t level
 /* Rotate-and-sum in place over `count` ciphertexts [count][2][level+1][N] with a hoisting
  * schedule: groups[n_groups] with sum = log2(N/2); group g with stride s does
  * y <- y + sum_{t=1}^{2^g-1} Rot_{t s}(y) from one ModUp, then s <- s 2^g.  All groups 1 is the
- * plain log-step sum.  Afterwards every slot holds the sum of all slots. */
+ * plain log-step sum.  Afterwards every slot holds the sum of all slots.  flags: 0 or
+ * LC_HOIST_QP_SUM. */
 int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
-                  const uint32_t* groups);
+                  const uint32_t* groups, uint32_t flags);
 
 /* ---------------------------------------------------------------- the method */
 
@@ -212,7 +219,8 @@ int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count,
  * in lexicographic order: Dis = rotate_sum(rescale(relin(sum_k (ct_i[k] - ct_j[k])^2))).
  * cts: host or device [n][chunks][2][n_q][N] at level L and scale `scale`;
  * out: host or device [n(n-1)/2][2][n_q-1][N]; *out_scale = scale^2 / q_L.
- * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits).  groups: hoisting schedule as in
+ * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits), optionally | LC_HOIST_QP_SUM.
+ * groups: hoisting schedule as in
  * lc_rotate_sum (NULL = all ones).  evk must hold the relinearisation key and every
  * rotation key the schedule needs. */
 int lc_distances(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,

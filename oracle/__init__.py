@@ -62,9 +62,9 @@ def lib():
         L.or_rescale.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.or_keyswitch.argtypes = [vp, vp, ctypes.c_int, vp, vp]
         L.or_rotate_hoisted.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
-        L.or_rotate_sum.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]
+        L.or_rotate_sum.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
         L.or_distances.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
-                                   ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
+                                   ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
         L.or_masked_aggregate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         _lib = L
     return _lib
@@ -337,17 +337,20 @@ class Context:
         lib().or_rotate_hoisted(self.h, _p(ct), level, len(rots), r, _ptr_array(keys), _ptr_array(outs))
         return outs
 
-    def rotate_sum(self, ct, level, groups: Sequence[int], rot_keys: dict):
+    def rotate_sum(self, ct, level, groups: Sequence[int], rot_keys: dict, qp_sum: bool = False):
+        """Rotate-and-sum with hoisting groups; qp_sum sums each group's inner products in Q U P
+        and switches down once (the one-ModDown hoisting variant)."""
         x = np.ascontiguousarray(ct).copy()
         g = np.array(groups, dtype=np.int32)
         kr = np.array(list(rot_keys.keys()), dtype=np.int32)
         ks = [rot_keys[k] for k in rot_keys]
-        st = lib().or_rotate_sum(self.h, _p(x), level, len(g), _p(g), len(kr), _p(kr), _ptr_array(ks))
+        st = lib().or_rotate_sum(self.h, _p(x), level, len(g), _p(g), len(kr), _p(kr), _ptr_array(ks),
+                                 int(qp_sum))
         if st:
             raise KeyError("missing rotation key")
         return x
 
-    def distances(self, cts: np.ndarray, rlk, groups, rot_keys: dict, pairs=None) -> np.ndarray:
+    def distances(self, cts: np.ndarray, rlk, groups, rot_keys: dict, pairs=None, qp_sum: bool = False) -> np.ndarray:
         """cts [n][chunks][2][L+1][N] -> [n_pairs][2][L][N] (i<j lexicographic, or `pairs`)."""
         n, chunks = cts.shape[0], cts.shape[1]
         L = len(self.prm.q) - 1
@@ -364,7 +367,7 @@ class Context:
             npairs = nsel
         out = np.zeros((npairs, 2, L, self.N), dtype=np.uint64)
         st = lib().or_distances(self.h, _p(np.ascontiguousarray(cts)), n, chunks, _p(rlk), len(g), _p(g),
-                                len(kr), _p(kr), _ptr_array(ks), nsel, _p(pl), _p(out))
+                                len(kr), _p(kr), _ptr_array(ks), nsel, _p(pl), int(qp_sum), _p(out))
         if st:
             raise KeyError("missing rotation key")
         return out

@@ -259,16 +259,22 @@ static void moddown_coef(const OrCtx& c, const u64* u_coef, int level, u64* out_
 // c_coef: coefficient domain [l+1][N]; keys[r]: evaluation domain [dnum][2][nq+np][N];
 // out[r]: evaluation domain [2][l+1][N] (the switched pair before adding phi_g(c0)).
 static void keyswitch_hoisted(OrCtx& c, const u64* c_coef, int level, int n_rot, const u64* gs,
-                              const u64* const* keys, u64* const* outs) {
+                              const u64* const* keys, u64* const* outs, bool qp_sum = false) {
     const size_t N = c.N;
     const int nl = level + 1, rows = nl + c.np, beta = n_digits(c, level);
     std::vector<u64> ext((size_t)beta * rows * N);
     for (int j = 0; j < beta; j++) modup_digit(c, c_coef, level, j, ext.data() + (size_t)j * rows * N);
 #pragma omp atomic
     c.n_modup += 1;
+    // qp_sum: the inner products of all rotations are summed over Q_l U P and switched down
+    // once (written to outs[0]); otherwise each rotation gets its own ModDown.
+    std::vector<u64> u0((size_t)rows * N, 0), u1((size_t)rows * N, 0);
     for (int r = 0; r < n_rot; r++) {
         const u64 g = gs[r];
-        std::vector<u64> u0((size_t)rows * N, 0), u1((size_t)rows * N, 0);
+        if (!qp_sum) {
+            std::fill(u0.begin(), u0.end(), 0);
+            std::fill(u1.begin(), u1.end(), 0);
+        }
 #pragma omp parallel for schedule(static) if (!omp_in_parallel())
         for (int t = 0; t < rows; t++) {
             const int mi = qp_mod_index(c, level, t);
@@ -288,10 +294,16 @@ static void keyswitch_hoisted(OrCtx& c, const u64* c_coef, int level, int n_rot,
                 }
             }
         }
-        moddown_eval(c, u0.data(), level, outs[r]);
-        moddown_eval(c, u1.data(), level, outs[r] + (size_t)nl * N);
 #pragma omp atomic
         c.n_keyswitch += 1;
+        if (!qp_sum) {
+            moddown_eval(c, u0.data(), level, outs[r]);
+            moddown_eval(c, u1.data(), level, outs[r] + (size_t)nl * N);
+        }
+    }
+    if (qp_sum) {
+        moddown_eval(c, u0.data(), level, outs[0]);
+        moddown_eval(c, u1.data(), level, outs[0] + (size_t)nl * N);
     }
 }
 
@@ -372,12 +384,34 @@ static void rotate_hoisted(OrCtx& c, const u64* ct, int level, int n_rot, const 
     }
 }
 
+// Hoisted group with the inner products summed in Q_l U P (one ModDown for the whole group):
+// out = (sum_r phi_{g_r}(c0) + ModDown(sum_r u0_r), ModDown(sum_r u1_r)).
+static void rotate_group_qpsum(OrCtx& c, const u64* ct, int level, int n_rot, const u64* gs,
+                               const u64* const* keys, u64* out) {
+    const size_t N = c.N;
+    const int nl = level + 1;
+    const size_t P = (size_t)nl * N;
+    std::vector<u64> c0(ct, ct + P), c1(ct + P, ct + 2 * P);
+    to_coef(c, c0.data(), nl);
+    to_coef(c, c1.data(), nl);
+    std::vector<u64*> outs(n_rot, out);
+    keyswitch_hoisted(c, c1.data(), level, n_rot, gs, keys, outs.data(), true);
+    for (int r = 0; r < n_rot; r++) {
+        std::vector<u64> a0(P);
+        for (int i = 0; i < nl; i++) automorph_row(c, c0.data() + (size_t)i * N, a0.data() + (size_t)i * N, c.mod[i], gs[r]);
+        to_eval(c, a0.data(), nl);
+        for (int i = 0; i < nl; i++)
+            for (size_t x = 0; x < N; x++)
+                out[(size_t)i * N + x] = add_mod(out[(size_t)i * N + x], a0[(size_t)i * N + x], c.mod[i]);
+    }
+}
+
 static u64 galois_of_rotation(const OrCtx& c, long r) { return pow_mod(5, (u64)r, 2 * (u64)c.N); }
 
 // rotate-and-sum with a hoisting schedule: for each group of size g (stride s, starting at 1):
 // y <- y + sum_{t=1}^{2^g-1} Rot_{t s}(y), all from one ModUp of y; then s <- s 2^g.
 static int rotate_sum(OrCtx& c, u64* ct, int level, int n_groups, const int* groups,
-                      int n_keys, const int* key_rot, const u64* const* keys) {
+                      int n_keys, const int* key_rot, const u64* const* keys, bool qp_sum = false) {
     const size_t P = (size_t)(level + 1) * c.N;
     long stride = 1;
     for (int gi = 0; gi < n_groups; gi++) {
@@ -395,8 +429,14 @@ static int rotate_sum(OrCtx& c, u64* ct, int level, int n_groups, const int* gro
             if (!ks[t - 1]) return -1;
             op[t - 1] = outs[t - 1].data();
         }
-        rotate_hoisted(c, ct, level, cnt, gs.data(), ks.data(), op.data());
-        for (int t = 0; t < cnt; t++)
+        int nsum = cnt;
+        if (qp_sum) {
+            rotate_group_qpsum(c, ct, level, cnt, gs.data(), ks.data(), op[0]);
+            nsum = 1;
+        } else {
+            rotate_hoisted(c, ct, level, cnt, gs.data(), ks.data(), op.data());
+        }
+        for (int t = 0; t < nsum; t++)
             for (int p = 0; p < 2; p++)
                 for (int i = 0; i <= level; i++)
                     for (size_t x = 0; x < c.N; x++) {
@@ -705,8 +745,8 @@ void or_rotate_hoisted(OrCtx* c, const u64* ct, int level, int n_rot, const long
 }
 
 int or_rotate_sum(OrCtx* c, u64* ct, int level, int n_groups, const int* groups, int n_keys,
-                  const int* key_rot, const u64* const* keys) {
-    return rotate_sum(*c, ct, level, n_groups, groups, n_keys, key_rot, keys);
+                  const int* key_rot, const u64* const* keys, int qp_sum) {
+    return rotate_sum(*c, ct, level, n_groups, groups, n_keys, key_rot, keys, qp_sum != 0);
 }
 
 // Server distances (Algorithm 1, "Server Executes"): for each pair i<j (lexicographic):
@@ -717,7 +757,7 @@ int or_rotate_sum(OrCtx* c, u64* ct, int level, int n_groups, const int* groups,
 // to out in list order.
 int or_distances(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, int n_groups,
                  const int* groups, int n_keys, const int* key_rot, const u64* const* keys,
-                 int n_sel, const int* pair_list, u64* out) {
+                 int n_sel, const int* pair_list, int qp_sum, u64* out) {
     const size_t N = c->N;
     const int L = c->nq - 1, nl = L + 1;
     const size_t P = (size_t)nl * N, CT = 2 * P;
@@ -744,7 +784,7 @@ int or_distances(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, in
         std::vector<u64> r2(CT), rs(2 * (size_t)L * N);
         relin(*c, acc.data(), L, rlk, r2.data());
         rescale(*c, r2.data(), 2, L, rs.data());
-        int st = rotate_sum(*c, rs.data(), L - 1, n_groups, groups, n_keys, key_rot, keys);
+        int st = rotate_sum(*c, rs.data(), L - 1, n_groups, groups, n_keys, key_rot, keys, qp_sum != 0);
         if (st) status = st;
         std::memcpy(out + (size_t)k * 2 * L * N, rs.data(), rs.size() * sizeof(u64));
     }

@@ -333,13 +333,22 @@ static void ks_modup(lc_ctx* c, const u64* d, size_t d_stride, int B, int level,
 }
 
 // inner product with one key + ModDown; W[b] = (add0 + MD(v0), add1 + MD(v1))
-static void ks_apply(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const u64* key, const KsBufs& k,
-                     const u64* add0, const u64* add1, size_t add_stride, u64* w, size_t w_stride) {
+// inner product of the extended digits with one key: v [B][2][rows][N]
+static void ks_inner(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const u64* key, const KsBufs& k,
+                     u64* v) {
     const size_t N = c->N;
     const int nl = level + 1, rows = nl + c->np;
     const int beta = c->digits(level);
     PROF(c, PROF_INNER, (double)N * 8.0 * ((double)B * beta * rows + 2.0 * beta * rows + 2.0 * B * rows), (uint64_t)B,
-         op_inner(c, k.ext, d, d_stride, B, level, key, k.v));
+         op_inner(c, k.ext, d, d_stride, B, level, key, v));
+    c->n_keyswitch += (uint64_t)B;
+}
+
+// ModDown of v (overwritten): W[b] = (add0 + MD(v0), add1 + MD(v1))
+static void ks_moddown(lc_ctx* c, u64* v, int B, int level, const KsBufs& k, const u64* add0, size_t add0_stride,
+                       const u64* add1, size_t add1_stride, u64* w, size_t w_stride) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np;
     RowMap mp{};
     mp.n = 2 * c->np;
     for (int p = 0; p < 2; p++)
@@ -347,13 +356,19 @@ static void ks_apply(lc_ctx* c, const u64* d, size_t d_stride, int B, int level,
             mp.row[p * c->np + m] = (uint16_t)(p * rows + nl + m);
             mp.mod[p * c->np + m] = (uint8_t)(c->nq + m);
         }
-    ntt_inv_p(c, k.v, (size_t)2 * rows * N, B, mp);
+    ntt_inv_p(c, v, (size_t)2 * rows * N, B, mp);
     PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * (c->np + nl), (uint64_t)B,
-         op_moddown_bconv(c, k.v, B, level, k.conv));
+         op_moddown_bconv(c, v, B, level, k.conv));
     ntt_polys(c, k.conv, 2 * B, nl, true);
     PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * nl * (add0 ? 4.0 : 3.0), (uint64_t)B,
-         op_moddown_combine(c, k.v, k.conv, B, level, add0, add1, add_stride, w, w_stride));
-    c->n_keyswitch += (uint64_t)B;
+         op_moddown_combine(c, v, k.conv, B, level, add0, add0_stride, add1, add1_stride, w, w_stride));
+}
+
+// inner product with one key + ModDown; W[b] = (add0 + MD(v0), add1 + MD(v1))
+static void ks_apply(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const u64* key, const KsBufs& k,
+                     const u64* add0, const u64* add1, size_t add_stride, u64* w, size_t w_stride) {
+    ks_inner(c, d, d_stride, B, level, key, k, k.v);
+    ks_moddown(c, k.v, B, level, k, add0, add_stride, add1, add_stride, w, w_stride);
 }
 
 static const SwKey* find_key(const lc_evk* evk, int32_t id) {
@@ -392,15 +407,21 @@ void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u
          op_rescale_combine(c, ct, r, B, deg, level, out));
 }
 
-static size_t rotsum_words(lc_ctx* c, int B, int level, int max_group) {
+static size_t rotsum_words(lc_ctx* c, int B, int level, int max_group, bool qp_sum = false) {
     const size_t wsz = (size_t)B * 2 * (level + 1) * c->N;
+    if (qp_sum)  // sum of the group's inner products over Q_l U P + accumulated phi(c0)
+        return ks_words(c, B, level) + (size_t)B * c->N * (2 * (level + 1 + c->np) + (level + 1));
     return ks_words(c, B, level) + wsz * (((size_t)1 << max_group) - 1);
 }
 
+// Rotate-and-sum of B ciphertexts y [B][2][level+1][N] in place.  With qp_sum, each hoisted
+// group sums its rotations' inner products over Q_l U P and switches down once:
+// y <- (y0 + sum_t phi_t(y0) + MD(sum_t u0_t), y1 + MD(sum_t u1_t)), u_t = phi_t(v_t).
 static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level, int n_groups, const uint32_t* groups,
-                         u64* tmp) {
+                         u64* tmp, bool qp_sum = false) {
     const size_t N = c->N;
-    const size_t P = (size_t)(level + 1) * N;
+    const int nl = level + 1, rows = nl + c->np;
+    const size_t P = (size_t)nl * N;
     KsBufs kb = ks_layout(c, tmp, B, level);
     u64* wbase = tmp + ks_words(c, B, level);
     long stride = 1;
@@ -413,12 +434,27 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
             if (!keys[t - 1]) return fail(c, LC_EKEY, "rotation key " + std::to_string(t * stride) + " missing");
         }
         ks_modup(c, y + P, 2 * P, B, level, kb);
-        for (int t = 0; t < cnt; t++)
-            ks_apply(c, y + P, 2 * P, B, level, keys[t]->data, kb, y, nullptr, 2 * P, wbase + (size_t)t * B * 2 * P,
-                     2 * P);
-        for (int t = 0; t < cnt; t++)
-            PROF(c, PROF_AUTO, (double)B * 2 * P * 8.0 * 3.0, (uint64_t)B,
-                 op_gather(c, wbase + (size_t)t * B * 2 * P, y, B * 2, level + 1, keys[t]->galois, true));
+        if (qp_sum && cnt > 1) {
+            u64* usum = wbase;                                // [B][2][rows][N]
+            u64* c0acc = usum + (size_t)B * 2 * rows * N;     // [B][nl][N]
+            for (int t = 0; t < cnt; t++) {
+                ks_inner(c, y + P, 2 * P, B, level, keys[t]->data, kb, kb.v);
+                PROF(c, PROF_AUTO, (double)B * 2 * rows * N * 8.0 * 3.0, (uint64_t)B,
+                     op_gather_qp(c, kb.v, usum, B * 2, nl, keys[t]->galois, t > 0));
+            }
+            cudaMemcpy2DAsync(c0acc, P * 8, y, 2 * P * 8, P * 8, B, cudaMemcpyDeviceToDevice, c->stream);
+            PROF(c, PROF_AUTO, (double)B * P * 8.0 * 3.0 * cnt, (uint64_t)B, {
+                for (int t = 0; t < cnt; t++) op_gather_c0(c, y, c0acc, B, nl, keys[t]->galois);
+            });
+            ks_moddown(c, usum, B, level, kb, c0acc, P, y + P, 2 * P, y, 2 * P);
+        } else {
+            for (int t = 0; t < cnt; t++)
+                ks_apply(c, y + P, 2 * P, B, level, keys[t]->data, kb, y, nullptr, 2 * P,
+                         wbase + (size_t)t * B * 2 * P, 2 * P);
+            for (int t = 0; t < cnt; t++)
+                PROF(c, PROF_AUTO, (double)B * 2 * P * 8.0 * 3.0, (uint64_t)B,
+                     op_gather(c, wbase + (size_t)t * B * 2 * P, y, B * 2, level + 1, keys[t]->galois, true));
+        }
         stride <<= g;
     }
     return LC_OK;
@@ -923,15 +959,16 @@ int lc_rotate(lc_ctx* c, const lc_evk* evk, const uint64_t* ct, uint32_t level, 
 }
 
 int lc_rotate_sum(lc_ctx* c, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
-                  const uint32_t* groups) {
+                  const uint32_t* groups, uint32_t flags) {
     if (!c || !evk || !cts || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_rotate_sum: bad argument");
     if (count == 0 || n_groups == 0) return LC_OK;
     int maxg = 1;
     for (uint32_t i = 0; i < n_groups; i++) maxg = std::max(maxg, (int)(groups ? groups[i] : 1));
     if (maxg > 8) return fail(c, LC_EINVAL, "group too large");
-    u64* t = lc_scratch(c, rotsum_words(c, (int)count, (int)level, maxg) * 8);
+    const bool qp = (flags & LC_HOIST_QP_SUM) != 0;
+    u64* t = lc_scratch(c, rotsum_words(c, (int)count, (int)level, maxg, qp) * 8);
     if (!t) return fail(c, LC_ENOMEM, "scratch");
-    int st = do_rotate_sum(c, evk, cts, (int)count, (int)level, (int)n_groups, groups, t);
+    int st = do_rotate_sum(c, evk, cts, (int)count, (int)level, (int)n_groups, groups, t, qp);
     if (st) return st;
     return check_launch(c, "lc_rotate_sum");
 }
@@ -1002,6 +1039,8 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     const size_t N = c->N;
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
     const int npairs = (int)(n * (n - 1) / 2);
+    const bool qp = (mode & LC_HOIST_QP_SUM) != 0;
+    mode &= 1u;
     std::vector<uint32_t> sched;
     if (n_groups == 0) {
         for (int i = 1; i < c->log_n; i++) sched.push_back(1);
@@ -1033,7 +1072,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     }
     // per-item scratch: acc3 + ct2 + key-switch buffers + rotation outputs
     const size_t per_item = 3 * Pin + 2 * Pin + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
-                            std::max<size_t>(rotsum_words(c, 1, L - 1, maxg), 0);
+                            std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp), 0);
     const int B = mode == LC_MODE_PER_OP ? 1 : max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
     const int Bw = std::min(B, npairs);
     u64* t = lc_scratch(c, per_item * Bw * 8);
@@ -1054,7 +1093,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         if (st) return st;
         u64* y = dout + (size_t)p0 * 2 * Pout;
         do_rescale(c, ct2, b, 2, L, y, tmp);
-        st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp);
+        st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp, qp);
         if (st) return st;
     }
     if (out_host) LC_CUDA(c, cudaMemcpyAsync(out, dout, out_words * 8, cudaMemcpyDeviceToHost, c->stream));

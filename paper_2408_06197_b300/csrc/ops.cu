@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv(const u64* __restrict__ v,
 // W[b][k] = (v_k - conv_k) P^-1 + add_k over 2 coefficients per thread; grid-stride over B*2*nl*N/2
 __global__ void k_moddown_combine(const u64* __restrict__ v, const u64* __restrict__ conv, int B, int nl, int rows,
                                   int log_n, const ModDownTab* __restrict__ tab, const ModConst* __restrict__ mc,
-                                  const u64* __restrict__ add0, const u64* __restrict__ add1, size_t add_stride,
-                                  u64* __restrict__ w, size_t w_stride) {
+                                  const u64* add0, size_t add0_stride, const u64* add1, size_t add1_stride,
+                                  u64* w, size_t w_stride) {
     const size_t N = (size_t)1 << log_n;
     const size_t total = (size_t)B * 2 * nl * N / 2;
     for (size_t h = (size_t)blockIdx.x * blockDim.x + threadIdx.x; h < total; h += (size_t)gridDim.x * blockDim.x) {
@@ -453,7 +453,8 @@ __global__ void k_moddown_combine(const u64* __restrict__ v, const u64* __restri
         u64 o1 = mul_shoup(sub_mod(vv.y, cc.y, q), pinv, pinvsh, q);
         const u64* add = k == 0 ? add0 : add1;
         if (add) {
-            const ulonglong2 aa = ld2(add + b * add_stride + ((size_t)i << log_n) + x);
+            const ulonglong2 aa = *reinterpret_cast<const ulonglong2*>(add + b * (k == 0 ? add0_stride : add1_stride) +
+                                                                       ((size_t)i << log_n) + x);
             o0 = add_mod(o0, aa.x, q);
             o1 = add_mod(o1, aa.y, q);
         }
@@ -499,20 +500,38 @@ __global__ void k_rescale_combine(const u64* __restrict__ ct, const u64* __restr
 }
 
 // ---------------------------------------------------------------------------- automorphism
-__global__ void k_gather(const u64* __restrict__ w, u64* __restrict__ y, int n_polys, int nl, int log_n, uint64_t g,
-                         const ModConst* __restrict__ mc, int accumulate) {
+// y[p][r][idx] (+)= w[p][r][perm_g(idx)] over n_polys polys of `rows` rows; row r uses modulus
+// r (r < nlq, a q row) or nq + r - nlq (a special-prime row)
+__global__ void k_gather(const u64* __restrict__ w, u64* __restrict__ y, int n_polys, int rows, int nlq, int nq,
+                         int log_n, uint64_t g, const ModConst* __restrict__ mc, int accumulate) {
     const size_t N = (size_t)1 << log_n;
-    const size_t total = (size_t)n_polys * nl * N;
+    const size_t total = (size_t)n_polys * rows * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const unsigned x = (unsigned)(idx & (N - 1));
         const size_t row = idx >> log_n;
         const u64 val = w[(row << log_n) + auto_src(x, g, log_n)];
         if (accumulate) {
-            const int i = (int)(row % nl);
-            y[idx] = add_mod(y[idx], val, mc[i].q);
+            const int r = (int)(row % rows);
+            const u64 q = mc[r < nlq ? r : nq + (r - nlq)].q;
+            y[idx] = add_mod(y[idx], val, q);
         } else {
             y[idx] = val;
         }
+    }
+}
+
+// acc[b][i][idx] += src[b*src_stride + i*N + perm_g(idx)] for B items of nl q rows
+__global__ void k_gather_items(const u64* __restrict__ src, size_t src_stride, u64* __restrict__ acc, int B, int nl,
+                               int log_n, uint64_t g, const ModConst* __restrict__ mc) {
+    const size_t N = (size_t)1 << log_n;
+    const size_t total = (size_t)B * nl * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const unsigned x = (unsigned)(idx & (N - 1));
+        const size_t row = idx >> log_n;
+        const int i = (int)(row % nl);
+        const size_t b = row / nl;
+        const u64 val = src[b * src_stride + ((size_t)i << log_n) + auto_src(x, g, log_n)];
+        acc[idx] = add_mod(acc[idx], val, mc[i].q);
     }
 }
 
@@ -695,12 +714,12 @@ void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv) {
     g_lc_launches += 1;
 }
 
-void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0, const u64* add1,
-                        size_t add_stride, u64* w, size_t w_stride) {
+void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0,
+                        size_t add0_stride, const u64* add1, size_t add1_stride, u64* w, size_t w_stride) {
     const int nl = level + 1, rows = nl + c->np;
     const size_t total = (size_t)B * 2 * nl * c->N / 2;
     k_moddown_combine<<<grid_for(total), kT, 0, c->stream>>>(v, conv, B, nl, rows, c->log_n, c->moddown, c->mc, add0,
-                                                             add1, add_stride, w, w_stride);
+                                                             add0_stride, add1, add1_stride, w, w_stride);
     g_lc_launches += 1;
 }
 
@@ -719,7 +738,22 @@ void op_rescale_combine(lc_ctx* c, const u64* ct, const u64* r, int B, int deg, 
 
 void op_gather(lc_ctx* c, const u64* w, u64* y, int n_polys, int nl, uint64_t g, bool accumulate) {
     const size_t total = (size_t)n_polys * nl * c->N;
-    k_gather<<<grid_for(total), kT, 0, c->stream>>>(w, y, n_polys, nl, c->log_n, g, c->mc, accumulate ? 1 : 0);
+    k_gather<<<grid_for(total), kT, 0, c->stream>>>(w, y, n_polys, nl, nl, c->nq, c->log_n, g, c->mc,
+                                                    accumulate ? 1 : 0);
+    g_lc_launches += 1;
+}
+
+void op_gather_c0(lc_ctx* c, const u64* ct, u64* acc, int B, int nl, uint64_t g) {
+    const size_t total = (size_t)B * nl * c->N;
+    k_gather_items<<<grid_for(total), kT, 0, c->stream>>>(ct, (size_t)2 * nl * c->N, acc, B, nl, c->log_n, g, c->mc);
+    g_lc_launches += 1;
+}
+
+void op_gather_qp(lc_ctx* c, const u64* w, u64* y, int n_polys, int nl, uint64_t g, bool accumulate) {
+    const int rows = nl + c->np;
+    const size_t total = (size_t)n_polys * rows * c->N;
+    k_gather<<<grid_for(total), kT, 0, c->stream>>>(w, y, n_polys, rows, nl, c->nq, c->log_n, g, c->mc,
+                                                    accumulate ? 1 : 0);
     g_lc_launches += 1;
 }
 

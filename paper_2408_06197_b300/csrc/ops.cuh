@@ -20,14 +20,18 @@ void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64
 void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext);
 void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* key, u64* v);
 void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv);
-// W[b][k] = (v_k - conv_k) P^-1 + add_k  (add pointers may be null; add0 stride add_stride)
+// W[b][k] = (v_k - conv_k) P^-1 + add_k  (add pointers may be null; per-item strides in words)
 void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0,
-                        const u64* add1, size_t add_stride, u64* w, size_t w_stride);
+                        size_t add0_stride, const u64* add1, size_t add1_stride, u64* w, size_t w_stride);
+// acc[b] += phi_g(c0 of ciphertext b) for B ciphertexts [B][2][nl][N] (acc [B][nl][N])
+void op_gather_c0(lc_ctx* c, const u64* ct, u64* acc, int B, int nl, uint64_t g);
 // rescale: lastc [B*deg][N] coefficient-domain copy of the last limb; r scratch [B*deg][level][N]
 void op_rescale_prep(lc_ctx* c, const u64* lastc, int Bdeg, int level, u64* r);
 void op_rescale_combine(lc_ctx* c, const u64* ct, const u64* r, int B, int deg, int level, u64* out);
 // y[p][i][idx] (+)= w[p][i][perm_g(idx)] over n_polys polys of nl limbs
 void op_gather(lc_ctx* c, const u64* w, u64* y, int n_polys, int nl, uint64_t g, bool accumulate);
+// same over polys of Q_l U P rows (nl q rows then the special-prime rows)
+void op_gather_qp(lc_ctx* c, const u64* w, u64* y, int n_polys, int nl, uint64_t g, bool accumulate);
 // per-row permutation (any rows, all of length N)
 void op_permute_rows(lc_ctx* c, const u64* in, u64* out, int rows, uint64_t g);
 // signed integers -> residues for rows with modulus indices mods[0..nrows)

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "liblancelot.so")
 LC_OK = 0
 LC_MODE_PER_OP = 0
 LC_MODE_BATCHED = 1
+LC_HOIST_QP_SUM = 2
 _ERRS = {-1: "LC_EINVAL", -2: "LC_ELEVEL", -3: "LC_ESCALE", -4: "LC_ENOMEM", -5: "LC_ECUDA",
          -6: "LC_ETIMEOUT", -7: "LC_EBUSY", -8: "LC_EKEY"}
 
@@ -77,7 +78,7 @@ def lib() -> ctypes.CDLL:
             "lc_rescale": [vp, vp, u32, u32, u32, vp],
             "lc_rescale_noalloc": [vp, vp, u32, u32, u32, vp],
             "lc_rotate": [vp, vp, vp, u32, u32, vp, vp],
-            "lc_rotate_sum": [vp, vp, vp, u32, u32, u32, vp],
+            "lc_rotate_sum": [vp, vp, vp, u32, u32, u32, vp, u32],
             "lc_distances": [vp, vp, vp, u32, u32, ctypes.c_double, u32, u32, vp, vp, vp],
             "lc_masked_aggregate": [vp, vp, vp, u32, u32, ctypes.c_double, vp, ctypes.c_double, u32, vp, vp],
             "lc_memcpy_h2d": [vp, vp, vp, ctypes.c_size_t],
@@ -376,11 +377,13 @@ class Context:
         self._check(lib().lc_rotate(self.h, evk.h, _t_ptr(ct), level, len(r), _np_ptr(r), _t_ptr(out)), "lc_rotate")
         return out
 
-    def rotate_sum(self, evk: "EvalKeys", ct: torch.Tensor, level: int, groups: Sequence[int]) -> torch.Tensor:
+    def rotate_sum(self, evk: "EvalKeys", ct: torch.Tensor, level: int, groups: Sequence[int],
+                   qp_sum: bool = False) -> torch.Tensor:
         y = ct.clone().contiguous()
         g = np.array(list(groups), dtype=np.uint32)
         count = y.numel() // (2 * (level + 1) * self.N)
-        self._check(lib().lc_rotate_sum(self.h, evk.h, _t_ptr(y), count, level, len(g), _np_ptr(g)), "lc_rotate_sum")
+        self._check(lib().lc_rotate_sum(self.h, evk.h, _t_ptr(y), count, level, len(g), _np_ptr(g),
+                                        LC_HOIST_QP_SUM if qp_sum else 0), "lc_rotate_sum")
         return y
 
     # ------------------------------------------------------------------ the method

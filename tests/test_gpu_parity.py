@@ -160,6 +160,56 @@ def test_hoisted_rotations_and_rotate_sum_bit_exact(env):
         assert np.array_equal(env.g_coeff(yg, L), env.o_coeff(yo))
 
 
+def test_qp_sum_hoisting_bit_exact_toy(toy):
+    X = np.random.default_rng(6).normal(0, 0.01, (1, 1, toy.prm.slots))
+    ocs, gcs = toy.encrypt_both(X, [0], [0])
+    sched = [2] + [1] * (len(toy.sched) - 2)
+    need = O.rotations_of_schedule(sched)
+    yo = toy.o.rotate_sum(ocs[0, 0], toy.L, sched, {r: toy.ork[r] for r in need}, qp_sum=True)
+    yg = toy.g.rotate_sum(toy.gevk, gcs[0, 0].contiguous(), toy.L, sched, qp_sum=True)
+    assert np.array_equal(toy.g_coeff(yg, toy.L), toy.o_coeff(yo))
+
+
+@pytest.fixture(scope="module")
+def prod_g2():
+    """Production parameters with the rotation keys of the hoisting schedule [2]*7 (21 keys)."""
+    e = Env.__new__(Env)
+    from paper_2408_06197_b300 import lancelot as LC
+    e.LC, e.kind = LC, "prod"
+    e.prm = O.params_production()
+    e.o = O.Context(e.prm)
+    e.g = _ctx("prod")
+    e.sched = [2] * 7
+    e.keys = KeySet(e.prm, 4, S.CFG_PLAIN, O.rotations_of_schedule(e.sched))
+    e.opk, e.orlk, e.ork = e.keys.oracle_keys(e.o)
+    e.gpk, e.gevk = e.keys.gpu_keys(e.g)
+    e.seed, e.config = 4, S.CFG_PLAIN
+    e.N, e.L = e.prm.N, e.prm.L
+    return e
+
+
+def test_qp_sum_distances_production_bit_exact(prod_g2):
+    e = prod_g2
+    w = S.Workload("p3g2", S.CFG_PLAIN, 15, 3, e.prm.slots, 4, (2,), "flip5", 1, 0)
+    W = S.client_updates(w)
+    X = S.split_chunks(W, e.prm.slots)
+    ocs, gcs = e.encrypt_both(X, range(3), range(1))
+    mode = e.LC.LC_MODE_BATCHED | e.LC.LC_HOIST_QP_SUM
+    Dg, sc = e.g.distances(e.gevk, gcs, 3, 1, e.prm.scale, mode=mode, groups=e.sched)
+    Do = e.o.distances(ocs, e.orlk, e.sched, e.ork, qp_sum=True)
+    assert np.array_equal(e.g_coeff(Dg, e.L - 1), e.o_coeff(Do))
+    Dp, _ = e.g.distances(e.gevk, gcs, 3, 1, e.prm.scale, mode=e.LC.LC_MODE_PER_OP | e.LC.LC_HOIST_QP_SUM,
+                          groups=e.sched)
+    assert torch.equal(Dg, Dp)
+    k = 0
+    for i in range(3):
+        for j in range(i + 1, 3):
+            ref = np.sum((W[i] - W[j]) ** 2)
+            v = e.g.decrypt(e.keys.s, Dg[k].contiguous(), e.L - 1, sc)
+            assert np.abs(v - ref).max() / ref < 1e-5
+            k += 1
+
+
 # ------------------------------------------------------------------------------- the method (toy)
 
 def _toy_inputs(toy):

@@ -351,6 +351,24 @@ def test_hoisted_group_and_counters(toy):
         assert np.abs(ctx.decrypt(toy["s"], y, prm.L, prm.scale) - ref_slots).max() < 5e-4
 
 
+def test_qp_sum_hoisting_variant(toy):
+    """One-ModDown hoisting (inner products of a group summed in Q U P): identical bits for
+    groups of one rotation, correct decryption and one ModUp per group of three rotations."""
+    prm, ctx = toy["prm"], toy["ctx"]
+    z = np.random.default_rng(20).normal(0, 1, prm.slots)
+    ct, _ = _enc(toy, z)
+    a = ctx.rotate_sum(ct, prm.L, [1, 1], toy["rk"])
+    b = ctx.rotate_sum(ct, prm.L, [1, 1], toy["rk"], qp_sum=True)
+    assert np.array_equal(a, b)
+    ctx.reset_counters()
+    y = ctx.rotate_sum(ct, prm.L, [2], toy["rk"], qp_sum=True)
+    assert ctx.counters() == (3, 1)
+    ref_slots = z + np.roll(z, -1) + np.roll(z, -2) + np.roll(z, -3)
+    assert np.abs(ctx.decrypt(toy["s"], y, prm.L, prm.scale) - ref_slots).max() < 5e-4
+    per_rot = ctx.rotate_sum(ct, prm.L, [2], toy["rk"])
+    assert not np.array_equal(y, per_rot)  # a different rounding, not the same algorithm
+
+
 def toy_distance_tolerance(prm):
     """10x the predicted 1-sigma error of a toy distance (rotation key-switch noise dominates):
     per rotation the switched noise is about sqrt(N) * 3.2 * q0/sqrt(12) / P per coefficient,
