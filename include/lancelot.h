@@ -116,6 +116,18 @@ int lc_profile(lc_ctx* ctx, int start, double* ms, double* bytes, uint64_t* laun
  * results are identical for every setting. */
 int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
 
+/* CUDA-graph capture of a sequence of calls on the context's stream (no counterpart in the
+ * paper; replaces per-call kernel launches with one graph launch).  Between lc_graph_begin and
+ * lc_graph_end only device-pointer evaluation calls may be made; their scratch must already be
+ * sized (run each call once before capturing), otherwise they fail with LC_ENOMEM.  The graph
+ * replays the captured launches on the same buffers; the stream must not be the legacy default
+ * stream. */
+typedef struct lc_graph lc_graph;
+int lc_graph_begin(lc_ctx* ctx);
+int lc_graph_end(lc_ctx* ctx, lc_graph** out);
+int lc_graph_launch(lc_ctx* ctx, const lc_graph* graph);
+void lc_graph_free(lc_graph* graph);
+
 /* ---------------------------------------------------------------- keys (KGC side) */
 
 /* Public key pk = ([-a s + e]_Q, a) (Section "CKKS Scheme Description", Key generation).

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <vector>
@@ -33,10 +34,20 @@ int fail(lc_ctx* c, int code, const std::string& msg) {
     } while (0)
 
 int check_launch(lc_ctx* c, const char* what) {
+    if (c && !c->debug_err.empty()) {
+        std::string m = c->debug_err;
+        c->debug_err.clear();
+        cudaGetLastError();
+        return fail(c, LC_ECUDA, std::string(what) + ": " + m);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, LC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     return LC_OK;
 }
+
+// An entry point reports only errors of its own launches: clear a non-sticky error left by other
+// code on this thread (a sticky device fault stays and is reported by the launches).
+void clear_prior_error() { cudaGetLastError(); }
 
 RowMap rows_seq(int n, int mod0 = 0, int row0 = 0) {
     RowMap m{};
@@ -61,7 +72,7 @@ bool is_host_ptr(const void* p) {
 
 // ------------------------------------------------------------------------------------ profiling
 static void prof_begin(lc_ctx* c) {
-    if (!c->prof_on) return;
+    if (!c->prof_on || c->capturing) return;
     if (c->ev_used + 2 > c->ev_pool.size()) {
         for (int i = 0; i < 256; i++) {
             cudaEvent_t e;
@@ -72,23 +83,33 @@ static void prof_begin(lc_ctx* c) {
     cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
 }
 static void prof_end(lc_ctx* c, int cls, double bytes, uint64_t units) {
-    if (!c->prof_on) return;
+    if (!c->prof_on || c->capturing) return;
     cudaEvent_t a = c->ev_pool[c->ev_used], b = c->ev_pool[c->ev_used + 1];
     cudaEventRecord(b, c->stream);
     c->ev_used += 2;
     c->prof.push_back(ProfRec{cls, a, b, bytes, units});
 }
-#define PROF(c, cls, bytes, units, stmt) \
-    do {                                 \
-        prof_begin(c);                   \
-        stmt;                            \
-        prof_end(c, cls, bytes, units);  \
+static void debug_check(lc_ctx* c, const char* what, int line) {
+    if (!c->debug || !c->debug_err.empty()) return;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) c->debug_err = std::string(what) + " (capi.cu:" + std::to_string(line) + "): " + cudaGetErrorString(e);
+}
+#define PROF(c, cls, bytes, units, stmt)      \
+    do {                                      \
+        prof_begin(c);                        \
+        stmt;                                 \
+        prof_end(c, cls, bytes, units);       \
+        debug_check(c, #stmt, __LINE__);      \
     } while (0)
 
 // ------------------------------------------------------------------------------------ memory
 void* lc_dev_alloc(lc_ctx* c, size_t bytes) {
     if (bytes == 0) bytes = 256;
-    if (c->has_alloc) return c->alloc.alloc(bytes, c->alloc.user);
+    if (c->has_alloc) {
+        void* p = c->alloc.alloc(bytes, c->alloc.user);
+        cudaGetLastError();  // a non-sticky error raised inside the caller's allocator is not ours
+        return p;
+    }
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -99,12 +120,20 @@ void* lc_dev_alloc(lc_ctx* c, size_t bytes) {
 
 void lc_dev_free(lc_ctx* c, void* p) {
     if (!p) return;
-    if (c->has_alloc) c->alloc.free(p, c->alloc.user);
-    else cudaFree(p);
+    if (c->has_alloc) {
+        c->alloc.free(p, c->alloc.user);
+        cudaGetLastError();
+    } else {
+        cudaFree(p);
+    }
 }
 
 u64* lc_scratch(lc_ctx* c, size_t bytes) {
     if (bytes <= c->scratch_bytes) return static_cast<u64*>(c->scratch);
+    if (c->capturing) {
+        c->err = "scratch would grow during graph capture: run the same call once before capturing";
+        return nullptr;
+    }
     cudaStreamSynchronize(c->stream);
     lc_dev_free(c, c->scratch);
     c->scratch = nullptr;
@@ -118,6 +147,7 @@ u64* lc_scratch(lc_ctx* c, size_t bytes) {
 
 static u64* stage_buf(lc_ctx* c, size_t bytes) {
     if (bytes <= c->stage_bytes) return static_cast<u64*>(c->stage);
+    if (c->capturing) return nullptr;
     cudaStreamSynchronize(c->stream);
     lc_dev_free(c, c->stage);
     c->stage = lc_dev_alloc(c, bytes);
@@ -273,6 +303,7 @@ static void ntt_fwd_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowM
     const double limbs = (double)batch * m.n;
     PROF(c, PROF_NTT, limbs * c->N * 16.0, (uint64_t)limbs,
          ntt_forward(base, stride, batch, m, c->log_n, c->tables(), c->stream));
+    if (c->debug && c->debug_err.size()) c->debug_err += " [forward NTT batch " + std::to_string(batch) + " rows " + std::to_string(m.n) + "]";
 }
 static void ntt_inv_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowMap& m) {
     const double limbs = (double)batch * m.n;
@@ -409,8 +440,9 @@ void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u
 
 static size_t rotsum_words(lc_ctx* c, int B, int level, int max_group, bool qp_sum = false) {
     const size_t wsz = (size_t)B * 2 * (level + 1) * c->N;
-    if (qp_sum)  // sum of the group's inner products over Q_l U P + accumulated phi(c0)
-        return ks_words(c, B, level) + (size_t)B * c->N * (2 * (level + 1 + c->np) + (level + 1));
+    if (qp_sum)  // the group's inner products and their sum over Q_l U P + accumulated phi(c0)
+        return ks_words(c, B, level) +
+               (size_t)B * c->N * ((((size_t)1 << max_group) - 1 + 1) * 2 * (level + 1 + c->np) + (level + 1));
     return ks_words(c, B, level) + wsz * (((size_t)1 << max_group) - 1);
 }
 
@@ -435,13 +467,23 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
         }
         ks_modup(c, y + P, 2 * P, B, level, kb);
         if (qp_sum && cnt > 1) {
-            u64* usum = wbase;                                // [B][2][rows][N]
-            u64* c0acc = usum + (size_t)B * 2 * rows * N;     // [B][nl][N]
+            const size_t vsz = (size_t)B * 2 * rows * N;
+            u64* vs = wbase;                                  // [cnt][B][2][rows][N]
+            u64* usum = vs + (size_t)cnt * vsz;               // [B][2][rows][N]
+            u64* c0acc = usum + vsz;                          // [B][nl][N]
+            std::vector<const u64*> kp(cnt);
+            std::vector<uint64_t> gs(cnt);
             for (int t = 0; t < cnt; t++) {
-                ks_inner(c, y + P, 2 * P, B, level, keys[t]->data, kb, kb.v);
-                PROF(c, PROF_AUTO, (double)B * 2 * rows * N * 8.0 * 3.0, (uint64_t)B,
-                     op_gather_qp(c, kb.v, usum, B * 2, nl, keys[t]->galois, t > 0));
+                kp[t] = keys[t]->data;
+                gs[t] = keys[t]->galois;
             }
+            const int beta = c->digits(level);
+            PROF(c, PROF_INNER,
+                 (double)N * 8.0 * ((double)B * beta * rows + 2.0 * cnt * beta * rows + 2.0 * cnt * B * rows),
+                 (uint64_t)B, op_inner_multi(c, kb.ext, y + P, 2 * P, B, level, kp.data(), cnt, vs, vsz));
+            c->n_keyswitch += (uint64_t)B * cnt;
+            PROF(c, PROF_AUTO, (double)vsz * 8.0 * (cnt + 1), (uint64_t)B,
+                 op_gather_sum_qp(c, vs, vsz, usum, B * 2, nl, gs.data(), cnt));
             cudaMemcpy2DAsync(c0acc, P * 8, y, 2 * P * 8, P * 8, B, cudaMemcpyDeviceToDevice, c->stream);
             PROF(c, PROF_AUTO, (double)B * P * 8.0 * 3.0 * cnt, (uint64_t)B, {
                 for (int t = 0; t < cnt; t++) op_gather_c0(c, y, c0acc, B, nl, keys[t]->galois);
@@ -564,6 +606,7 @@ int lc_ctx_create(const lc_params* prm, int device, void* stream, const lc_alloc
     c->nq = (int)prm->n_q;
     c->np = (int)prm->n_p;
     c->dnum = (int)prm->dnum;
+    c->debug = getenv("LC_DEBUG") != nullptr;
     c->alpha = (c->nq + c->dnum - 1) / c->dnum;
     if (c->alpha > LC_MAX_SRC || c->nq + c->np > LC_MAX_DST) {
         delete c;
@@ -630,6 +673,7 @@ int lc_counters(lc_ctx* c, uint64_t* out, int reset) {
 }
 
 int lc_pk_gen(lc_ctx* c, const int8_t* s, const uint64_t* a, const int32_t* e, uint64_t* pk) {
+    clear_prior_error();
     if (!c || !s || !a || !e || !pk) return fail(c, LC_EINVAL, "lc_pk_gen: null argument");
     const size_t N = c->N;
     const int nq = c->nq;
@@ -672,6 +716,7 @@ void lc_evk_free(lc_evk* k) {
 }
 
 int lc_evk_add(lc_ctx* c, lc_evk* evk, const int8_t* s, int32_t rotation, const uint64_t* a, const int32_t* e) {
+    clear_prior_error();
     if (!c || !evk || !s || !a || !e) return fail(c, LC_EINVAL, "lc_evk_add: null argument");
     const int32_t id = rotation < 0 ? -1 : rotation;
     if (rotation == 0) return fail(c, LC_EINVAL, "rotation 0 has no key");
@@ -739,6 +784,7 @@ int lc_evk_add(lc_ctx* c, lc_evk* evk, const int8_t* s, int32_t rotation, const 
 }
 
 int lc_evk_export(lc_ctx* c, const lc_evk* evk, int32_t rotation, uint64_t* out) {
+    clear_prior_error();
     if (!c || !evk || !out) return fail(c, LC_EINVAL, "lc_evk_export: null argument");
     const SwKey* k = find_key(evk, rotation < 0 ? -1 : rotation);
     if (!k) return fail(c, LC_EKEY, "key missing");
@@ -786,6 +832,7 @@ int lc_decode(lc_ctx* c, const double* m, double scale, double* z_out) {
 
 int lc_encrypt(lc_ctx* c, const uint64_t* pk, const int64_t* m, const int8_t* r, const int32_t* e0, const int32_t* e1,
                uint32_t count, uint64_t* out) {
+    clear_prior_error();
     if (!c || !pk || !m || !r || !e0 || !e1 || !out) return fail(c, LC_EINVAL, "lc_encrypt: null argument");
     if (count == 0) return LC_OK;
     const size_t N = c->N;
@@ -831,6 +878,7 @@ int lc_encrypt(lc_ctx* c, const uint64_t* pk, const int64_t* m, const int8_t* r,
 }
 
 int lc_decrypt(lc_ctx* c, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out) {
+    clear_prior_error();
     if (!c || !s || !ct || !res_out || deg < 2 || deg > 3) return fail(c, LC_EINVAL, "lc_decrypt: bad argument");
     if ((int)level >= c->nq) return fail(c, LC_ELEVEL, "level out of range");
     const size_t N = c->N;
@@ -885,36 +933,42 @@ int lc_crt_to_double(lc_ctx* c, const uint64_t* res, uint32_t level, double* m_o
 }
 
 int lc_to_coeff(lc_ctx* c, uint64_t* data, uint32_t n_polys, uint32_t level) {
+    clear_prior_error();
     if (!c || !data || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_to_coeff: bad argument");
     ntt_polys(c, data, (int)n_polys, (int)level + 1, false);
     return check_launch(c, "lc_to_coeff");
 }
 
 int lc_to_eval(lc_ctx* c, uint64_t* data, uint32_t n_polys, uint32_t level) {
+    clear_prior_error();
     if (!c || !data || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_to_eval: bad argument");
     ntt_polys(c, data, (int)n_polys, (int)level + 1, true);
     return check_launch(c, "lc_to_eval");
 }
 
 int lc_add(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out) {
+    clear_prior_error();
     if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_add: bad argument");
     op_addsub(c, a, b, out, (int)n_polys, (int)level + 1, false);
     return check_launch(c, "lc_add");
 }
 
 int lc_sub(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_polys, uint32_t level, uint64_t* out) {
+    clear_prior_error();
     if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_sub: bad argument");
     op_addsub(c, a, b, out, (int)n_polys, (int)level + 1, true);
     return check_launch(c, "lc_sub");
 }
 
 int lc_tensor(lc_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t level, uint64_t* out) {
+    clear_prior_error();
     if (!c || !a || !b || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_tensor: bad argument");
     op_tensor(c, a, b, out, (int)level + 1);
     return check_launch(c, "lc_tensor");
 }
 
 int lc_relin(lc_ctx* c, const lc_evk* evk, const uint64_t* ct3, uint32_t count, uint32_t level, uint64_t* out) {
+    clear_prior_error();
     if (!c || !evk || !ct3 || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_relin: bad argument");
     if (count == 0) return LC_OK;
     u64* t = lc_scratch(c, ks_words(c, (int)count, (int)level) * 8);
@@ -925,6 +979,7 @@ int lc_relin(lc_ctx* c, const lc_evk* evk, const uint64_t* ct3, uint32_t count, 
 }
 
 int lc_rescale(lc_ctx* c, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out) {
+    clear_prior_error();
     if (!c || !ct || !out || level < 1 || (int)level >= c->nq || deg < 1 || deg > 3)
         return fail(c, LC_EINVAL, "lc_rescale: bad argument");
     if (count == 0) return LC_OK;
@@ -936,6 +991,7 @@ int lc_rescale(lc_ctx* c, const uint64_t* ct, uint32_t count, uint32_t deg, uint
 
 int lc_rotate(lc_ctx* c, const lc_evk* evk, const uint64_t* ct, uint32_t level, uint32_t n_rot, const int32_t* rots,
               uint64_t* out) {
+    clear_prior_error();
     if (!c || !evk || !ct || !out || (n_rot && !rots) || (int)level >= c->nq)
         return fail(c, LC_EINVAL, "lc_rotate: bad argument");
     if (n_rot == 0) return LC_OK;
@@ -960,6 +1016,7 @@ int lc_rotate(lc_ctx* c, const lc_evk* evk, const uint64_t* ct, uint32_t level, 
 
 int lc_rotate_sum(lc_ctx* c, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
                   const uint32_t* groups, uint32_t flags) {
+    clear_prior_error();
     if (!c || !evk || !cts || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_rotate_sum: bad argument");
     if (count == 0 || n_groups == 0) return LC_OK;
     int maxg = 1;
@@ -1026,6 +1083,60 @@ static int max_batch_for(lc_ctx* c, size_t words_per_item, size_t budget_words) 
     return (int)b;
 }
 
+struct lc_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;
+};
+
+int lc_graph_begin(lc_ctx* c) {
+    if (!c) return LC_EINVAL;
+    if (!c->stream) return fail(c, LC_EINVAL, "graph capture needs a context stream other than the legacy default");
+    if (c->capturing) return fail(c, LC_EBUSY, "already capturing");
+    LC_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->capture_launches0 = g_lc_launches.load();
+    return LC_OK;
+}
+
+int lc_graph_end(lc_ctx* c, lc_graph** out) {
+    if (!c || !out) return LC_EINVAL;
+    if (!c->capturing) return fail(c, LC_EINVAL, "not capturing");
+    c->capturing = false;
+    lc_graph* g = new (std::nothrow) lc_graph();
+    if (!g) return LC_ENOMEM;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g->graph);
+    if (e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return fail(c, LC_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        cudaGetLastError();
+        return fail(c, LC_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    g->launches = g_lc_launches.load() - c->capture_launches0;
+    *out = g;
+    return LC_OK;
+}
+
+int lc_graph_launch(lc_ctx* c, const lc_graph* g) {
+    if (!c || !g) return LC_EINVAL;
+    LC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
+    g_lc_launches += g->launches;
+    return LC_OK;
+}
+
+void lc_graph_free(lc_graph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
 int lc_set_max_batch(lc_ctx* c, uint32_t max_items) {
     if (!c) return LC_EINVAL;
     c->max_batch = max_items;
@@ -1034,6 +1145,7 @@ int lc_set_max_batch(lc_ctx* c, uint32_t max_items) {
 
 int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                  uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale) {
+    clear_prior_error();
     if (!c || !evk || !cts || !out || n < 2 || chunks == 0) return fail(c, LC_EINVAL, "lc_distances: bad argument");
     const int L = c->nq - 1;
     const size_t N = c->N;
@@ -1077,6 +1189,10 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     const int Bw = std::min(B, npairs);
     u64* t = lc_scratch(c, per_item * Bw * 8);
     if (!t) return fail(c, LC_ENOMEM, "scratch");
+    {
+        const int st0 = check_launch(c, "lc_distances (set-up)");
+        if (st0) return st0;
+    }
     u64* acc3 = t;
     u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
     u64* tmp = ct2 + (size_t)Bw * 2 * Pin;
@@ -1089,11 +1205,17 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
                  mode == LC_MODE_PER_OP ? op_sq_acc_pairs(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3)
                                         : op_sq_acc_tiled(c, din, (int)n, (int)chunks, c->nq, p0, b, acc3));
         }
-        int st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+        int st = check_launch(c, "lc_distances (tensor accumulate)");
+        if (st) return st;
+        st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+        if (!st) st = check_launch(c, "lc_distances (relinearisation)");
         if (st) return st;
         u64* y = dout + (size_t)p0 * 2 * Pout;
         do_rescale(c, ct2, b, 2, L, y, tmp);
+        st = check_launch(c, "lc_distances (rescale)");
+        if (st) return st;
         st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp, qp);
+        if (!st) st = check_launch(c, "lc_distances (rotate-and-sum)");
         if (st) return st;
     }
     if (out_host) LC_CUDA(c, cudaMemcpyAsync(out, dout, out_words * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1104,6 +1226,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
 
 int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                         const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out, double* out_scale) {
+    clear_prior_error();
     if (!c || !evk || !cts || !masks || !out || n == 0 || chunks == 0)
         return fail(c, LC_EINVAL, "lc_masked_aggregate: bad argument");
     const int L = c->nq - 1;

@@ -96,6 +96,10 @@ struct lc_ctx {
     std::string err;
     uint64_t n_keyswitch = 0, n_modup = 0;
     uint32_t max_batch = 0;  // 0 = limited only by the scratch budget
+    bool debug = false;      // LC_DEBUG set: check every launch, remember the first failure
+    std::string debug_err;
+    bool capturing = false;  // inside lc_graph_begin / lc_graph_end
+    uint64_t capture_launches0 = 0;
     // profiling
     bool prof_on = false;
     std::vector<ProfRec> prof;

@@ -16,6 +16,13 @@ struct ModList {
     u64 val[LC_MAX_ROWS];
 };
 
+struct KeyPtrs {
+    const u64* p[8];
+};
+struct Galois {
+    uint64_t g[8];
+};
+
 ModList make_list(const int* mods, int n, const u64* vals = nullptr) {
     ModList l{};
     l.n = n;
@@ -394,6 +401,64 @@ __global__ void __launch_bounds__(kT) k_inner(const u64* __restrict__ ext, const
     st2(vc + 2, reduce128c(c[2], q, r64, r64sh, osh), reduce128c(c[3], q, r64, r64sh, osh));
 }
 
+// key inner product for T keys of one hoisted group, reading the extended digits once:
+// v_t = sum_j E_j * key_t,j for t < T.  keys: device array of T key pointers.
+// grid: x = batch item, y = tile of 2*kT coefficients, z = row t of Q_l U P
+template <int T>
+__global__ void __launch_bounds__(kT) k_inner_multi(const u64* __restrict__ ext, const u64* __restrict__ d,
+                                                    size_t d_stride, int beta, int nl, int rows, int alpha, int nq,
+                                                    int nqp, int log_n, KeyPtrs keys, const ModConst* __restrict__ mc,
+                                                    u64* __restrict__ v, size_t v_key_stride) {
+    const int b = blockIdx.x, t = blockIdx.z;
+    const size_t N = (size_t)1 << log_n;
+    const size_t x = ((size_t)blockIdx.y * kT + threadIdx.x) * 2;
+    const int kt = t < nl ? t : nq + (t - nl);
+    const ModConst& mcr = mc[kt];
+    const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
+    u128v a[T][2], c[T][2];
+#pragma unroll
+    for (int k = 0; k < T; k++) a[k][0] = a[k][1] = c[k][0] = c[k][1] = u128v{0, 0};
+    for (int j = 0; j < beta; j++) {
+        const u64* src = (t < nl && t / alpha == j) ? d + (size_t)b * d_stride + ((size_t)t << log_n)
+                                                     : ext + (((size_t)b * beta + j) * rows + t) * N;
+        const ulonglong2 e = ld2(src + x);
+        const size_t ko = (((size_t)j * 2 + 0) * nqp + kt) * N + x;
+        const size_t ka = (size_t)nqp * N;
+#pragma unroll
+        for (int k = 0; k < T; k++) {
+            const ulonglong2 kb2 = ld2(keys.p[k] + ko), ka2 = ld2(keys.p[k] + ko + ka);
+            mac128(a[k][0], e.x, kb2.x);
+            mac128(a[k][1], e.y, kb2.y);
+            mac128(c[k][0], e.x, ka2.x);
+            mac128(c[k][1], e.y, ka2.y);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < T; k++) {
+        u64* vb = v + k * v_key_stride + (size_t)b * 2 * rows * N + (size_t)t * N + x;
+        st2(vb, reduce128c(a[k][0], q, r64, r64sh, osh), reduce128c(a[k][1], q, r64, r64sh, osh));
+        st2(vb + (size_t)rows * N, reduce128c(c[k][0], q, r64, r64sh, osh), reduce128c(c[k][1], q, r64, r64sh, osh));
+    }
+}
+
+// usum[p][r][idx] = sum_t src_t[p][r][perm_{g_t}(idx)] over polys of `rows` rows (Q_l U P)
+template <int T>
+__global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64* __restrict__ usum, int n_polys,
+                             int rows, int nlq, int nq, int log_n, Galois gs, const ModConst* __restrict__ mc) {
+    const size_t N = (size_t)1 << log_n;
+    const size_t total = (size_t)n_polys * rows * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const unsigned x = (unsigned)(idx & (N - 1));
+        const size_t row = idx >> log_n;
+        const int r = (int)(row % rows);
+        const u64 q = mc[r < nlq ? r : nq + (r - nlq)].q;
+        u64 acc = 0;
+#pragma unroll
+        for (int k = 0; k < T; k++) acc = add_mod(acc, src[k * src_stride + (row << log_n) + auto_src(x, gs.g[k], log_n)], q);
+        usum[idx] = acc;
+    }
+}
+
 // ModDown conversion of the K special-prime rows.  grid: x = tile of 2*kT coefficients, y = b*2 + k
 template <int K>
 __global__ void __launch_bounds__(kT) k_moddown_bconv(const u64* __restrict__ v, int nl, int rows, int log_n,
@@ -694,6 +759,53 @@ void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, i
     dim3 grid(B, (unsigned)(c->N / (4 * kT)), rows);
     k_inner<<<grid, kT, 0, c->stream>>>(ext, d, d_stride, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n,
                                         key, c->mc, v);
+    g_lc_launches += 1;
+}
+
+void op_inner_multi(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* const* keys,
+                    int T, u64* v, size_t v_key_stride) {
+    const int beta = c->digits(level);
+    const int nl = level + 1, rows = nl + c->np;
+    dim3 grid(B, (unsigned)(c->N / (2 * kT)), rows);
+    KeyPtrs kp{};
+    for (int k = 0; k < T && k < 8; k++) kp.p[k] = keys[k];
+#define LC_IM(TT)                                                                                                   \
+    k_inner_multi<TT><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, \
+                                                  c->log_n, kp, c->mc, v, v_key_stride)
+    switch (T) {
+        case 1: LC_IM(1); break;
+        case 2: LC_IM(2); break;
+        case 3: LC_IM(3); break;
+        case 4: LC_IM(4); break;
+        case 5: LC_IM(5); break;
+        case 6: LC_IM(6); break;
+        case 7: LC_IM(7); break;
+        default: break;
+    }
+#undef LC_IM
+    g_lc_launches += 1;
+}
+
+void op_gather_sum_qp(lc_ctx* c, const u64* src, size_t src_stride, u64* usum, int n_polys, int nl,
+                      const uint64_t* gs, int T) {
+    const int rows = nl + c->np;
+    const size_t total = (size_t)n_polys * rows * c->N;
+    Galois g{};
+    for (int k = 0; k < T && k < 8; k++) g.g[k] = gs[k];
+#define LC_GS(TT)                                                                                                \
+    k_gather_sum<TT><<<grid_for(total), kT, 0, c->stream>>>(src, src_stride, usum, n_polys, rows, nl, c->nq, c->log_n, \
+                                                            g, c->mc)
+    switch (T) {
+        case 1: LC_GS(1); break;
+        case 2: LC_GS(2); break;
+        case 3: LC_GS(3); break;
+        case 4: LC_GS(4); break;
+        case 5: LC_GS(5); break;
+        case 6: LC_GS(6); break;
+        case 7: LC_GS(7); break;
+        default: break;
+    }
+#undef LC_GS
     g_lc_launches += 1;
 }
 

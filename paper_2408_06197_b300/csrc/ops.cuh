@@ -19,6 +19,13 @@ void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64
 //  scratch layout is owned by the caller (see capi.cu)
 void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext);
 void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* key, u64* v);
+// inner products of one hoisted group's T keys (T <= 7), reading the extended digits once:
+// v + t * v_key_stride receives [B][2][rows][N] for key t
+void op_inner_multi(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* const* keys,
+                    int T, u64* v, size_t v_key_stride);
+// usum = sum_t phi_{g_t}(src_t) over n_polys polys of Q_l U P rows (src_t = src + t * src_stride)
+void op_gather_sum_qp(lc_ctx* c, const u64* src, size_t src_stride, u64* usum, int n_polys, int nl,
+                      const uint64_t* gs, int T);
 void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv);
 // W[b][k] = (v_k - conv_k) P^-1 + add_k  (add pointers may be null; per-item strides in words)
 void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0,

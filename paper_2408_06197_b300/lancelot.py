@@ -8,8 +8,11 @@ is missing or cannot be loaded the call raises -- there is no CPU path.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import sys
+import weakref
 from typing import Dict, Iterable, List, Optional, Sequence
 
 import numpy as np
@@ -37,6 +40,23 @@ class LancelotError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("log_n", u32), ("n_q", u32), ("n_p", u32), ("dnum", u32), ("q", vp), ("p", vp)]
 
+
+_LIVE = weakref.WeakSet()  # contexts, key sets and graphs still holding library handles
+
+
+def _close_all():
+    """Releases every live handle at interpreter exit, while torch and CUDA are still up."""
+    objs = list(_LIVE)
+    for kind in (Graph, EvalKeys, Context):
+        for o in objs:
+            if isinstance(o, kind):
+                try:
+                    o.close()
+                except Exception:
+                    pass
+
+
+atexit.register(_close_all)
 
 _ALLOC_FN = ctypes.CFUNCTYPE(vp, ctypes.c_size_t, vp)
 _FREE_FN = ctypes.CFUNCTYPE(None, vp, vp)
@@ -86,11 +106,15 @@ def lib() -> ctypes.CDLL:
             "lc_launches": [vp],
             "lc_profile": [vp, ctypes.c_int, vp, vp, vp],
             "lc_set_max_batch": [vp, u32],
+            "lc_graph_begin": [vp],
+            "lc_graph_end": [vp, vp],
+            "lc_graph_launch": [vp, vp],
+            "lc_graph_free": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name in ("lc_ctx_destroy", "lc_evk_free") else ctypes.c_int
+            f.restype = None if name in ("lc_ctx_destroy", "lc_evk_free", "lc_graph_free") else ctypes.c_int
         L.lc_last_error.argtypes = [vp]
         L.lc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -105,6 +129,31 @@ def _np_ptr(a: np.ndarray):
 def _t_ptr(t: torch.Tensor):
     assert t.is_contiguous()
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(buf, words: int, what: str, host_ok: bool = False):
+    """The library trusts raw pointers; check every caller buffer here so that a wrong shape raises
+    instead of letting a kernel read or write past its end."""
+    if isinstance(buf, torch.Tensor):
+        if buf.dtype not in (torch.int64, torch.uint64) or not buf.is_cuda or not buf.is_contiguous():
+            raise LancelotError(f"{what}: needs a contiguous 64-bit CUDA tensor")
+        n = buf.numel()
+    elif isinstance(buf, np.ndarray) and host_ok:
+        if buf.dtype != np.uint64 or not buf.flags.c_contiguous:
+            raise LancelotError(f"{what}: needs a C-contiguous uint64 array")
+        n = buf.size
+    else:
+        raise LancelotError(f"{what}: unsupported buffer type {type(buf).__name__}")
+    if n != words:
+        raise LancelotError(f"{what}: has {n} words, expected {words}")
+    return buf
+
+
+def _whole(buf, unit: int, what: str) -> int:
+    n = buf.numel()
+    if unit <= 0 or n == 0 or n % unit:
+        raise LancelotError(f"{what}: {n} words is not a whole number of {unit}-word items")
+    return n // unit
 
 
 def launches() -> int:
@@ -177,13 +226,20 @@ class Context:
             dev, st = device, self.stream
 
             def _a(nbytes, user):
+                if sys.is_finalizing():
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
                 except RuntimeError:
                     return None
 
             def _f(ptr, user):
-                torch.cuda.caching_allocator_delete(ptr)
+                if sys.is_finalizing():
+                    return  # the process is exiting: leave the memory to the driver
+                try:
+                    torch.cuda.caching_allocator_delete(ptr)
+                except Exception:
+                    pass
 
             self._afn, self._ffn = _ALLOC_FN(_a), _FREE_FN(_f)
             self._alloc = _Allocator(self._afn, self._ffn, None)
@@ -194,6 +250,8 @@ class Context:
         if st != LC_OK:
             raise LancelotError(f"lc_ctx_create: {_ERRS.get(st, st)}")
         self.h = h
+        self._deps = weakref.WeakSet()  # key sets and graphs made on this context
+        _LIVE.add(self)
 
     @classmethod
     def production(cls, **kw):
@@ -207,6 +265,11 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            for dep in list(getattr(self, "_deps", ())):
+                try:
+                    dep.close()
+                except Exception:
+                    pass
             lib().lc_ctx_destroy(self.h)
             self.h = None
 
@@ -228,6 +291,18 @@ class Context:
         if st != LC_OK:
             msg = lib().lc_last_error(self.h)
             raise LancelotError(f"{what}: {_ERRS.get(st, st)} {msg.decode() if msg else ''}")
+
+    def capture(self, fn) -> "Graph":
+        """Captures the library calls made by fn() on this context's stream into a CUDA graph.
+        Run fn() once before capturing so that every scratch buffer is already sized."""
+        self._check(lib().lc_graph_begin(self.h), "lc_graph_begin")
+        try:
+            fn()
+        finally:
+            h = ctypes.c_void_p()
+            st = lib().lc_graph_end(self.h, ctypes.byref(h))
+        self._check(st, "lc_graph_end")
+        return Graph(self, h)
 
     def set_max_batch(self, max_items: int):
         self._check(lib().lc_set_max_batch(self.h, int(max_items)), "lc_set_max_batch")
@@ -255,10 +330,16 @@ class Context:
 
     def h2d(self, dst: torch.Tensor, src: np.ndarray):
         """Stream-ordered host->device copy through the C ABI (src pinned or pageable)."""
+        if not (isinstance(dst, torch.Tensor) and dst.is_cuda and dst.is_contiguous()
+                and dst.numel() * dst.element_size() == src.nbytes):
+            raise LancelotError("h2d: destination must be a contiguous CUDA tensor of the same byte size")
         self._check(lib().lc_memcpy_h2d(self.h, _t_ptr(dst), ctypes.c_void_p(src.ctypes.data), src.nbytes),
                     "lc_memcpy_h2d")
 
     def d2h(self, dst: np.ndarray, src: torch.Tensor):
+        if not (isinstance(src, torch.Tensor) and src.is_cuda and src.is_contiguous()
+                and src.numel() * src.element_size() == dst.nbytes and dst.flags.c_contiguous):
+            raise LancelotError("d2h: source must be a contiguous CUDA tensor of the same byte size")
         self._check(lib().lc_memcpy_d2h(self.h, ctypes.c_void_p(dst.ctypes.data), _t_ptr(src), dst.nbytes),
                     "lc_memcpy_d2h")
 
@@ -296,8 +377,13 @@ class Context:
                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
         m = np.ascontiguousarray(m, np.int64).reshape(-1, self.N)
         count = m.shape[0]
+        for name, arr in (("r", r), ("e0", e0), ("e1", e1)):
+            if np.asarray(arr).size != count * self.N:
+                raise LancelotError(f"encrypt: {name} must hold {count} x N values")
+        _need(pk, 2 * self.nq * self.N, "encrypt: pk")
         if out is None:
             out = self.empty(count, 2, self.nq, self.N)
+        _need(out, count * 2 * self.nq * self.N, "encrypt: out")
         self._check(lib().lc_encrypt(self.h, _t_ptr(pk), _np_ptr(m), _np_ptr(np.ascontiguousarray(r, np.int8)),
                                      _np_ptr(np.ascontiguousarray(e0, np.int32)),
                                      _np_ptr(np.ascontiguousarray(e1, np.int32)), count, _t_ptr(out)), "lc_encrypt")
@@ -306,6 +392,7 @@ class Context:
     def decrypt_residues(self, s: np.ndarray, ct: torch.Tensor, level: int) -> np.ndarray:
         ct = ct.contiguous()
         deg = ct.shape[-3] if ct.dim() >= 3 else 2
+        _need(ct, deg * (level + 1) * self.N, "decrypt: ct")
         res = np.zeros((level + 1, self.N), dtype=np.uint64)
         self._check(lib().lc_decrypt(self.h, _np_ptr(np.ascontiguousarray(s, np.int8)), _t_ptr(ct), deg, level,
                                      _np_ptr(res)), "lc_decrypt")
@@ -320,42 +407,48 @@ class Context:
     # ------------------------------------------------------------------ interchange
     def to_coeff(self, data: torch.Tensor, level: int) -> torch.Tensor:
         x = data.clone().contiguous()
-        n_polys = x.numel() // ((level + 1) * self.N)
+        n_polys = _whole(x, (level + 1) * self.N, "to_coeff")
         self._check(lib().lc_to_coeff(self.h, _t_ptr(x), n_polys, level), "lc_to_coeff")
         return x
 
     def to_eval(self, data: torch.Tensor, level: int) -> torch.Tensor:
         x = data.clone().contiguous()
-        n_polys = x.numel() // ((level + 1) * self.N)
+        n_polys = _whole(x, (level + 1) * self.N, "to_eval")
         self._check(lib().lc_to_eval(self.h, _t_ptr(x), n_polys, level), "lc_to_eval")
         return x
 
     # ------------------------------------------------------------------ primitives
     def add(self, a, b, level):
+        _whole(a, (level + 1) * self.N, "add")
+        _need(b, a.numel(), "add: b")
         out = torch.empty_like(a)
         self._check(lib().lc_add(self.h, _t_ptr(a), _t_ptr(b), a.numel() // ((level + 1) * self.N), level,
                                  _t_ptr(out)), "lc_add")
         return out
 
     def sub(self, a, b, level):
+        _whole(a, (level + 1) * self.N, "sub")
+        _need(b, a.numel(), "sub: b")
         out = torch.empty_like(a)
         self._check(lib().lc_sub(self.h, _t_ptr(a), _t_ptr(b), a.numel() // ((level + 1) * self.N), level,
                                  _t_ptr(out)), "lc_sub")
         return out
 
     def tensor(self, a, b, level):
+        _need(a, 2 * (level + 1) * self.N, "tensor: a")
+        _need(b, 2 * (level + 1) * self.N, "tensor: b")
         out = self.empty(3, level + 1, self.N)
         self._check(lib().lc_tensor(self.h, _t_ptr(a), _t_ptr(b), level, _t_ptr(out)), "lc_tensor")
         return out
 
     def relin(self, evk: "EvalKeys", ct3: torch.Tensor, level: int) -> torch.Tensor:
-        count = ct3.numel() // (3 * (level + 1) * self.N)
+        count = _whole(ct3, 3 * (level + 1) * self.N, "relin")
         out = self.empty(count, 2, level + 1, self.N)
         self._check(lib().lc_relin(self.h, evk.h, _t_ptr(ct3), count, level, _t_ptr(out)), "lc_relin")
         return out
 
     def rescale(self, ct: torch.Tensor, level: int, deg: int = 2) -> torch.Tensor:
-        count = ct.numel() // (deg * (level + 1) * self.N)
+        count = _whole(ct, deg * (level + 1) * self.N, "rescale")
         out = self.empty(count, deg, level, self.N)
         self._check(lib().lc_rescale(self.h, _t_ptr(ct), count, deg, level, _t_ptr(out)), "lc_rescale")
         return out
@@ -364,15 +457,17 @@ class Context:
                         out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Rescale through the entry point that allocates nothing (fixed 16 MiB library scratch);
         pass a preallocated `out` when no allocation may happen at all."""
-        count = ct.numel() // (deg * (level + 1) * self.N)
+        count = _whole(ct, deg * (level + 1) * self.N, "rescale_noalloc")
         if out is None:
             out = self.empty(count, deg, level, self.N)
+        _need(out, count * deg * level * self.N, "rescale_noalloc: out")
         self._check(lib().lc_rescale_noalloc(self.h, _t_ptr(ct), count, deg, level, _t_ptr(out)),
                     "lc_rescale_noalloc")
         return out
 
     def rotate(self, evk: "EvalKeys", ct: torch.Tensor, level: int, rots: Sequence[int]) -> torch.Tensor:
         r = np.array(list(rots), dtype=np.int32)
+        _need(ct, 2 * (level + 1) * self.N, "rotate: ct")
         out = self.empty(len(r), 2, level + 1, self.N)
         self._check(lib().lc_rotate(self.h, evk.h, _t_ptr(ct), level, len(r), _np_ptr(r), _t_ptr(out)), "lc_rotate")
         return out
@@ -381,7 +476,7 @@ class Context:
                    qp_sum: bool = False) -> torch.Tensor:
         y = ct.clone().contiguous()
         g = np.array(list(groups), dtype=np.uint32)
-        count = y.numel() // (2 * (level + 1) * self.N)
+        count = _whole(y, 2 * (level + 1) * self.N, "rotate_sum")
         self._check(lib().lc_rotate_sum(self.h, evk.h, _t_ptr(y), count, level, len(g), _np_ptr(g),
                                         LC_HOIST_QP_SUM if qp_sum else 0), "lc_rotate_sum")
         return y
@@ -395,6 +490,8 @@ class Context:
         if out is None:
             out = (np.empty((npairs, 2, self.L, self.N), dtype=np.uint64) if host
                    else self.empty(npairs, 2, self.L, self.N))
+        _need(cts, n * chunks * 2 * self.nq * self.N, "distances: cts", host_ok=True)
+        _need(out, npairs * 2 * self.L * self.N, "distances: out", host_ok=True)
         g = np.array(list(groups) if groups else [], dtype=np.uint32)
         sc = ctypes.c_double()
         pin = _np_ptr(cts) if host else _t_ptr(cts)
@@ -409,6 +506,9 @@ class Context:
         if out is None:
             out = (np.empty((chunks, 2, self.L, self.N), dtype=np.uint64) if host
                    else self.empty(chunks, 2, self.L, self.N))
+        _need(cts, n * chunks * 2 * self.nq * self.N, "masked_aggregate: cts", host_ok=True)
+        _need(masks, n * 2 * self.nq * self.N, "masked_aggregate: masks", host_ok=True)
+        _need(out, chunks * 2 * self.L * self.N, "masked_aggregate: out", host_ok=True)
         sc = ctypes.c_double()
         pin = _np_ptr(cts) if host else _t_ptr(cts)
         pm = _np_ptr(masks) if isinstance(masks, np.ndarray) else _t_ptr(masks)
@@ -416,6 +516,29 @@ class Context:
         self._check(lib().lc_masked_aggregate(self.h, evk.h, pin, n, chunks, scale, pm, mask_scale, mode, pout,
                                               ctypes.byref(sc)), "lc_masked_aggregate")
         return out, sc.value
+
+
+class Graph:
+    """A captured sequence of library calls; launch() replays it on the context's stream."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        ctx._deps.add(self)
+        _LIVE.add(self)
+
+    def launch(self):
+        self.ctx._check(lib().lc_graph_launch(self.ctx.h, self.h), "lc_graph_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lc_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class EvalKeys:
@@ -426,6 +549,8 @@ class EvalKeys:
         h = ctypes.c_void_p()
         ctx._check(lib().lc_evk_create(ctx.h, ctypes.byref(h)), "lc_evk_create")
         self.h = h
+        ctx._deps.add(self)
+        _LIVE.add(self)
         self.rotations: List[int] = []
 
     def add(self, s: np.ndarray, rotation: Optional[int], a: np.ndarray, e: np.ndarray):
@@ -445,7 +570,8 @@ class EvalKeys:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().lc_evk_free(self.h)
+            if getattr(self.ctx, "h", None):  # the keys are freed through their (live) context
+                lib().lc_evk_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -275,6 +275,37 @@ def test_batched_waves_match_single_wave(toy):
     assert torch.equal(D1, D2)
 
 
+def test_graph_replay_matches_direct_calls(toy):
+    """A captured distances + aggregate step replays on new inputs written into the same buffers."""
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    from paper_2408_06197_b300 import lancelot as LC
+    with torch.cuda.stream(stream):
+        g = LC.Context.toy(stream=stream)
+        pk, evk = toy.keys.gpu_keys(g)
+        cts = gcs.clone()
+        out_d = g.empty(w.n_pairs, 2, toy.L, toy.N)  # level L-1 ciphertexts have L limbs
+        out_a = g.empty(w.chunks, 2, toy.L, toy.N)
+        masks = gcs[:, 0].contiguous()
+
+    def step():
+        g.distances(evk, cts, w.n_clients, w.chunks, toy.prm.scale, out=out_d)
+        g.masked_aggregate(evk, cts, w.n_clients, w.chunks, toy.prm.scale, masks, toy.prm.scale, out=out_a)
+
+    with torch.cuda.stream(stream):
+        step()
+        graph = g.capture(step)
+        cts.copy_(torch.flip(gcs, dims=[0]))  # new inputs in the captured buffer
+        graph.launch()
+        g.sync()
+        got_d, got_a = out_d.clone(), out_a.clone()
+        step()
+        g.sync()
+    assert torch.equal(got_d, out_d) and torch.equal(got_a, out_a)
+    graph.close()
+
+
 def test_host_buffers_match_device_buffers(toy):
     w, W, X, ocs, gcs = _toy_inputs(toy)
     host = toy.LC.torch_to_u64(gcs.contiguous())
