@@ -247,6 +247,31 @@ int lc_masked_aggregate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uin
                         double scale, const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out,
                         double* out_scale);
 
+/* ---------------------------------------------------------------- multi-job (uneven) batches */
+
+/* One aggregation round of one tenant: its evaluation keys, its clients' ciphertexts and its
+ * outputs (all device pointers, layouts as in lc_distances / lc_masked_aggregate). */
+typedef struct {
+    const lc_evk* evk;     /* the tenant's relinearisation + rotation keys */
+    const uint64_t* cts;   /* [n][chunks][2][n_q][N] at level L */
+    uint32_t n;            /* clients (>= 2 for distances) */
+    uint32_t chunks;       /* ciphertexts per client (ragged across jobs) */
+    const uint64_t* masks; /* [n][2][n_q][N], for lc_batch_aggregate */
+    uint64_t* out_dist;    /* [n(n-1)/2][2][n_q-1][N], for lc_batch_distances */
+    uint64_t* out_agg;     /* [chunks][2][n_q-1][N], for lc_batch_aggregate */
+} lc_job;
+
+/* Encrypted distances of several rounds at once (Algorithm 1 "Server Executes" per job): all
+ * (job, pair) items -- different client counts, model sizes and key sets -- run together in
+ * batched waves; each job's results are bit-identical to lc_distances on that job alone with
+ * the same schedule.  flags: 0 or LC_HOIST_QP_SUM; groups as in lc_rotate_sum (sizes <= 3).
+ * Synchronises the stream between waves (descriptors are rewritten). */
+int lc_batch_distances(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t n_groups,
+                       const uint32_t* groups);
+/* Masked aggregates of several rounds at once (Algorithm 1 "ServerUpdate" per job); each job's
+ * results are bit-identical to lc_masked_aggregate on that job alone. */
+int lc_batch_aggregate(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1224,6 +1224,247 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     return check_launch(c, "lc_distances");
 }
 
+// ------------------------------------------------------------------------------------ multi-job batches
+}  // extern "C"
+namespace {
+// host-built descriptors of one wave, uploaded into the tail of the scratch arena
+struct WaveBlob {
+    std::vector<unsigned char> bytes;
+    template <typename T>
+    size_t put(const T* p, size_t n) {
+        size_t off = (bytes.size() + 255) & ~(size_t)255;
+        bytes.resize(off + n * sizeof(T));
+        std::memcpy(bytes.data() + off, p, n * sizeof(T));
+        return off;
+    }
+};
+bool job_ok(lc_ctx* c, const lc_job& j, bool agg) {
+    if (!j.evk || !j.cts || j.chunks == 0) return false;
+    if (agg) return j.n >= 1 && j.masks && j.out_agg;
+    return j.n >= 2 && j.out_dist;
+}
+}  // namespace
+
+// relinearisation + rescale + (optional) rotate-and-sum of `b` items whose degree-2 sums are in
+// acc3, with per-item key pointer arrays already on the device; results in y [b][2][L][N]
+static int items_tail(lc_ctx* c, u64* acc3, u64* ct2, u64* y, u64* tmp, int b, const u64* const* relin_keys,
+                      const std::vector<const u64* const*>& group_keys, const std::vector<int>& group_t,
+                      const std::vector<std::vector<uint64_t>>& group_gal, bool rotate, bool qp) {
+    const int L = c->nq - 1;
+    const size_t N = c->N;
+    const size_t Pin = (size_t)c->nq * N;
+    {
+        KsBufs kb = ks_layout(c, tmp, b, L);
+        ks_modup(c, acc3 + 2 * Pin, 3 * Pin, b, L, kb);
+        PROF(c, PROF_INNER, (double)N * 8.0 * b * (c->digits(L) + 2.0) * (L + 1 + c->np), (uint64_t)b,
+             op_inner_items(c, kb.ext, acc3 + 2 * Pin, 3 * Pin, b, L, relin_keys, 1, kb.v, 0));
+        c->n_keyswitch += (uint64_t)b;
+        ks_moddown(c, kb.v, b, L, kb, acc3, 3 * Pin, acc3 + Pin, 3 * Pin, ct2, 2 * Pin);
+    }
+    do_rescale(c, ct2, b, 2, L, y, tmp);
+    if (!rotate) return check_launch(c, "batch (relinearise + rescale)");
+    const int level = L - 1, nl = L, rows = nl + c->np;
+    const size_t P = (size_t)nl * N;
+    KsBufs kb = ks_layout(c, tmp, b, level);
+    u64* wbase = tmp + ks_words(c, b, level);
+    for (size_t gi = 0; gi < group_keys.size(); gi++) {
+        const int cnt = group_t[gi];
+        ks_modup(c, y + P, 2 * P, b, level, kb);
+        if (qp && cnt > 1) {
+            const size_t vsz = (size_t)b * 2 * rows * N;
+            u64* vs = wbase;
+            u64* usum = vs + (size_t)cnt * vsz;
+            u64* c0acc = usum + vsz;
+            PROF(c, PROF_INNER, (double)N * 8.0 * b * (c->digits(level) + 2.0 * cnt) * rows, (uint64_t)b,
+                 op_inner_items(c, kb.ext, y + P, 2 * P, b, level, group_keys[gi], cnt, vs, vsz));
+            c->n_keyswitch += (uint64_t)b * cnt;
+            PROF(c, PROF_AUTO, (double)vsz * 8.0 * (cnt + 1), (uint64_t)b,
+                 op_gather_sum_qp(c, vs, vsz, usum, b * 2, nl, group_gal[gi].data(), cnt));
+            cudaMemcpy2DAsync(c0acc, P * 8, y, 2 * P * 8, P * 8, b, cudaMemcpyDeviceToDevice, c->stream);
+            PROF(c, PROF_AUTO, (double)b * P * 8.0 * 3.0 * cnt, (uint64_t)b, {
+                for (int t = 0; t < cnt; t++) op_gather_c0(c, y, c0acc, b, nl, group_gal[gi][t]);
+            });
+            ks_moddown(c, usum, b, level, kb, c0acc, P, y + P, 2 * P, y, 2 * P);
+        } else {
+            // one ModDown per rotation: W_t = (y0 + MD(v_t0), MD(v_t1)) in the pre-permuted frame
+            const size_t vsz = (size_t)b * 2 * rows * N;
+            u64* vs = wbase;                             // [cnt][b][2][rows][N]
+            u64* ws = vs + (size_t)cnt * vsz;            // [cnt][b][2][nl][N]
+            PROF(c, PROF_INNER, (double)N * 8.0 * b * (c->digits(level) + 2.0 * cnt) * rows, (uint64_t)b,
+                 op_inner_items(c, kb.ext, y + P, 2 * P, b, level, group_keys[gi], cnt, vs, vsz));
+            c->n_keyswitch += (uint64_t)b * cnt;
+            for (int t = 0; t < cnt; t++)
+                ks_moddown(c, vs + (size_t)t * vsz, b, level, kb, y, 2 * P, nullptr, 0, ws + (size_t)t * b * 2 * P,
+                           2 * P);
+            for (int t = 0; t < cnt; t++)
+                PROF(c, PROF_AUTO, (double)b * 2 * P * 8.0 * 3.0, (uint64_t)b,
+                     op_gather(c, ws + (size_t)t * b * 2 * P, y, b * 2, nl, group_gal[gi][t], true));
+        }
+    }
+    return check_launch(c, "batch (rotate-and-sum)");
+}
+
+extern "C" {
+
+int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t n_groups,
+                       const uint32_t* groups) {
+    if (!c || (!jobs && n_jobs)) return fail(c, LC_EINVAL, "lc_batch_distances: bad argument");
+    clear_prior_error();
+    const int L = c->nq - 1;
+    const size_t N = c->N;
+    const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    const bool qp = (flags & LC_HOIST_QP_SUM) != 0;
+    std::vector<uint32_t> sched;
+    if (n_groups == 0) {
+        for (int i = 1; i < c->log_n; i++) sched.push_back(1);
+    } else {
+        uint32_t sum = 0;
+        for (uint32_t i = 0; i < n_groups; i++) {
+            sched.push_back(groups ? groups[i] : 1);
+            sum += sched.back();
+        }
+        if ((int)sum != c->log_n - 1) return fail(c, LC_EINVAL, "schedule must sum to log2(slots)");
+    }
+    int maxg = 1;
+    for (uint32_t g : sched) maxg = std::max(maxg, (int)g);
+    if (maxg > 3) return fail(c, LC_EINVAL, "batched groups are limited to size 3");
+    // every item: (job, pair)
+    struct It { int job, i, j, p; };
+    std::vector<It> items;
+    for (uint32_t jb = 0; jb < n_jobs; jb++) {
+        const lc_job& J = jobs[jb];
+        if (!job_ok(c, J, false)) return fail(c, LC_EINVAL, "lc_batch_distances: job " + std::to_string(jb) + " invalid");
+        if (!find_key(J.evk, -1)) return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": relinearisation key missing");
+        long stride = 1;
+        for (uint32_t g : sched) {
+            for (int t = 1; t < (1 << g); t++)
+                if (!find_key(J.evk, (int32_t)(t * stride)))
+                    return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": rotation key " + std::to_string(t * stride) +
+                                                " missing");
+            stride <<= g;
+        }
+        int p = 0;
+        for (uint32_t i = 0; i < J.n; i++)
+            for (uint32_t j = i + 1; j < J.n; j++) items.push_back(It{(int)jb, (int)i, (int)j, p++});
+    }
+    if (items.empty()) return LC_OK;
+    const size_t rot_words = std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp),
+                                              ks_words(c, 1, L - 1) + ((((size_t)1 << maxg) - 1) * 2 * (L + c->np) +
+                                                                       (((size_t)1 << maxg) - 1) * 2 * L) * N);
+    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
+                            rot_words + 64;
+    const int Bw = std::min<int>(max_batch_for(c, per_item, (size_t)8 << 30 >> 3), (int)items.size());
+    const size_t desc_words = (size_t)Bw * 64 + 4096;
+    u64* t = lc_scratch(c, (per_item * Bw + desc_words) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* acc3 = t;
+    u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
+    u64* y = ct2 + (size_t)Bw * 2 * Pin;
+    u64* tmp = y + (size_t)Bw * 2 * Pout;
+    unsigned char* desc = reinterpret_cast<unsigned char*>(t + per_item * Bw);
+    for (size_t w0 = 0; w0 < items.size(); w0 += Bw) {
+        const int b = (int)std::min<size_t>(Bw, items.size() - w0);
+        WaveBlob blob;
+        std::vector<PairItem> pi(b);
+        std::vector<const u64*> rk(b);
+        std::vector<u64*> dst(b);
+        std::vector<std::vector<const u64*>> gk(sched.size(), std::vector<const u64*>());
+        std::vector<std::vector<uint64_t>> gal(sched.size());
+        std::vector<int> gt(sched.size());
+        for (int k = 0; k < b; k++) {
+            const It& it = items[w0 + k];
+            const lc_job& J = jobs[it.job];
+            const size_t cs = (size_t)J.chunks * 2 * Pin;
+            pi[k] = PairItem{J.cts + (size_t)it.i * cs, J.cts + (size_t)it.j * cs, (int)J.chunks, k};
+            rk[k] = find_key(J.evk, -1)->data;
+            dst[k] = J.out_dist + (size_t)it.p * 2 * Pout;
+            long stride = 1;
+            for (size_t gi = 0; gi < sched.size(); gi++) {
+                const int cnt = (1 << sched[gi]) - 1;
+                gt[gi] = cnt;
+                for (int tt = 1; tt <= cnt; tt++) {
+                    const SwKey* key = find_key(J.evk, (int32_t)(tt * stride));
+                    gk[gi].push_back(key->data);
+                    if (k == 0) gal[gi].push_back(key->galois);
+                }
+                stride <<= sched[gi];
+            }
+        }
+        const size_t o_items = blob.put(pi.data(), pi.size());
+        const size_t o_rk = blob.put(rk.data(), rk.size());
+        const size_t o_dst = blob.put(dst.data(), dst.size());
+        std::vector<size_t> o_gk(sched.size());
+        for (size_t gi = 0; gi < sched.size(); gi++) o_gk[gi] = blob.put(gk[gi].data(), gk[gi].size());
+        if (blob.bytes.size() > desc_words * 8) return fail(c, LC_EINVAL, "descriptor area too small");
+        LC_CUDA(c, cudaMemcpyAsync(desc, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice, c->stream));
+        PROF(c, PROF_TENSOR, 0.0, (uint64_t)b,
+             op_sq_acc_items(c, reinterpret_cast<const PairItem*>(desc + o_items), b, c->nq, acc3));
+        std::vector<const u64* const*> gkd(sched.size());
+        for (size_t gi = 0; gi < sched.size(); gi++) gkd[gi] = reinterpret_cast<const u64* const*>(desc + o_gk[gi]);
+        int st = items_tail(c, acc3, ct2, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), gkd, gt, gal,
+                            true, qp);
+        if (st) return st;
+        op_copy_items(c, y, 2 * Pout, reinterpret_cast<u64* const*>(desc + o_dst), b);
+        // the next wave rewrites the descriptors: wait until this wave has consumed them
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return check_launch(c, "lc_batch_distances");
+}
+
+int lc_batch_aggregate(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs) {
+    if (!c || (!jobs && n_jobs)) return fail(c, LC_EINVAL, "lc_batch_aggregate: bad argument");
+    clear_prior_error();
+    const int L = c->nq - 1;
+    const size_t N = c->N;
+    const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    struct It { int job, k; };
+    std::vector<It> items;
+    for (uint32_t jb = 0; jb < n_jobs; jb++) {
+        const lc_job& J = jobs[jb];
+        if (!job_ok(c, J, true)) return fail(c, LC_EINVAL, "lc_batch_aggregate: job " + std::to_string(jb) + " invalid");
+        if (!find_key(J.evk, -1)) return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": relinearisation key missing");
+        for (uint32_t k = 0; k < J.chunks; k++) items.push_back(It{(int)jb, (int)k});
+    }
+    if (items.empty()) return LC_OK;
+    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) + 64;
+    const int Bw = std::min<int>(max_batch_for(c, per_item, (size_t)8 << 30 >> 3), (int)items.size());
+    const size_t desc_words = (size_t)Bw * 16 + 1024;
+    u64* t = lc_scratch(c, (per_item * Bw + desc_words) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* acc3 = t;
+    u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
+    u64* y = ct2 + (size_t)Bw * 2 * Pin;
+    u64* tmp = y + (size_t)Bw * 2 * Pout;
+    unsigned char* desc = reinterpret_cast<unsigned char*>(t + per_item * Bw);
+    for (size_t w0 = 0; w0 < items.size(); w0 += Bw) {
+        const int b = (int)std::min<size_t>(Bw, items.size() - w0);
+        WaveBlob blob;
+        std::vector<AggItem> ai(b);
+        std::vector<const u64*> rk(b);
+        std::vector<u64*> dst(b);
+        for (int k = 0; k < b; k++) {
+            const It& it = items[w0 + k];
+            const lc_job& J = jobs[it.job];
+            ai[k] = AggItem{J.cts, J.masks, (int)J.n, (int)J.chunks, it.k, k};
+            rk[k] = find_key(J.evk, -1)->data;
+            dst[k] = J.out_agg + (size_t)it.k * 2 * Pout;
+        }
+        const size_t o_items = blob.put(ai.data(), ai.size());
+        const size_t o_rk = blob.put(rk.data(), rk.size());
+        const size_t o_dst = blob.put(dst.data(), dst.size());
+        if (blob.bytes.size() > desc_words * 8) return fail(c, LC_EINVAL, "descriptor area too small");
+        LC_CUDA(c, cudaMemcpyAsync(desc, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice, c->stream));
+        PROF(c, PROF_TENSOR, 0.0, (uint64_t)b,
+             op_mask_acc_items(c, reinterpret_cast<const AggItem*>(desc + o_items), b, c->nq, acc3));
+        int st = items_tail(c, acc3, ct2, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), {}, {}, {},
+                            false, false);
+        if (st) return st;
+        op_copy_items(c, y, 2 * Pout, reinterpret_cast<u64* const*>(desc + o_dst), b);
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return check_launch(c, "lc_batch_aggregate");
+}
+
 int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                         const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out, double* out_scale) {
     clear_prior_error();

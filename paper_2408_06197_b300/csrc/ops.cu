@@ -1,6 +1,7 @@
 // Evaluation kernels of the Lancelot server path (elementwise RNS arithmetic, tensor and
 // lazy accumulation, base conversion, key inner product, rescale, automorphism).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include "ops.cuh"
 
 std::atomic<uint64_t> g_lc_launches{0};
@@ -306,6 +307,81 @@ __global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, in
     o[2 * P] = reduce128(s11, m);
 }
 
+// ---------------------------------------------------------------------------- multi-job items
+// tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
+__global__ void __launch_bounds__(kT) k_sq_acc_items(const PairItem* __restrict__ items, int nl, int log_n,
+                                                     const ModConst* __restrict__ mc, u64* __restrict__ out) {
+    const PairItem it = items[blockIdx.x];
+    const int limb = blockIdx.z;
+    const size_t N = (size_t)1 << log_n;
+    const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
+    const ModConst m = mc[limb];
+    const size_t P = (size_t)nl * N;
+    const u64* ai = it.a + (size_t)limb * N + x;
+    const u64* aj = it.b + (size_t)limb * N + x;
+    u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
+    for (int k = 0; k < it.chunks; k++) {
+        const u64 a0 = __ldg(ai), a1 = __ldg(ai + P), b0 = __ldg(aj), b1 = __ldg(aj + P);
+        ai += 2 * P;
+        aj += 2 * P;
+        const u64 x0 = sub_mod(a0, b0, m.q), x1 = sub_mod(a1, b1, m.q);
+        mac128(s00, x0, x0);
+        mac128(s01, x0, x1);
+        mac128(s11, x1, x1);
+        if ((k & 7) == 7) {
+            fold(s00, m);
+            fold(s01, m);
+            fold(s11, m);
+        }
+    }
+    u64* o = out + (size_t)it.slot * 3 * P + (size_t)limb * N + x;
+    o[0] = reduce128(s00, m);
+    const u64 d1 = reduce128(s01, m);
+    o[P] = add_mod(d1, d1, m.q);
+    o[2 * P] = reduce128(s11, m);
+}
+
+// masked accumulate of one chunk of one job per item.  grid: x = item, y = tile, z = limb
+__global__ void __launch_bounds__(kT) k_mask_acc_items(const AggItem* __restrict__ items, int nl, int log_n,
+                                                       const ModConst* __restrict__ mc, u64* __restrict__ out) {
+    const AggItem it = items[blockIdx.x];
+    const int limb = blockIdx.z;
+    const size_t N = (size_t)1 << log_n;
+    const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
+    const ModConst m = mc[limb];
+    const size_t P = (size_t)nl * N;
+    u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
+    for (int i = 0; i < it.n; i++) {
+        const u64* a = it.cts + ((size_t)i * it.chunks + it.k) * 2 * P + (size_t)limb * N + x;
+        const u64* w = it.masks + (size_t)i * 2 * P + (size_t)limb * N + x;
+        const u64 a0 = __ldg(a), a1 = __ldg(a + P), m0 = __ldg(w), m1 = __ldg(w + P);
+        mac128(s00, a0, m0);
+        mac128(s01, a0, m1);
+        mac128(s01, a1, m0);
+        mac128(s11, a1, m1);
+        if ((i & 3) == 3) {
+            fold(s00, m);
+            fold(s01, m);
+            fold(s11, m);
+        }
+    }
+    u64* o = out + (size_t)it.slot * 3 * P + (size_t)limb * N + x;
+    o[0] = reduce128(s00, m);
+    o[P] = reduce128(s01, m);
+    o[2 * P] = reduce128(s11, m);
+}
+
+// words-per-item copy to per-item destinations.  grid: x = chunk of 2*kT words, y = item
+__global__ void k_copy_items(const u64* __restrict__ src, size_t words, u64* const* __restrict__ dst) {
+    const int b = blockIdx.y;
+    u64* d = dst[b];
+    const u64* s = src + (size_t)b * words;
+    for (size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < words; i += (size_t)gridDim.x * blockDim.x * 2) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(s + i);
+        *reinterpret_cast<ulonglong2*>(d + i) = v;
+    }
+}
+
 // ---------------------------------------------------------------------------- base conversion
 // All four kernels handle VEC consecutive coefficients per thread with 16-byte accesses; the
 // per-destination reduction constants come from the shared-memory copy of the table.
@@ -427,6 +503,48 @@ __global__ void __launch_bounds__(kT) k_inner_multi(const u64* __restrict__ ext,
 #pragma unroll
         for (int k = 0; k < T; k++) {
             const ulonglong2 kb2 = ld2(keys.p[k] + ko), ka2 = ld2(keys.p[k] + ko + ka);
+            mac128(a[k][0], e.x, kb2.x);
+            mac128(a[k][1], e.y, kb2.y);
+            mac128(c[k][0], e.x, ka2.x);
+            mac128(c[k][1], e.y, ka2.y);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < T; k++) {
+        u64* vb = v + k * v_key_stride + (size_t)b * 2 * rows * N + (size_t)t * N + x;
+        st2(vb, reduce128c(a[k][0], q, r64, r64sh, osh), reduce128c(a[k][1], q, r64, r64sh, osh));
+        st2(vb + (size_t)rows * N, reduce128c(c[k][0], q, r64, r64sh, osh), reduce128c(c[k][1], q, r64, r64sh, osh));
+    }
+}
+
+// same as k_inner_multi with per-item keys: keys[b * T + t]
+template <int T>
+__global__ void __launch_bounds__(kT) k_inner_items(const u64* __restrict__ ext, const u64* __restrict__ d,
+                                                    size_t d_stride, int beta, int nl, int rows, int alpha, int nq,
+                                                    int nqp, int log_n, const u64* const* __restrict__ keys,
+                                                    const ModConst* __restrict__ mc, u64* __restrict__ v,
+                                                    size_t v_key_stride) {
+    const int b = blockIdx.x, t = blockIdx.z;
+    const size_t N = (size_t)1 << log_n;
+    const size_t x = ((size_t)blockIdx.y * kT + threadIdx.x) * 2;
+    const int kt = t < nl ? t : nq + (t - nl);
+    const ModConst& mcr = mc[kt];
+    const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
+    const u64* kp[T];
+#pragma unroll
+    for (int k = 0; k < T; k++) kp[k] = keys[(size_t)b * T + k];
+    u128v a[T][2], c[T][2];
+#pragma unroll
+    for (int k = 0; k < T; k++) a[k][0] = a[k][1] = c[k][0] = c[k][1] = u128v{0, 0};
+    for (int j = 0; j < beta; j++) {
+        const u64* src = (t < nl && t / alpha == j) ? d + (size_t)b * d_stride + ((size_t)t << log_n)
+                                                     : ext + (((size_t)b * beta + j) * rows + t) * N;
+        const ulonglong2 e = ld2(src + x);
+        const size_t ko = (((size_t)j * 2 + 0) * nqp + kt) * N + x;
+        const size_t ka = (size_t)nqp * N;
+#pragma unroll
+        for (int k = 0; k < T; k++) {
+            const ulonglong2 kb2 = ld2(kp[k] + ko), ka2 = ld2(kp[k] + ko + ka);
             mac128(a[k][0], e.x, kb2.x);
             mac128(a[k][1], e.y, kb2.y);
             mac128(c[k][0], e.x, ka2.x);
@@ -915,3 +1033,47 @@ void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods, int nrow
     k_square_rows<<<grid_for((size_t)nrows * c->N), kT, 0, c->stream>>>(s, out, ml, c->log_n, c->mc);
     g_lc_launches += 1;
 }
+
+void op_sq_acc_items(lc_ctx* c, const PairItem* items_dev, int count, int nl, u64* out) {
+    if (count <= 0) return;
+    dim3 grid(count, (unsigned)(c->N / kT), nl);
+    k_sq_acc_items<<<grid, kT, 0, c->stream>>>(items_dev, nl, c->log_n, c->mc, out);
+    g_lc_launches += 1;
+}
+
+void op_mask_acc_items(lc_ctx* c, const AggItem* items_dev, int count, int nl, u64* out) {
+    if (count <= 0) return;
+    dim3 grid(count, (unsigned)(c->N / kT), nl);
+    k_mask_acc_items<<<grid, kT, 0, c->stream>>>(items_dev, nl, c->log_n, c->mc, out);
+    g_lc_launches += 1;
+}
+
+void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level,
+                    const u64* const* keys_dev, int T, u64* v, size_t v_key_stride) {
+    const int beta = c->digits(level);
+    const int nl = level + 1, rows = nl + c->np;
+    dim3 grid(B, (unsigned)(c->N / (2 * kT)), rows);
+#define LC_II(TT)                                                                                                   \
+    k_inner_items<TT><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, \
+                                                  c->log_n, keys_dev, c->mc, v, v_key_stride)
+    switch (T) {
+        case 1: LC_II(1); break;
+        case 2: LC_II(2); break;
+        case 3: LC_II(3); break;
+        case 4: LC_II(4); break;
+        case 5: LC_II(5); break;
+        case 6: LC_II(6); break;
+        case 7: LC_II(7); break;
+        default: break;
+    }
+#undef LC_II
+    g_lc_launches += 1;
+}
+
+void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev, int B) {
+    if (B <= 0) return;
+    dim3 grid((unsigned)std::min<size_t>((words / 2 + kT - 1) / kT, 4096), B);
+    k_copy_items<<<grid, kT, 0, c->stream>>>(src, words, dst_dev);
+    g_lc_launches += 1;
+}
+

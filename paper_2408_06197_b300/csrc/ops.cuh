@@ -55,3 +55,29 @@ void op_enc_combine(lc_ctx* c, const u64* m, const u64* r, const u64* e0, const 
 void op_dec_combine(lc_ctx* c, const u64* ct, const u64* s, int deg, int nl, u64* out);
 // elementwise square (evaluation domain), nl rows of modulus index = row
 void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods_host, int nrows);
+
+// ------------------------------------------------------------------ multi-job (ragged) batches
+// one pair of one job: client chunk arrays a, b ([chunks][2][nl][N]), result slot `slot`
+struct PairItem {
+    const u64* a;
+    const u64* b;
+    int chunks;
+    int slot;
+};
+// one chunk k of one job: the job's ciphertexts ([n][chunks][2][nl][N]) and masks ([n][2][nl][N])
+struct AggItem {
+    const u64* cts;
+    const u64* masks;
+    int n;
+    int chunks;
+    int k;
+    int slot;
+};
+void op_sq_acc_items(lc_ctx* c, const PairItem* items_dev, int count, int nl, u64* out);
+void op_mask_acc_items(lc_ctx* c, const AggItem* items_dev, int count, int nl, u64* out);
+// inner products with per-item keys: keys_dev[b * T + t] is item b's key for slot t
+void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level,
+                    const u64* const* keys_dev, int T, u64* v, size_t v_key_stride);
+// dst_dev[b] <- src + b * words (words per item)
+void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev, int B);
+

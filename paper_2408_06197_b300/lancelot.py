@@ -62,6 +62,11 @@ _ALLOC_FN = ctypes.CFUNCTYPE(vp, ctypes.c_size_t, vp)
 _FREE_FN = ctypes.CFUNCTYPE(None, vp, vp)
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("evk", vp), ("cts", vp), ("n", u32), ("chunks", u32), ("masks", vp), ("out_dist", vp),
+                ("out_agg", vp)]
+
+
 class _Allocator(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", vp)]
 
@@ -110,6 +115,8 @@ def lib() -> ctypes.CDLL:
             "lc_graph_end": [vp, vp],
             "lc_graph_launch": [vp, vp],
             "lc_graph_free": [vp],
+            "lc_batch_distances": [vp, vp, u32, u32, u32, vp],
+            "lc_batch_aggregate": [vp, vp, u32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -516,6 +523,51 @@ class Context:
         self._check(lib().lc_masked_aggregate(self.h, evk.h, pin, n, chunks, scale, pm, mask_scale, mode, pout,
                                               ctypes.byref(sc)), "lc_masked_aggregate")
         return out, sc.value
+
+
+class Job:
+    """One aggregation round: its tenant's keys, client ciphertexts [n][chunks][2][nq][N] and,
+    for the aggregate, masks [n][2][nq][N].  Outputs are allocated on demand."""
+
+    def __init__(self, evk: "EvalKeys", cts: torch.Tensor, n: int, chunks: int, masks: Optional[torch.Tensor] = None):
+        ctx = evk.ctx
+        _need(cts, n * chunks * 2 * ctx.nq * ctx.N, "Job: cts")
+        if masks is not None:
+            _need(masks, n * 2 * ctx.nq * ctx.N, "Job: masks")
+        self.evk, self.cts, self.n, self.chunks, self.masks = evk, cts, n, chunks, masks
+        self.out_dist: Optional[torch.Tensor] = None
+        self.out_agg: Optional[torch.Tensor] = None
+
+    def _c(self) -> _Job:
+        return _Job(self.evk.h.value, self.cts.data_ptr(), self.n, self.chunks,
+                    self.masks.data_ptr() if self.masks is not None else None,
+                    self.out_dist.data_ptr() if self.out_dist is not None else None,
+                    self.out_agg.data_ptr() if self.out_agg is not None else None)
+
+
+def batch_distances(ctx: "Context", jobs: Sequence[Job], mode_flags: int = 0,
+                    groups: Optional[Sequence[int]] = None):
+    """Distances of several rounds (different n, model sizes, tenants) in shared batched waves."""
+    for j in jobs:
+        if j.out_dist is None:
+            j.out_dist = ctx.empty(j.n * (j.n - 1) // 2, 2, ctx.L, ctx.N)
+        _need(j.out_dist, j.n * (j.n - 1) // 2 * 2 * ctx.L * ctx.N, "batch_distances: out")
+    arr = (_Job * max(1, len(jobs)))(*[j._c() for j in jobs])
+    g = np.array(list(groups) if groups else [], dtype=np.uint32)
+    ctx._check(lib().lc_batch_distances(ctx.h, arr, len(jobs), int(mode_flags) & LC_HOIST_QP_SUM, len(g),
+                                        _np_ptr(g) if len(g) else None), "lc_batch_distances")
+
+
+def batch_aggregate(ctx: "Context", jobs: Sequence[Job]):
+    """Masked aggregates of several rounds in shared batched waves."""
+    for j in jobs:
+        if j.masks is None:
+            raise LancelotError("batch_aggregate: job without masks")
+        if j.out_agg is None:
+            j.out_agg = ctx.empty(j.chunks, 2, ctx.L, ctx.N)
+        _need(j.out_agg, j.chunks * 2 * ctx.L * ctx.N, "batch_aggregate: out")
+    arr = (_Job * max(1, len(jobs)))(*[j._c() for j in jobs])
+    ctx._check(lib().lc_batch_aggregate(ctx.h, arr, len(jobs)), "lc_batch_aggregate")
 
 
 class Graph:

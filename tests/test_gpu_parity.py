@@ -330,6 +330,56 @@ def test_edge_cases(toy):
         toy.g.distances(toy.gevk, gcs, 4, 1, toy.prm.scale, groups=[1, 1])  # does not cover all slots
 
 
+def _job_inputs(env, keys, w, seed_client0):
+    W = S.client_updates(w)
+    X = S.split_chunks(W, env.prm.slots)
+    m = plaintexts(env.o, env.prm, X).reshape(-1, env.N)
+    r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), range(w.chunks), env.N, job=w.job)
+    return W, X, m, r, e0, e1
+
+
+def test_uneven_batch_matches_each_job_alone(toy):
+    """Jobs with different client counts, chunk counts and tenants (key sets) batched together give
+    each job exactly the results it gets alone (distances with the log-step and the one-ModDown
+    schedules, and masked aggregates)."""
+    LC = toy.LC
+    g = toy.g
+    keys_b = KeySet(toy.prm, 7, S.CFG_UNEVEN, O.rotations_of_schedule(toy.sched) + [3])
+    _, evk_b = keys_b.gpu_keys(g)
+    pk_b = g.pk_gen(keys_b.s, keys_b.pk_a, keys_b.pk_e)
+    specs = [(3, 1, toy.gevk, toy.gpk, 0), (5, 3, evk_b, pk_b, 1), (2, 2, toy.gevk, toy.gpk, 2), (4, 2, evk_b, pk_b, 3)]
+    jobs = []
+    for n, chunks, evk, pk, jid in specs:
+        w = S.Workload(f"u{jid}", S.CFG_UNEVEN, 12, n, chunks * toy.prm.slots - 7, 2, (n - 1,), "scale5", 1, 1, job=jid)
+        W, X, m, r, e0, e1 = _job_inputs(toy, None, w, 0)
+        cts = g.encrypt(pk, m, r, e0, e1).reshape(n, chunks, 2, toy.L + 1, toy.N)
+        masks = g.encrypt(pk, m.reshape(n, chunks, -1)[:, 0].copy(), r.reshape(n, chunks, -1)[:, 0].copy(),
+                          e0.reshape(n, chunks, -1)[:, 0].copy(), e1.reshape(n, chunks, -1)[:, 0].copy())
+        jobs.append(LC.Job(evk, cts, n, chunks, masks))
+    for sched, flags in ((None, 0), ([2] + [1] * (len(toy.sched) - 2), LC.LC_HOIST_QP_SUM)):
+        for j in jobs:
+            j.out_dist = None
+        LC.batch_distances(g, jobs, LC.LC_MODE_BATCHED | flags, sched)
+        for j in jobs:
+            alone, _ = g.distances(j.evk, j.cts, j.n, j.chunks, toy.prm.scale, mode=LC.LC_MODE_BATCHED | flags,
+                                   groups=sched)
+            assert torch.equal(alone, j.out_dist)
+    LC.batch_aggregate(g, jobs)
+    for j in jobs:
+        alone, _ = g.masked_aggregate(j.evk, j.cts, j.n, j.chunks, toy.prm.scale, j.masks, toy.prm.scale)
+        assert torch.equal(alone, j.out_agg)
+    g.set_max_batch(3)  # several waves: still identical
+    try:
+        for j in jobs:
+            j.out_dist = None
+        LC.batch_distances(g, jobs)
+        for j in jobs:
+            alone, _ = g.distances(j.evk, j.cts, j.n, j.chunks, toy.prm.scale)
+            assert torch.equal(alone, j.out_dist)
+    finally:
+        g.set_max_batch(0)
+
+
 # ------------------------------------------------------------------------------- production sizes
 
 def test_production_distances_small_bit_exact(prod):
