@@ -249,6 +249,105 @@ def run_micro(args):
                                 for k, v in prof.items()}}), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+SERVING_SCHED = [2] * 7
+
+
+def build_serving(LC, g, tenants: int, seed: int = 3, honest: int = 48, byz: int = 16):
+    """Tenants with resident keys (relin + 21 rotation keys of the one-ModDown schedule) and, per
+    tenant, a device pool of encrypted update chunks (`honest` draws of N(0, 0.01^2) per slot and
+    `byz` draws scaled by 5) from which arriving rounds are assembled."""
+    import torch
+    from paper_2408_06197_b300 import serving as SV
+    N, slots = g.N, g.slots
+    qp = g.q + g.p
+    out = []
+    for t in range(tenants):
+        s = S.secret_key(seed, S.CFG_SERVING, N, job=t)
+        pa, pe = S.pk_rand(seed, S.CFG_SERVING, g.q, N, job=t)
+        pk = g.pk_gen(s, pa, pe)
+        evk = g.evk()
+        evk.add(s, None, *S.swk_rand(seed, S.CFG_SERVING, qp, g.dnum, N, None, job=t))
+        for r in LC.rotations_of_schedule(SERVING_SCHED):
+            evk.add(s, r, *S.swk_rand(seed, S.CFG_SERVING, qp, g.dnum, N, r, job=t))
+        vals = [S.rng(seed, S.CFG_SERVING, t, i, 0, S.P_UPDATE).normal(0.0, 0.01, slots) for i in range(honest + byz)]
+        vals = [v * (5.0 if i >= honest else 1.0) for i, v in enumerate(vals)]
+        m = np.stack([g.encode(v, g.scale) for v in vals])
+        r, e0, e1 = S.enc_rand_batch(seed, S.CFG_SERVING, range(honest + byz), [0], N, job=t)
+        pool = g.encrypt(pk, m, r, e0, e1)
+        out.append((SV.Tenant(evk, pk, s), pool))
+    return out
+
+
+def run_serving(args):
+    """Poisson round stream over 4 tenants (sizes of the uneven-batch workload: n in {5,10,20,40},
+    d in {2^16..2^22}), HBM admission budget, continuous batching, GPU read-out + host Krum +
+    GPU mask encryption as the KGC step.  One JSON line per arrival rate."""
+    import torch
+    from paper_2408_06197_b300 import lancelot as LC
+    from paper_2408_06197_b300 import serving as SV
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    honest, byz = 48, 16
+    with torch.cuda.stream(stream):
+        g = LC.Context.production(device=local, stream=stream)
+        ten = build_serving(LC, g, args.tenants, honest=honest, byz=byz)
+        tenants = [t for t, _ in ten]
+        pools = [p for _, p in ten]
+
+        def ingest(r):
+            """Round r's client chunks, assembled on the device from its tenant's pool (honest
+            clients from the honest draws, the last n/5 clients from the x5 draws)."""
+            pick = S.rng(3, S.CFG_SERVING, r.rid, 0, 0, S.P_JOB)
+            idx = pick.integers(0, honest, size=(r.n, r.chunks))
+            nb = r.n // 5
+            if nb:
+                idx[r.n - nb:] = honest + pick.integers(0, byz, size=(nb, r.chunks))
+            it = torch.from_numpy(idx.reshape(-1)).to(pools[r.tenant].device, non_blocking=True)
+            return pools[r.tenant].index_select(0, it).view(r.n, r.chunks, 2, g.nq, g.N)
+
+        def mask_rand(r, i):
+            return S.enc_rand(3, S.CFG_SERVING, i, S.MASK_CHUNK, g.N, job=r.rid)
+
+        def rounds_of(stream_rounds):
+            out = []
+            for x in stream_rounds:
+                nb = x.n_clients // 5
+                out.append(SV.Round(x.rid, x.tenant, x.n_clients, max(1, -(-x.d // g.slots)), x.arrival, f=nb,
+                                    n_select=max(1, x.n_clients - 2 * nb - 3), average=True))
+            return out
+
+        # warm-up: a few rounds of every size class, untimed
+        warm = rounds_of(S.serving_rounds(seed=4, n_rounds=args.warmup, rate=1e9, tenants=args.tenants))
+        SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=SERVING_SCHED).run(warm, realtime=False)
+        torch.cuda.synchronize()
+        for rate in [float(x) for x in args.rates.split(",")]:
+            rounds = rounds_of(S.serving_rounds(seed=3, n_rounds=args.rounds, rate=rate, tenants=args.tenants))
+            srv = SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=SERVING_SCHED)
+            clocks = Clocks(local)
+            clocks.start()
+            l0 = LC.launches()
+            t0 = time.perf_counter()
+            done = srv.run(rounds, realtime=True)
+            span = time.perf_counter() - t0
+            ck = clocks.stop()
+            summ = SV.latency_summary(done)
+            line = {"metric": "served aggregation rounds: round latency (arrival -> aggregate ready)",
+                    "impl": "ours", "rate_per_s": rate, "rounds": summ["rounds"], "p50_ms": summ["p50_ms"],
+                    "p99_ms": summ["p99_ms"], "kgc_p50_ms": summ["kgc_p50_ms"],
+                    "pairs_per_s": summ["pairs"] / span, "rounds_per_s": len(done) / span,
+                    "mean_rounds_per_batch": srv.stats["rounds_batched"] / max(1, srv.stats["distance_batches"]),
+                    "max_resident_gb": srv.stats["max_used"] / 1e9, "gpu_launches": LC.launches() - l0,
+                    "clocks": ck, "dtype": "u64", "data": "synthetic",
+                    "config": {"workload": "serving_N32768_4tenants_n{5,10,20,40}_d{2^16..2^22}_poisson",
+                               "tenants": args.tenants, "budget_gb": args.budget_gb,
+                               "rotation_schedule": "g2qp", "seed": 3}}
+            print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -265,6 +364,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the per-operation reference measurement")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels eagerly instead of replaying a CUDA graph")
     ap.add_argument("--micro", action="store_true", help="small isolated kernel case for profiler captures")
+    ap.add_argument("--serving", action="store_true", help="Poisson-arrival serving loop; one line per rate")
+    ap.add_argument("--rates", default="1,2,5", help="serving arrival rates (rounds/s), comma separated")
+    ap.add_argument("--rounds", type=int, default=100, help="serving rounds per rate")
+    ap.add_argument("--tenants", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -273,6 +377,9 @@ def main():
         return
     if args.micro:
         run_micro(args)
+        return
+    if args.serving:
+        run_serving(args)
         return
 
     import torch

@@ -169,6 +169,13 @@ int lc_encrypt(lc_ctx* ctx, const uint64_t* pk, const int64_t* m, const int8_t* 
  * mod Q_level.  ct: device [deg][level+1][N] (deg 2 or 3); s: host int8[N];
  * res_out: host uint64[level+1][N], coefficient domain. */
 int lc_decrypt(lc_ctx* ctx, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out);
+/* KGC read-out of ciphertexts that hold one value in every slot (the rotate-and-summed
+ * distances of Algorithm 1): the average of the slots, which is coefficient 0 of the plaintext
+ * divided by the scale, computed from c0 + c1 s on limb q_0 only (a GPU reduction per
+ * ciphertext).  Valid while |value * scale| < q_0 / 2.  s: host int8[N]; cts: device
+ * [count][2][level+1][N]; out: host double[count]. */
+int lc_decrypt_const(lc_ctx* ctx, const int8_t* s, const uint64_t* cts, uint32_t count, uint32_t level, double scale,
+                     double* out);
 /* Centred CRT of residues[level+1][N] (host) to doubles m_out[N] (host), exact big-integer. */
 int lc_crt_to_double(lc_ctx* ctx, const uint64_t* res, uint32_t level, double* m_out);
 

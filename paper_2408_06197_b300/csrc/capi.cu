@@ -900,6 +900,34 @@ int lc_decrypt(lc_ctx* c, const int8_t* s, const uint64_t* ct, uint32_t deg, uin
     return check_launch(c, "lc_decrypt");
 }
 
+int lc_decrypt_const(lc_ctx* c, const int8_t* s, const uint64_t* cts, uint32_t count, uint32_t level, double scale,
+                     double* out) {
+    if (!c || !s || !cts || !out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_decrypt_const: bad argument");
+    if (count == 0) return LC_OK;
+    clear_prior_error();
+    const size_t N = c->N;
+    u64* t = lc_scratch(c, (2 * N + count + 8) * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    u64* s0 = t;
+    u64* raw = s0 + N;
+    u64* res = raw + N;
+    const int mods[1] = {0};
+    LC_CUDA(c, cudaMemcpyAsync(raw, s, N, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), 1, mods, 1, s0);
+    RowMap m = rows_seq(1);
+    ntt_fwd_p(c, s0, N, 1, m);
+    op_const_coef0(c, cts, (size_t)2 * (level + 1) * N, (int)count, s0, res);
+    std::vector<u64> h(count);
+    LC_CUDA(c, cudaMemcpyAsync(h.data(), res, count * 8, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const u64 q0 = c->mod[0];
+    for (uint32_t k = 0; k < count; k++) {
+        const double v = h[k] > q0 / 2 ? -(double)(q0 - h[k]) : (double)h[k];
+        out[k] = v / scale;
+    }
+    return check_launch(c, "lc_decrypt_const");
+}
+
 int lc_crt_to_double(lc_ctx* c, const uint64_t* res, uint32_t level, double* m_out) {
     if (!c || !res || !m_out || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_crt_to_double: bad argument");
     const size_t N = c->N;

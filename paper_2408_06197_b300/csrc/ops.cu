@@ -382,6 +382,32 @@ __global__ void k_copy_items(const u64* __restrict__ src, size_t words, u64* con
     }
 }
 
+// KGC read-out of ciphertexts that hold one value in every slot: coefficient 0 of c0 + c1 s
+// mod q0, i.e. N^-1 * sum_idx (c0 + c1 s)[idx] over the evaluation-domain limb 0.
+// grid: x = ciphertext; block reduction of 128-bit partial sums.
+__global__ void __launch_bounds__(kT) k_const_coef0(const u64* __restrict__ cts, size_t ct_stride,
+                                                   const u64* __restrict__ s0, int log_n,
+                                                   const ModConst* __restrict__ mc, u64* __restrict__ out) {
+    __shared__ u64 red[kT];
+    const ModConst m = mc[0];
+    const size_t N = (size_t)1 << log_n;
+    const size_t P = ct_stride / 2;  // words per polynomial
+    const u64* c0 = cts + (size_t)blockIdx.x * ct_stride;
+    const u64* c1 = c0 + P;
+    u128v acc{0, 0};
+    for (size_t i = threadIdx.x; i < N; i += kT) {
+        const u64 v = add_mod(c0[i], mul_mod(c1[i], s0[i], m), m.q);
+        add128(acc, v);
+    }
+    red[threadIdx.x] = reduce128(acc, m);
+    __syncthreads();
+    for (int w = kT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = add_mod(red[threadIdx.x], red[threadIdx.x + w], m.q);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = mul_shoup(red[0], m.n_inv, m.n_inv_sh, m.q);
+}
+
 // ---------------------------------------------------------------------------- base conversion
 // All four kernels handle VEC consecutive coefficients per thread with 16-byte accesses; the
 // per-destination reduction constants come from the shared-memory copy of the table.
@@ -1074,6 +1100,12 @@ void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev,
     if (B <= 0) return;
     dim3 grid((unsigned)std::min<size_t>((words / 2 + kT - 1) / kT, 4096), B);
     k_copy_items<<<grid, kT, 0, c->stream>>>(src, words, dst_dev);
+    g_lc_launches += 1;
+}
+
+void op_const_coef0(lc_ctx* c, const u64* cts, size_t ct_stride, int count, const u64* s0, u64* out) {
+    if (count <= 0) return;
+    k_const_coef0<<<count, kT, 0, c->stream>>>(cts, ct_stride, s0, c->log_n, c->mc, out);
     g_lc_launches += 1;
 }
 

@@ -80,4 +80,7 @@ void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, in
                     const u64* const* keys_dev, int T, u64* v, size_t v_key_stride);
 // dst_dev[b] <- src + b * words (words per item)
 void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev, int B);
+// coefficient 0 (mod q0) of c0 + c1 s for `count` ciphertexts (stride ct_stride words), s0 = s in
+// the evaluation domain of limb 0
+void op_const_coef0(lc_ctx* c, const u64* cts, size_t ct_stride, int count, const u64* s0, u64* out);
 

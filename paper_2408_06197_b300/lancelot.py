@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "lc_graph_free": [vp],
             "lc_batch_distances": [vp, vp, u32, u32, u32, vp],
             "lc_batch_aggregate": [vp, vp, u32],
+            "lc_decrypt_const": [vp, vp, vp, u32, u32, ctypes.c_double, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -404,6 +405,16 @@ class Context:
         self._check(lib().lc_decrypt(self.h, _np_ptr(np.ascontiguousarray(s, np.int8)), _t_ptr(ct), deg, level,
                                      _np_ptr(res)), "lc_decrypt")
         return res
+
+    def decrypt_const(self, s: np.ndarray, cts: torch.Tensor, level: int, scale: float) -> np.ndarray:
+        """Slot average of each ciphertext holding one value in every slot (KGC read-out)."""
+        if cts.numel() == 0:
+            return np.zeros(0, dtype=np.float64)
+        count = _whole(cts, 2 * (level + 1) * self.N, "decrypt_const")
+        out = np.zeros(count, dtype=np.float64)
+        self._check(lib().lc_decrypt_const(self.h, _np_ptr(np.ascontiguousarray(s, np.int8)), _t_ptr(cts), count,
+                                           level, scale, _np_ptr(out)), "lc_decrypt_const")
+        return out
 
     def decrypt(self, s: np.ndarray, ct: torch.Tensor, level: int, scale: float) -> np.ndarray:
         res = self.decrypt_residues(s, ct, level)

@@ -1,0 +1,186 @@
+"""Serving loop for encrypted aggregation rounds (continuous batching on one GPU).
+
+A round is one federated-learning aggregation of one tenant (Algorithm 1): its clients'
+ciphertexts arrive on the device, the server computes the encrypted pair distances, the key
+generation center decrypts them, selects the clients (Algorithm 2) and returns an encrypted
+mask, and the server computes the masked aggregate.  The loop
+
+* admits waiting rounds in arrival order while their device footprint fits the HBM budget;
+* at every tick runs ONE batched distances call over all admitted rounds in the distance phase
+  and ONE batched aggregate call over all rounds in the aggregate phase
+  (lc_batch_distances / lc_batch_aggregate: rounds of different sizes and tenants share the
+  same launches, so rounds that arrive while others run join the next wave);
+* runs the KGC step between the phases (read-out of the distances on the GPU, Krum /
+  Multi-Krum on the host, encryption of the masks on the GPU) and times it separately;
+* keeps the tenants' evaluation keys resident for the whole run.
+
+Results of a round do not depend on which other rounds share its batches (exact integer
+arithmetic); tests/test_serving.py checks this.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import kgc
+from . import lancelot as LC
+
+WAITING, DIST, AGG, DONE = "waiting", "distances", "aggregate", "done"
+
+
+@dataclasses.dataclass
+class Tenant:
+    """A tenant's resident keys.  `s` stands for the KGC's secret (the KGC step runs in-process)."""
+    evk: "LC.EvalKeys"
+    pk: torch.Tensor
+    s: np.ndarray
+
+
+@dataclasses.dataclass
+class Round:
+    rid: int
+    tenant: int
+    n: int
+    chunks: int
+    arrival: float                      # seconds since the start of the run
+    f: int = 1                          # assumed Byzantine count for Krum
+    n_select: int = 1                   # clients kept (Multi-Krum averages them)
+    average: bool = False
+    cts: Optional[torch.Tensor] = None  # device [n][chunks][2][nq][N], filled at admission
+    state: str = WAITING
+    job: Optional["LC.Job"] = None
+    selected: Optional[List[int]] = None
+    distances: Optional[np.ndarray] = None
+    t_admit: float = 0.0
+    t_dist: float = 0.0
+    t_kgc: float = 0.0
+    t_done: float = 0.0
+    kgc_seconds: float = 0.0
+
+    @property
+    def pairs(self) -> int:
+        return self.n * (self.n - 1) // 2
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+class Server:
+    def __init__(self, ctx: "LC.Context", tenants: Sequence[Tenant], budget_bytes: float,
+                 ingest: Callable[[Round], torch.Tensor],
+                 mask_rand: Callable[[Round, int], tuple],
+                 groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM):
+        self.ctx, self.tenants, self.budget = ctx, list(tenants), float(budget_bytes)
+        self.ingest, self.mask_rand = ingest, mask_rand
+        self.groups = list(groups) if groups else [2] * ((ctx.log_n - 1) // 2) + [1] * ((ctx.log_n - 1) % 2)
+        self.flags = flags
+        self.waiting: List[Round] = []
+        self.active: List[Round] = []
+        self.done: List[Round] = []
+        self.used = 0.0
+        self.stats = {"distance_batches": 0, "rounds_batched": 0, "aggregate_batches": 0, "max_used": 0.0}
+        self.t0 = time.perf_counter()
+
+    # ------------------------------------------------------------------ accounting
+    def footprint(self, r: Round) -> float:
+        c = self.ctx
+        words = (r.n * r.chunks * 2 * c.nq + r.pairs * 2 * c.L + r.n * 2 * c.nq + r.chunks * 2 * c.L) * c.N
+        return 8.0 * words
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, r: Round):
+        self.waiting.append(r)
+
+    # ------------------------------------------------------------------ scheduling
+    def _admit(self):
+        while self.waiting:
+            r = self.waiting[0]
+            fp = self.footprint(r)
+            if self.used + fp > self.budget and self.active:
+                break
+            self.waiting.pop(0)
+            self.used += fp
+            self.stats["max_used"] = max(self.stats["max_used"], self.used)
+            r.cts = self.ingest(r)
+            r.job = LC.Job(self.tenants[r.tenant].evk, r.cts, r.n, r.chunks)
+            r.state, r.t_admit = DIST, self.now()
+            self.active.append(r)
+
+    def _kgc(self, r: Round):
+        """Decrypt the pair distances, select the clients, encrypt the mask (one ciphertext per
+        client holding its weight in every slot)."""
+        t = time.perf_counter()
+        c, ten = self.ctx, self.tenants[r.tenant]
+        sc = c.scale * c.scale / c.q[c.L]
+        vals = c.decrypt_const(ten.s, r.job.out_dist, c.L - 1, sc)
+        d = np.zeros((r.n, r.n))
+        k = 0
+        for i in range(r.n):
+            for j in range(i + 1, r.n):
+                d[i, j] = d[j, i] = vals[k]
+                k += 1
+        r.distances = d
+        r.selected = kgc.krum_select(d, r.f, r.n_select)
+        w = kgc.mask_weights(r.n, r.selected, average=r.average)
+        m = np.zeros((r.n, c.N), dtype=np.int64)
+        m[:, 0] = np.rint(w * c.scale).astype(np.int64)  # a constant in every slot encodes to (w scale, 0, ...)
+        rs, e0s, e1s = zip(*[self.mask_rand(r, i) for i in range(r.n)])
+        r.job.masks = c.encrypt(ten.pk, m, np.stack(rs), np.stack(e0s), np.stack(e1s))
+        r.kgc_seconds = time.perf_counter() - t
+        r.state, r.t_kgc = AGG, self.now()
+
+    def tick(self) -> bool:
+        """One scheduler step; returns False when there was nothing to run."""
+        self._admit()
+        dist = [r for r in self.active if r.state == DIST]
+        agg = [r for r in self.active if r.state == AGG]
+        if not dist and not agg:
+            return False
+        if agg:
+            LC.batch_aggregate(self.ctx, [r.job for r in agg])
+            self.stats["aggregate_batches"] += 1
+            self.ctx.sync()
+            now = self.now()
+            for r in agg:
+                r.state, r.t_done = DONE, now
+                self.active.remove(r)
+                self.done.append(r)
+                self.used -= self.footprint(r)
+                r.cts = None  # the ciphertexts leave the device; outputs stay with the round
+                r.job.cts = None
+        if dist:
+            LC.batch_distances(self.ctx, [r.job for r in dist], LC.LC_MODE_BATCHED | self.flags, self.groups)
+            self.stats["distance_batches"] += 1
+            self.stats["rounds_batched"] += len(dist)
+            self.ctx.sync()
+            now = self.now()
+            for r in dist:
+                r.t_dist = now
+                self._kgc(r)
+        return True
+
+    def run(self, rounds: Sequence[Round], realtime: bool = True) -> List[Round]:
+        """Feeds rounds at their arrival times (or all at once) and runs until all are done."""
+        pending = sorted(rounds, key=lambda r: r.arrival)
+        self.t0 = time.perf_counter()
+        while pending or self.waiting or self.active:
+            now = self.now()
+            while pending and (not realtime or pending[0].arrival <= now):
+                self.submit(pending.pop(0))
+            if not self.tick() and pending:
+                time.sleep(max(0.0, min(0.01, pending[0].arrival - self.now())))
+        return self.done
+
+
+def latency_summary(done: Sequence[Round]) -> Dict[str, float]:
+    lat = np.array([r.latency for r in done]) * 1e3
+    kg = np.array([r.kgc_seconds for r in done]) * 1e3
+    return {"rounds": len(done), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "kgc_p50_ms": float(np.percentile(kg, 50)), "pairs": int(sum(r.pairs for r in done))}

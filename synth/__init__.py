@@ -201,3 +201,27 @@ def split_chunks(x: np.ndarray, slots: int) -> np.ndarray:
     out = np.zeros(x.shape[:-1] + (chunks * slots,), dtype=np.float64)
     out[..., : x.shape[-1]] = x
     return out.reshape(x.shape[:-1] + (chunks, slots))
+
+
+@dataclasses.dataclass(frozen=True)
+class ServingRound:
+    rid: int
+    arrival: float        # seconds from the start of the run
+    tenant: int
+    n_clients: int
+    d: int
+
+
+def serving_rounds(seed: int = 3, n_rounds: int = 1000, rate: float = 1.0, tenants: int = 4,
+                   sizes=(5, 10, 20, 40), lengths=(1 << 16, 1 << 18, 1 << 20, 1 << 22)):
+    """Round stream of the serving workload: Poisson arrivals at `rate` per second, tenant
+    uniform over `tenants`, n uniform over `sizes`, d uniform over `lengths` (the uneven-batch
+    size distribution).  The draws depend on (seed, n_rounds index) only, not on the rate:
+    inter-arrival gaps are unit exponentials divided by the rate."""
+    g = rng(seed, CFG_SERVING, 0, 0, 0, P_ARRIVAL)
+    gaps = g.exponential(1.0, size=n_rounds)
+    ten = g.integers(0, tenants, size=n_rounds)
+    ns = g.choice(np.asarray(sizes), size=n_rounds)
+    ds = g.choice(np.asarray(lengths), size=n_rounds)
+    t = np.cumsum(gaps) / rate
+    return [ServingRound(i, float(t[i]), int(ten[i]), int(ns[i]), int(ds[i])) for i in range(n_rounds)]
