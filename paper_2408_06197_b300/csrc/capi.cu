@@ -438,11 +438,17 @@ void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u
          op_rescale_combine(c, ct, r, B, deg, level, out));
 }
 
+// algorithmic bytes of one fused group inner product: the extended digits (own rows from the
+// input), the group's keys, phi(c0)'s input, and the two outputs
+static double inner_gather_bytes(lc_ctx* c, int B, int level, int cnt) {
+    const int nl = level + 1, rows = nl + c->np, beta = c->digits(level);
+    return (double)c->N * 8.0 * ((double)B * beta * rows + 2.0 * cnt * beta * rows + 2.0 * B * rows + 2.0 * B * nl);
+}
+
 static size_t rotsum_words(lc_ctx* c, int B, int level, int max_group, bool qp_sum = false) {
     const size_t wsz = (size_t)B * 2 * (level + 1) * c->N;
-    if (qp_sum)  // the group's inner products and their sum over Q_l U P + accumulated phi(c0)
-        return ks_words(c, B, level) +
-               (size_t)B * c->N * ((((size_t)1 << max_group) - 1 + 1) * 2 * (level + 1 + c->np) + (level + 1));
+    if (qp_sum)  // the group's sum over Q_l U P + accumulated phi(c0); single-rotation groups use wsz
+        return ks_words(c, B, level) + std::max(wsz, (size_t)B * c->N * (2 * (level + 1 + c->np) + (level + 1)));
     return ks_words(c, B, level) + wsz * (((size_t)1 << max_group) - 1);
 }
 
@@ -468,26 +474,18 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
         ks_modup(c, y + P, 2 * P, B, level, kb);
         if (qp_sum && cnt > 1) {
             const size_t vsz = (size_t)B * 2 * rows * N;
-            u64* vs = wbase;                                  // [cnt][B][2][rows][N]
-            u64* usum = vs + (size_t)cnt * vsz;               // [B][2][rows][N]
-            u64* c0acc = usum + vsz;                          // [B][nl][N]
+            u64* usum = wbase;      // [B][2][rows][N]
+            u64* c0acc = usum + vsz;  // [B][nl][N]
             std::vector<const u64*> kp(cnt);
             std::vector<uint64_t> gs(cnt);
             for (int t = 0; t < cnt; t++) {
                 kp[t] = keys[t]->data;
                 gs[t] = keys[t]->galois;
             }
-            const int beta = c->digits(level);
-            PROF(c, PROF_INNER,
-                 (double)N * 8.0 * ((double)B * beta * rows + 2.0 * cnt * beta * rows + 2.0 * cnt * B * rows),
-                 (uint64_t)B, op_inner_multi(c, kb.ext, y + P, 2 * P, B, level, kp.data(), cnt, vs, vsz));
+            PROF(c, PROF_INNER, inner_gather_bytes(c, B, level, cnt), (uint64_t)B,
+                 op_inner_gather(c, kb.ext, y + P, 2 * P, y, 2 * P, B, level, kp.data(), nullptr, gs.data(), cnt, usum,
+                                 c0acc));
             c->n_keyswitch += (uint64_t)B * cnt;
-            PROF(c, PROF_AUTO, (double)vsz * 8.0 * (cnt + 1), (uint64_t)B,
-                 op_gather_sum_qp(c, vs, vsz, usum, B * 2, nl, gs.data(), cnt));
-            cudaMemcpy2DAsync(c0acc, P * 8, y, 2 * P * 8, P * 8, B, cudaMemcpyDeviceToDevice, c->stream);
-            PROF(c, PROF_AUTO, (double)B * P * 8.0 * 3.0 * cnt, (uint64_t)B, {
-                for (int t = 0; t < cnt; t++) op_gather_c0(c, y, c0acc, B, nl, keys[t]->galois);
-            });
             ks_moddown(c, usum, B, level, kb, c0acc, P, y + P, 2 * P, y, 2 * P);
         } else {
             for (int t = 0; t < cnt; t++)
@@ -1300,18 +1298,12 @@ static int items_tail(lc_ctx* c, u64* acc3, u64* ct2, u64* y, u64* tmp, int b, c
         ks_modup(c, y + P, 2 * P, b, level, kb);
         if (qp && cnt > 1) {
             const size_t vsz = (size_t)b * 2 * rows * N;
-            u64* vs = wbase;
-            u64* usum = vs + (size_t)cnt * vsz;
+            u64* usum = wbase;
             u64* c0acc = usum + vsz;
-            PROF(c, PROF_INNER, (double)N * 8.0 * b * (c->digits(level) + 2.0 * cnt) * rows, (uint64_t)b,
-                 op_inner_items(c, kb.ext, y + P, 2 * P, b, level, group_keys[gi], cnt, vs, vsz));
+            PROF(c, PROF_INNER, inner_gather_bytes(c, b, level, cnt), (uint64_t)b,
+                 op_inner_gather(c, kb.ext, y + P, 2 * P, y, 2 * P, b, level, nullptr, group_keys[gi],
+                                 group_gal[gi].data(), cnt, usum, c0acc));
             c->n_keyswitch += (uint64_t)b * cnt;
-            PROF(c, PROF_AUTO, (double)vsz * 8.0 * (cnt + 1), (uint64_t)b,
-                 op_gather_sum_qp(c, vs, vsz, usum, b * 2, nl, group_gal[gi].data(), cnt));
-            cudaMemcpy2DAsync(c0acc, P * 8, y, 2 * P * 8, P * 8, b, cudaMemcpyDeviceToDevice, c->stream);
-            PROF(c, PROF_AUTO, (double)b * P * 8.0 * 3.0 * cnt, (uint64_t)b, {
-                for (int t = 0; t < cnt; t++) op_gather_c0(c, y, c0acc, b, nl, group_gal[gi][t]);
-            });
             ks_moddown(c, usum, b, level, kb, c0acc, P, y + P, 2 * P, y, 2 * P);
         } else {
             // one ModDown per rotation: W_t = (y0 + MD(v_t0), MD(v_t1)) in the pre-permuted frame

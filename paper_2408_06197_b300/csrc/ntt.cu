@@ -23,19 +23,34 @@ __device__ __forceinline__ u64* limb_ptr(u64* base, size_t batch_stride, const R
     return base + (size_t)bi * batch_stride + ((size_t)map.row[r] << log_n);
 }
 
-// Cooley-Tukey butterfly (Harvey): inputs and outputs in [0, 4q), one conditional subtraction
+// Two value-range disciplines, chosen per CTA from the limb's prime:
+//  * q >= 2^46 (the 50/60-bit primes): Harvey-lazy, forward values in [0, 4q) and inverse values in
+//    [0, 2q), one conditional subtraction per butterfly;
+//  * q < 2^46 (the 30/40-bit primes): no conditional subtraction inside the network.  Forward
+//    values grow by less than 2q per stage (at most 4q + 2q log2(N) < 2^52), inverse values at most
+//    double per stage (below 2^(s+2) q after s stages, < 2^64 for log2(N) <= 16), and the last
+//    stage reduces fully.  Outputs are the same canonical residues in both disciplines.
+constexpr u64 kLazyLimit = 1ull << 46;
+
+// Cooley-Tukey butterfly; t = y w (lazy Shoup) is in [0, 2q) for any y < 2^64
+template <bool LZ>
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
-    const u64 xr = csub(x, two_q);                   // [0, 2q)
-    const u64 t = mul_shoup_lazy(y, w.x, w.y, q);    // [0, 2q) for any y < 2^64
+    const u64 xr = LZ ? x : csub(x, two_q);
+    const u64 t = mul_shoup_lazy(y, w.x, w.y, q);
     x = xr + t;
     y = xr + two_q - t;
 }
-// Gentleman-Sande butterfly, inputs/outputs in [0, 2q)
-__device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
-    u64 a = x + y;
-    u64 b = x + two_q - y;
-    x = csub(a, two_q);
+// Gentleman-Sande butterfly; ky is a multiple of q not below y (LZ), else y < 2q
+template <bool LZ>
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q, u64 ky) {
+    const u64 a = x + y;
+    const u64 b = x + (LZ ? ky : two_q) - y;
+    x = LZ ? a : csub(a, two_q);
     y = mul_shoup_lazy(b, w.x, w.y, q);
+}
+// any x < 2^64 -> [0, q)
+__device__ __forceinline__ u64 reduce_word(u64 x, const ModConst& mc) {
+    return csub(x - __umul64hi(x, mc.one_sh) * mc.q, mc.q);
 }
 
 // swizzle for the row-pass tile: XOR word bits 0..3 with bits 4..7
@@ -45,18 +60,12 @@ __device__ __forceinline__ ulonglong2 ldtw(const ulonglong2* t, int i) { return 
 
 // ------------------------------------------------------------------------------ column pass
 // forward: row bits C-1 .. 0 (global bits log_n-1 .. 8)
-template <int C>
-__global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+template <int C, bool LZ>
+__device__ __forceinline__ void fwd_col_body(u64* a, u64* s, const ModConst& mc, const ulonglong2* tw, int col0) {
     constexpr int LOGN = C + 8;
     constexpr int T = 1 << C;
     constexpr int RS = 1 << (C - 4);  // row stride of a thread's 16 words in phase 1
     constexpr int R2 = C - 4;         // row bits left for phase 2
-    __shared__ u64 s[R2 > 0 ? (16 << C) : 1];
-    int mi;
-    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
-    const int col0 = blockIdx.x * 16;
-    const ModConst mc = tb.mc[mi];
-    const ulonglong2* tw = tb.fwd + ((size_t)mi << LOGN);
     const int tid = threadIdx.x;
     const int c = tid & 15, rg = tid >> 4;
     u64 x[16];
@@ -69,7 +78,8 @@ __global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_st
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
             // row = rg + RS*u with rg < RS <= 2^b: row >> (b+1) = u >> (b+1-R2), a compile-time offset
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q, mc.two_q);
+            ct_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q,
+                        mc.two_q);
         }
     }
     if constexpr (R2 == 0) {
@@ -93,9 +103,9 @@ __global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_st
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     if (v >> st & 1) continue;
-                    ct_bfly(y[v], y[v | (1 << st)],
-                            ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
-                            mc.two_q);
+                    ct_bfly<LZ>(y[v], y[v | (1 << st)],
+                                ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
+                                mc.two_q);
                 }
             }
 #pragma unroll
@@ -104,19 +114,27 @@ __global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_st
     }
 }
 
-// inverse: row bits 0 .. C-1; the last stage (t = N/2) folds N^-1
 template <int C>
-__global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+__global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+    constexpr int LOGN = C + 8;
+    __shared__ u64 s[C > 4 ? (16 << C) : 1];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.fwd + ((size_t)mi << LOGN);
+    if (mc.q < kLazyLimit)
+        fwd_col_body<C, true>(a, s, mc, tw, blockIdx.x * 16);
+    else
+        fwd_col_body<C, false>(a, s, mc, tw, blockIdx.x * 16);
+}
+
+// inverse: row bits 0 .. C-1 (global stages 8 .. log_n-1); the last stage (t = N/2) folds N^-1
+template <int C, bool LZ>
+__device__ __forceinline__ void inv_col_body(u64* a, u64* s, const ModConst& mc, const ulonglong2* tw, int col0) {
     constexpr int LOGN = C + 8;
     constexpr int T = 1 << C;
     constexpr int RS = 1 << (C - 4);
     constexpr int R2 = C - 4;
-    __shared__ u64 s[R2 > 0 ? (16 << C) : 1];
-    int mi;
-    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
-    const int col0 = blockIdx.x * 16;
-    const ModConst mc = tb.mc[mi];
-    const ulonglong2* tw = tb.inv + ((size_t)mi << LOGN);
     const int tid = threadIdx.x;
     const int c = tid & 15, rg = tid >> 4;
     u64 x[16];
@@ -138,9 +156,9 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     if (v >> st & 1) continue;
-                    gs_bfly(y[v], y[v | (1 << st)],
-                            ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
-                            mc.two_q);
+                    gs_bfly<LZ>(y[v], y[v | (1 << st)],
+                                ldtw(tw, (1 << (LOGN - 9 - b)) + ((grp << R2) >> (b + 1)) + (v >> (b + 1))), mc.q,
+                                mc.two_q, mc.two_q << (b + 8));
                 }
             }
 #pragma unroll
@@ -159,13 +177,13 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
             if (st == 3) {
                 // final stage (t = N/2): (x + y) N^-1 and (x - y) psi^{-br(1)} N^-1, fully reduced
                 const u64 xa = x[u] + x[u | 8];
-                const u64 xb = x[u] + mc.two_q - x[u | 8];
+                const u64 xb = x[u] + (LZ ? (mc.two_q << (b + 8)) : mc.two_q) - x[u | 8];
                 const ulonglong2 wl = ldtw(tw, 0);
                 x[u] = mul_shoup(xa, mc.n_inv, mc.n_inv_sh, mc.q);
                 x[u | 8] = mul_shoup(xb, wl.x, wl.y, mc.q);
             } else {
-                gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q,
-                        mc.two_q);
+                gs_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, (1 << (LOGN - 9 - b)) + (u >> (b + 1 - R2))), mc.q,
+                            mc.two_q, mc.two_q << (b + 8));
             }
         }
     }
@@ -173,19 +191,28 @@ __global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_st
     for (int u = 0; u < 16; u++) a[((size_t)(rg + RS * u) << 8) + col0 + c] = x[u];
 }
 
-// ------------------------------------------------------------------------------ row pass
-// forward: bits 7 .. 0 inside 256-word blocks; input in [0, 4q), output fully reduced to [0, q)
-__global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
-                                                           NttTables tb) {
-    constexpr int E = 8 * 256;
-    __shared__ u64 s[E];
+template <int C>
+__global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+    constexpr int LOGN = C + 8;
+    __shared__ u64 s[C > 4 ? (16 << C) : 1];
     int mi;
-    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, log_n, mi) + (size_t)blockIdx.x * E;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, LOGN, mi);
     const ModConst mc = tb.mc[mi];
-    const ulonglong2* tw = tb.fwd + ((size_t)mi << log_n);
+    const ulonglong2* tw = tb.inv + ((size_t)mi << LOGN);
+    if (mc.q < kLazyLimit)
+        inv_col_body<C, true>(a, s, mc, tw, blockIdx.x * 16);
+    else
+        inv_col_body<C, false>(a, s, mc, tw, blockIdx.x * 16);
+}
+
+// ------------------------------------------------------------------------------ row pass
+// forward: bits 7 .. 0 inside 256-word blocks; output fully reduced to [0, q)
+template <bool LZ>
+__device__ __forceinline__ void fwd_row_body(u64* a, u64* s, const ModConst& mc, const ulonglong2* tw, int log_n,
+                                             int g_blk) {
     const int tid = threadIdx.x;
     const int lo = tid & 15, blk = tid >> 4;
-    const int g0 = blockIdx.x * E + (blk << 8);
+    const int g0 = g_blk + (blk << 8);
     u64 x[16];
 #pragma unroll
     for (int u = 0; u < 16; u++) x[u] = a[(blk << 8) + lo + 16 * u];
@@ -196,8 +223,8 @@ __global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t 
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
             // j = g0 + lo + 16u, g0 a multiple of 256, lo < 16: j >> (b+1) = (g0 >> (b+1)) + (u >> (b-3))
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))), mc.q,
-                    mc.two_q);
+            ct_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))),
+                        mc.q, mc.two_q);
         }
     }
 #pragma unroll
@@ -212,29 +239,40 @@ __global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t 
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
             // j = (g0 + 16 lo) + u with the bracket a multiple of 16: offset u >> (b+1)
-            ct_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))),
-                    mc.q, mc.two_q);
+            ct_bfly<LZ>(x[u], x[u | (1 << st)],
+                        ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))), mc.q,
+                        mc.two_q);
         }
     }
 #pragma unroll
-    for (int u = 0; u < 16; u++) s[swz((blk << 8) + 16 * lo + u)] = csub(csub(x[u], mc.two_q), mc.q);
+    for (int u = 0; u < 16; u++)
+        s[swz((blk << 8) + 16 * lo + u)] = LZ ? reduce_word(x[u], mc) : csub(csub(x[u], mc.two_q), mc.q);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];
 }
 
-// inverse: bits 0 .. 7 inside 256-word blocks; output in [0, 2q) for the column pass
-__global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+__global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
                                                            NttTables tb) {
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
     int mi;
     u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, log_n, mi) + (size_t)blockIdx.x * E;
     const ModConst mc = tb.mc[mi];
-    const ulonglong2* tw = tb.inv + ((size_t)mi << log_n);
+    const ulonglong2* tw = tb.fwd + ((size_t)mi << log_n);
+    if (mc.q < kLazyLimit)
+        fwd_row_body<true>(a, s, mc, tw, log_n, blockIdx.x * E);
+    else
+        fwd_row_body<false>(a, s, mc, tw, log_n, blockIdx.x * E);
+}
+
+// inverse: bits 0 .. 7 inside 256-word blocks (global stages 0 .. 7), input in [0, 2q)
+template <bool LZ>
+__device__ __forceinline__ void inv_row_body(u64* a, u64* s, const ModConst& mc, const ulonglong2* tw, int log_n,
+                                             int g_blk) {
     const int tid = threadIdx.x;
     const int lo = tid & 15, blk = tid >> 4;
-    const int g0 = blockIdx.x * E + (blk << 8);
+    const int g0 = g_blk + (blk << 8);
     u64 x[16];
 #pragma unroll
     for (int u = 0; u < 16; u++) s[swz((blk << 8) + lo + 16 * u)] = a[(blk << 8) + lo + 16 * u];
@@ -247,8 +285,9 @@ __global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t 
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))),
-                    mc.q, mc.two_q);
+            gs_bfly<LZ>(x[u], x[u | (1 << st)],
+                        ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))), mc.q,
+                        mc.two_q, mc.two_q << b);
         }
     }
 #pragma unroll
@@ -262,12 +301,26 @@ __global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t 
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            gs_bfly(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))), mc.q,
-                    mc.two_q);
+            gs_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + (u >> (b - 3))),
+                        mc.q, mc.two_q, mc.two_q << b);
         }
     }
 #pragma unroll
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = x[u];
+}
+
+__global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+                                                           NttTables tb) {
+    constexpr int E = 8 * 256;
+    __shared__ u64 s[E];
+    int mi;
+    u64* a = limb_ptr(base, batch_stride, map, blockIdx.y, log_n, mi) + (size_t)blockIdx.x * E;
+    const ModConst mc = tb.mc[mi];
+    const ulonglong2* tw = tb.inv + ((size_t)mi << log_n);
+    if (mc.q < kLazyLimit)
+        inv_row_body<true>(a, s, mc, tw, log_n, blockIdx.x * E);
+    else
+        inv_row_body<false>(a, s, mc, tw, log_n, blockIdx.x * E);
 }
 
 }  // namespace

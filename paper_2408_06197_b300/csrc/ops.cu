@@ -603,6 +603,84 @@ __global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64
     }
 }
 
+// One hoisted group with a single ModDown, fused: for the T rotations g_t of the group,
+//   usum[b][p][r][x]  = sum_t sum_j E_j[b][r][s_t] * key_t[j][p][r][s_t],   s_t = perm_{g_t}(x)
+//   c0acc[b][r][x]    = y0[b][r][x] + sum_t y0[b][r][s_t]                    (rows r < nl)
+// i.e. sum_t phi_{g_t}(<E, key_t>) with the keys stored pre-permuted by phi_{g_t}^-1, without
+// writing the per-rotation products.  E_j is the j-th extended digit (own rows from d).  All
+// products of one output sum in 128 bits (T * beta < 64 terms below q^2 < 2^120) and reduce
+// once, so the result equals the per-rotation reduction exactly.
+// grid: x = tile of kT coefficients, y = row r of Q_l U P, z = group of kBT items.
+constexpr int kBT = 4;
+template <int T, bool ITEMS>
+__global__ void __launch_bounds__(kT) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+                                                     size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
+                                                     int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
+                                                     int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
+                                                     Galois gs, const ModConst* __restrict__ mc,
+                                                     u64* __restrict__ usum, u64* __restrict__ c0acc) {
+    const size_t N = (size_t)1 << log_n;
+    const unsigned x = blockIdx.x * kT + threadIdx.x;
+    const int r = blockIdx.y;
+    const int b0 = blockIdx.z * kBT;
+    const int nb = min(kBT, B - b0);
+    const int kt = r < nl ? r : nq + (r - nl);
+    const ModConst& mcr = mc[kt];
+    const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
+    unsigned src[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) src[t] = auto_src(x, gs.g[t], log_n);
+    u128v a[kBT][2];
+#pragma unroll
+    for (int i = 0; i < kBT; i++) a[i][0] = a[i][1] = u128v{0, 0};
+    const size_t ka = (size_t)nqp * N;
+    for (int j = 0; j < beta; j++) {
+        const bool own = r < nl && r / alpha == j;
+        const size_t ko = ((size_t)j * 2 * nqp + kt) * N;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const unsigned s = src[t];
+            u64 k0 = 0, k1 = 0;
+            if (!ITEMS) {
+                k0 = __ldg(keys.p[t] + ko + s);
+                k1 = __ldg(keys.p[t] + ko + ka + s);
+            }
+#pragma unroll
+            for (int i = 0; i < kBT; i++) {
+                if (i < nb) {
+                    const int b = b0 + i;
+                    if (ITEMS) {
+                        const u64* kp = keys_dev[(size_t)b * T + t];
+                        k0 = __ldg(kp + ko + s);
+                        k1 = __ldg(kp + ko + ka + s);
+                    }
+                    const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
+                                       : ext + (((size_t)b * beta + j) * rows + r) * N;
+                    const u64 ev = __ldg(e + s);
+                    mac128(a[i][0], ev, k0);
+                    mac128(a[i][1], ev, k1);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kBT; i++) {
+        if (i < nb) {
+            const int b = b0 + i;
+            u64* ub = usum + ((size_t)b * 2 * rows + r) * N + x;
+            ub[0] = reduce128c(a[i][0], q, r64, r64sh, osh);
+            ub[(size_t)rows * N] = reduce128c(a[i][1], q, r64, r64sh, osh);
+            if (r < nl) {
+                const u64* yb = y0 + (size_t)b * y0_stride + ((size_t)r << log_n);
+                u64 acc = __ldg(yb + x);
+#pragma unroll
+                for (int t = 0; t < T; t++) acc += __ldg(yb + src[t]);  // T + 1 < 16 terms below q < 2^60
+                c0acc[((size_t)b * nl + r) * N + x] = reduce64(acc, mcr);
+            }
+        }
+    }
+}
+
 // ModDown conversion of the K special-prime rows.  grid: x = tile of 2*kT coefficients, y = b*2 + k
 template <int K>
 __global__ void __launch_bounds__(kT) k_moddown_bconv(const u64* __restrict__ v, int nl, int rows, int log_n,
@@ -927,6 +1005,41 @@ void op_inner_multi(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, in
         default: break;
     }
 #undef LC_IM
+    g_lc_launches += 1;
+}
+
+void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, const u64* y0, size_t y0_stride, int B,
+                     int level, const u64* const* keys, const u64* const* keys_dev, const uint64_t* gs, int T,
+                     u64* usum, u64* c0acc) {
+    const int beta = c->digits(level);
+    const int nl = level + 1, rows = nl + c->np;
+    dim3 grid((unsigned)(c->N / kT), rows, (unsigned)((B + kBT - 1) / kBT));
+    KeyPtrs kp{};
+    Galois g{};
+    for (int k = 0; k < T && k < 8; k++) {
+        kp.p[k] = keys ? keys[k] : nullptr;
+        g.g[k] = gs[k];
+    }
+#define LC_IG(TT)                                                                                                    \
+    if (keys_dev)                                                                                                    \
+        k_inner_gather<TT, true><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,     \
+                                                             c->alpha, c->nq, c->nq + c->np, c->log_n, kp, keys_dev, \
+                                                             g, c->mc, usum, c0acc);                                 \
+    else                                                                                                             \
+        k_inner_gather<TT, false><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,    \
+                                                              c->alpha, c->nq, c->nq + c->np, c->log_n, kp, nullptr, \
+                                                              g, c->mc, usum, c0acc)
+    switch (T) {
+        case 1: LC_IG(1); break;
+        case 2: LC_IG(2); break;
+        case 3: LC_IG(3); break;
+        case 4: LC_IG(4); break;
+        case 5: LC_IG(5); break;
+        case 6: LC_IG(6); break;
+        case 7: LC_IG(7); break;
+        default: break;
+    }
+#undef LC_IG
     g_lc_launches += 1;
 }
 

@@ -26,6 +26,12 @@ void op_inner_multi(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, in
 // usum = sum_t phi_{g_t}(src_t) over n_polys polys of Q_l U P rows (src_t = src + t * src_stride)
 void op_gather_sum_qp(lc_ctx* c, const u64* src, size_t src_stride, u64* usum, int n_polys, int nl,
                       const uint64_t* gs, int T);
+// one hoisted group (T <= 7 rotations, one ModDown), fused inner products + automorphisms:
+// usum [B][2][rows][N] = sum_t phi_{g_t}(<E, key_t>), c0acc [B][nl][N] = y0 + sum_t phi_{g_t}(y0).
+// Keys: host array keys[t] shared by all items, or (keys == null) device table keys_dev[b * T + t].
+void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, const u64* y0, size_t y0_stride, int B,
+                     int level, const u64* const* keys, const u64* const* keys_dev, const uint64_t* gs, int T,
+                     u64* usum, u64* c0acc);
 void op_moddown_bconv(lc_ctx* c, const u64* v, int B, int level, u64* conv);
 // W[b][k] = (v_k - conv_k) P^-1 + add_k  (add pointers may be null; per-item strides in words)
 void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int level, const u64* add0,
