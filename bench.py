@@ -203,8 +203,9 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- kernel micro case
 def run_micro(args):
-    """Small isolated case for profiler captures (about 3 GB on the device, inputs larger than
-    L2): batched distances of 10 clients x 8 chunks (45 pairs), 960 limbs transformed forward and
+    """Small isolated case for profiler captures (about 4 GB on the device, inputs larger than
+    L2): batched distances of 10 clients x 8 chunks (45 pairs, one-ModDown rotation groups), 960
+    limbs transformed forward and
     back, 16 degree-2 triples relinearised and rescaled at level 14, and 16 ciphertexts rotated
     at level 13.  Prints per-class timings."""
     import torch
@@ -222,8 +223,9 @@ def run_micro(args):
     ct3 = torch.randint(0, 1 << 40, (B, 3, g.nq, N), device="cuda", generator=gen)
     cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
     limbs = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
-    # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input)
-    for r in LC.rotations_of_schedule([1] * (g.log_n - 1)):
+    # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input),
+    # rotate-and-sum in 7 one-ModDown groups of 3 rotations (21 keys)
+    for r in LC.rotations_of_schedule(SCHEDULES["g2qp"]):
         if r != 1:
             evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
     rng = np.random.default_rng(5)
@@ -236,7 +238,8 @@ def run_micro(args):
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             g.profile_start()
-        g.distances(evk, dcts, 10, 8, g.scale, out=dout)
+        g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
+                    groups=SCHEDULES["g2qp"], out=dout)
         x = g.to_eval(limbs, g.L)
         g.to_coeff(x, g.L)
         r2 = g.relin(evk, ct3, g.L)

@@ -610,56 +610,73 @@ __global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64
 // writing the per-rotation products.  E_j is the j-th extended digit (own rows from d).  All
 // products of one output sum in 128 bits (T * beta < 64 terms below q^2 < 2^120) and reduce
 // once, so the result equals the per-rotation reduction exactly.
-// grid: x = tile of kT coefficients, y = row r of Q_l U P, z = group of kBT items.
-constexpr int kBT = 4;
+// perm_g maps the aligned pair {2m, 2m+1} onto an aligned pair {s, s^1} (the pair bit is the top
+// bit of the bit-reversed index, and X -> X^g adds an odd multiple of 2^(log_n-1) to it), so a
+// thread owns two coefficients and every gather is one 16-byte load plus a conditional swap.
+// grid: x = group of kBT items (fastest, so that consecutive blocks share the key tile in L2),
+// y = tile of 2 kTG coefficients, z = row r of Q_l U P.
+constexpr int kBT = 2;
+constexpr int kTG = 128;
+__device__ __forceinline__ ulonglong2 ld2_swap(const u64* p, unsigned s0, bool sw) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p + s0));
+    return sw ? make_ulonglong2(v.y, v.x) : v;
+}
 template <int T, bool ITEMS>
-__global__ void __launch_bounds__(kT) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+__global__ void __launch_bounds__(kTG) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
                                                      int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
                                                      Galois gs, const ModConst* __restrict__ mc,
                                                      u64* __restrict__ usum, u64* __restrict__ c0acc) {
     const size_t N = (size_t)1 << log_n;
-    const unsigned x = blockIdx.x * kT + threadIdx.x;
-    const int r = blockIdx.y;
-    const int b0 = blockIdx.z * kBT;
+    const unsigned x = (blockIdx.y * kTG + threadIdx.x) * 2;
+    const int r = blockIdx.z;
+    const int b0 = blockIdx.x * kBT;
     const int nb = min(kBT, B - b0);
     const int kt = r < nl ? r : nq + (r - nl);
     const ModConst& mcr = mc[kt];
     const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
-    unsigned src[T];
+    unsigned s0[T];
+    bool sw[T];
 #pragma unroll
-    for (int t = 0; t < T; t++) src[t] = auto_src(x, gs.g[t], log_n);
-    u128v a[kBT][2];
+    for (int t = 0; t < T; t++) {
+        const unsigned sv = auto_src(x, gs.g[t], log_n);
+        s0[t] = sv & ~1u;
+        sw[t] = sv & 1u;
+    }
+    // items past the end of the batch repeat the last one; their results are not stored
+    int bi[kBT];
 #pragma unroll
-    for (int i = 0; i < kBT; i++) a[i][0] = a[i][1] = u128v{0, 0};
+    for (int i = 0; i < kBT; i++) bi[i] = b0 + min(i, nb - 1);
+    u128v a[kBT][2][2];
+#pragma unroll
+    for (int i = 0; i < kBT; i++) a[i][0][0] = a[i][0][1] = a[i][1][0] = a[i][1][1] = u128v{0, 0};
     const size_t ka = (size_t)nqp * N;
     for (int j = 0; j < beta; j++) {
         const bool own = r < nl && r / alpha == j;
         const size_t ko = ((size_t)j * 2 * nqp + kt) * N;
 #pragma unroll
         for (int t = 0; t < T; t++) {
-            const unsigned s = src[t];
-            u64 k0 = 0, k1 = 0;
+            ulonglong2 k0, k1;
             if (!ITEMS) {
-                k0 = __ldg(keys.p[t] + ko + s);
-                k1 = __ldg(keys.p[t] + ko + ka + s);
+                k0 = ld2_swap(keys.p[t] + ko, s0[t], sw[t]);
+                k1 = ld2_swap(keys.p[t] + ko + ka, s0[t], sw[t]);
             }
 #pragma unroll
             for (int i = 0; i < kBT; i++) {
-                if (i < nb) {
-                    const int b = b0 + i;
-                    if (ITEMS) {
-                        const u64* kp = keys_dev[(size_t)b * T + t];
-                        k0 = __ldg(kp + ko + s);
-                        k1 = __ldg(kp + ko + ka + s);
-                    }
-                    const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
-                                       : ext + (((size_t)b * beta + j) * rows + r) * N;
-                    const u64 ev = __ldg(e + s);
-                    mac128(a[i][0], ev, k0);
-                    mac128(a[i][1], ev, k1);
+                const int b = bi[i];
+                if (ITEMS) {
+                    const u64* kp = keys_dev[(size_t)b * T + t];
+                    k0 = ld2_swap(kp + ko, s0[t], sw[t]);
+                    k1 = ld2_swap(kp + ko + ka, s0[t], sw[t]);
                 }
+                const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
+                                   : ext + (((size_t)b * beta + j) * rows + r) * N;
+                const ulonglong2 ev = ld2_swap(e, s0[t], sw[t]);
+                mac128(a[i][0][0], ev.x, k0.x);
+                mac128(a[i][0][1], ev.y, k0.y);
+                mac128(a[i][1][0], ev.x, k1.x);
+                mac128(a[i][1][1], ev.y, k1.y);
             }
         }
     }
@@ -668,14 +685,20 @@ __global__ void __launch_bounds__(kT) k_inner_gather(const u64* __restrict__ ext
         if (i < nb) {
             const int b = b0 + i;
             u64* ub = usum + ((size_t)b * 2 * rows + r) * N + x;
-            ub[0] = reduce128c(a[i][0], q, r64, r64sh, osh);
-            ub[(size_t)rows * N] = reduce128c(a[i][1], q, r64, r64sh, osh);
+            st2(ub, reduce128c(a[i][0][0], q, r64, r64sh, osh), reduce128c(a[i][0][1], q, r64, r64sh, osh));
+            st2(ub + (size_t)rows * N, reduce128c(a[i][1][0], q, r64, r64sh, osh),
+                reduce128c(a[i][1][1], q, r64, r64sh, osh));
             if (r < nl) {
                 const u64* yb = y0 + (size_t)b * y0_stride + ((size_t)r << log_n);
-                u64 acc = __ldg(yb + x);
+                const ulonglong2 self = ld2(yb + x);
+                u64 c0 = self.x, c1 = self.y;  // T + 1 < 16 terms below q < 2^60
 #pragma unroll
-                for (int t = 0; t < T; t++) acc += __ldg(yb + src[t]);  // T + 1 < 16 terms below q < 2^60
-                c0acc[((size_t)b * nl + r) * N + x] = reduce64(acc, mcr);
+                for (int t = 0; t < T; t++) {
+                    const ulonglong2 v = ld2_swap(yb, s0[t], sw[t]);
+                    c0 += v.x;
+                    c1 += v.y;
+                }
+                st2(c0acc + ((size_t)b * nl + r) * N + x, reduce64(c0, mcr), reduce64(c1, mcr));
             }
         }
     }
@@ -1013,7 +1036,7 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
                      u64* usum, u64* c0acc) {
     const int beta = c->digits(level);
     const int nl = level + 1, rows = nl + c->np;
-    dim3 grid((unsigned)(c->N / kT), rows, (unsigned)((B + kBT - 1) / kBT));
+    dim3 grid((unsigned)((B + kBT - 1) / kBT), (unsigned)(c->N / (2 * kTG)), rows);
     KeyPtrs kp{};
     Galois g{};
     for (int k = 0; k < T && k < 8; k++) {
@@ -1022,11 +1045,11 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
     }
 #define LC_IG(TT)                                                                                                    \
     if (keys_dev)                                                                                                    \
-        k_inner_gather<TT, true><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,     \
+        k_inner_gather<TT, true><<<grid, kTG, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,    \
                                                              c->alpha, c->nq, c->nq + c->np, c->log_n, kp, keys_dev, \
                                                              g, c->mc, usum, c0acc);                                 \
     else                                                                                                             \
-        k_inner_gather<TT, false><<<grid, kT, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,    \
+        k_inner_gather<TT, false><<<grid, kTG, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,   \
                                                               c->alpha, c->nq, c->nq + c->np, c->log_n, kp, nullptr, \
                                                               g, c->mc, usum, c0acc)
     switch (T) {
