@@ -16,6 +16,8 @@
  *    deferred device errors.  A context is used by one host thread at a time.
  *  - Ciphertext buffers are plain pointers in the layout [poly][limb][N] of uint64 words,
  *    limb i holding the residues mod q_i, in the library's evaluation ("NTT") domain.
+ *    Every word is a canonical residue in [0, q_i); the kernels rely on it (words outside
+ *    that range give unspecified results, never a fault).
  *    Batches are contiguous: [count][poly][limb][N].  Unless a parameter says "host or
  *    device", pointers to ciphertext words are device pointers owned by the caller.
  *    The canonical interchange form is the COEFFICIENT domain (lc_to_coeff / lc_to_eval):

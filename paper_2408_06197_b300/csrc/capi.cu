@@ -1264,8 +1264,10 @@ struct WaveBlob {
         return off;
     }
 };
+// (chunk and client counts are bounded far above any device memory so that the tensor kernels'
+// 64-bit partial sums cannot overflow)
 bool job_ok(lc_ctx* c, const lc_job& j, bool agg) {
-    if (!j.evk || !j.cts || j.chunks == 0) return false;
+    if (!j.evk || !j.cts || j.chunks == 0 || j.chunks >= (1u << 20) || j.n >= (1u << 21)) return false;
     if (agg) return j.n >= 1 && j.masks && j.out_agg;
     return j.n >= 2 && j.out_dist;
 }

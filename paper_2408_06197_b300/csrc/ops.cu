@@ -141,8 +141,6 @@ __global__ void __launch_bounds__(kT) k_sq_acc_pairs(const u64* __restrict__ cts
 constexpr int kTX = 32;
 constexpr int kStages = 4;
 constexpr int kMaxSlots = 16;                  // client slots staged per chunk (2 blocks of 8, or 11)
-constexpr int kWarps = kT / 32;                // 8 pair slots
-constexpr int kPPT = 8;                        // pairs per thread: 64 / 8 (and ceil(55 / 8) = 7)
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -152,9 +150,43 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N_>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_)); }
 
-__global__ void __launch_bounds__(kT, 2) k_sq_acc_tiled(const u64* __restrict__ cts, int n, int chunks, int nl,
-                                                        int log_n, int cb, int p0, int np,
-                                                        const ModConst* __restrict__ mc, u64* __restrict__ out) {
+// Exact sums of products of residues below 2^40 without 128-bit carry chains: each operand is
+// split into 20-bit halves (v = h 2^20 + l), each partial product is one 32x32 -> 64-bit
+// multiply-add, and the three weights (2^40, 2^20, 1) accumulate separately in 64 bits (each
+// term < 2^41, so up to 2^20 chunks cannot overflow).
+struct Acc3 {
+    u64 a, b, c;  // sum h h', sum (h l' + l h'), sum l l'
+};
+__device__ __forceinline__ void mac_split(Acc3& s, unsigned h, unsigned l, unsigned h2, unsigned l2) {
+    s.a += (u64)h * h2;
+    s.b += (u64)h * l2;
+    s.b += (u64)l * h2;
+    s.c += (u64)l * l2;
+}
+__device__ __forceinline__ void sq_split(Acc3& s, unsigned h, unsigned l) {  // b holds sum h l (doubled at the end)
+    s.a += (u64)h * h;
+    s.b += (u64)h * l;
+    s.c += (u64)l * l;
+}
+// a 2^40 + b 2^20 * bmul + c mod q
+__device__ __forceinline__ u64 acc3_reduce(const Acc3& s, int bshift, const ModConst& m) {
+    u128v v{s.c, 0};
+    add128(v, s.a << 40);
+    v.hi += s.a >> 24;
+    add128(v, s.b << bshift);
+    v.hi += s.b >> (64 - bshift);
+    return reduce128(v, m);
+}
+
+// WARPS warps, PPT pair slots per thread; SPLIT: the limbs' primes are below 2^40 (20-bit split
+// arithmetic), else 128-bit multiply-accumulate with a fold every 8 chunks.  Limb = limb0 + z.
+template <int WARPS, int PPT, bool SPLIT>
+__global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(const u64* __restrict__ cts, int n, int chunks,
+                                                                int nl, int limb0, int log_n, int cb, int p0, int np,
+                                                                const ModConst* __restrict__ mc,
+                                                                u64* __restrict__ out) {
+    constexpr int NT = WARPS * 32;
+    constexpr int UPT = (kMaxSlots * 2 * (kTX / 2) + NT - 1) / NT;  // 16-byte copy units per thread
     __shared__ __align__(16) u64 sh[kStages][kMaxSlots][2][kTX];
     const int nb = (n + cb - 1) / cb;
     int bp = blockIdx.x, I = 0;
@@ -168,18 +200,18 @@ __global__ void __launch_bounds__(kT, 2) k_sq_acc_tiled(const u64* __restrict__ 
     const bool diag = I == J;
     const int total = diag ? cntI * (cntI - 1) / 2 : cntI * cntJ;
     const int nslots = diag ? cntI : cntI + cntJ;
-    const int limb = blockIdx.z;
+    const int limb = limb0 + blockIdx.z;
     const size_t N = (size_t)1 << log_n;
     const int tid = threadIdx.x, x = tid & 31, warp = tid >> 5;
     const size_t x0 = (size_t)blockIdx.y * kTX;
     const ModConst m = mc[limb];
     const size_t P = (size_t)nl * N;
     // per pair: (output index << 8) | (slot a << 4) | slot b, or -1 when the pair is not owned
-    int pk[kPPT];
+    int pk[PPT];
     bool any = false;
 #pragma unroll
-    for (int k = 0; k < kPPT; k++) {
-        const int pi = warp + kWarps * k;
+    for (int k = 0; k < PPT; k++) {
+        const int pi = warp + WARPS * k;
         pk[k] = -1;
         int sa = 0, sb = 0;
         if (pi < total) {
@@ -209,14 +241,14 @@ __global__ void __launch_bounds__(kT, 2) k_sq_acc_tiled(const u64* __restrict__ 
         }
     }
     if (!__syncthreads_or(any)) return;
-    // 16-byte copy units: (client slot, poly, coefficient pair): 32 per slot, <= 512 -> 2 per thread
+    // 16-byte copy units: (client slot, poly, coefficient pair): 32 per slot, <= 512 in all
     const int units = nslots * 2 * (kTX / 2);
-    const u64* gsrc[2];
-    int ucs[2], upp[2], uxx[2];
-    bool ucopy[2];
+    const u64* gsrc[UPT];
+    int ucs[UPT], upp[UPT], uxx[UPT];
+    bool ucopy[UPT];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int u = tid + h * kT;
+    for (int h = 0; h < UPT; h++) {
+        const int u = tid + h * NT;
         ucopy[h] = u < units;
         ucs[h] = u / kTX;
         upp[h] = (u / (kTX / 2)) & 1;
@@ -228,91 +260,134 @@ __global__ void __launch_bounds__(kT, 2) k_sq_acc_tiled(const u64* __restrict__ 
 #pragma unroll
     for (int st = 0; st < kStages - 1; st++) {
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < UPT; h++)
             if (ucopy[h] && st < chunks) cp_async16(&sh[st][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)st * chunk_stride);
         cp_async_commit();
     }
-    u128v s00[kPPT], s01[kPPT], s11[kPPT];
+    Acc3 t00[SPLIT ? PPT : 1], t01[SPLIT ? PPT : 1], t11[SPLIT ? PPT : 1];
+    u128v s00[SPLIT ? 1 : PPT], s01[SPLIT ? 1 : PPT], s11[SPLIT ? 1 : PPT];
 #pragma unroll
-    for (int k = 0; k < kPPT; k++) s00[k] = s01[k] = s11[k] = u128v{0, 0};
+    for (int k = 0; k < PPT; k++) {
+        if (SPLIT)
+            t00[k] = t01[k] = t11[k] = Acc3{0, 0, 0};
+        else
+            s00[k] = s01[k] = s11[k] = u128v{0, 0};
+    }
     for (int k = 0; k < chunks; k++) {
         cp_async_wait<kStages - 2>();
         __syncthreads();
         {
             const int nk = k + kStages - 1;
 #pragma unroll
-            for (int h = 0; h < 2; h++)
+            for (int h = 0; h < UPT; h++)
                 if (ucopy[h] && nk < chunks)
                     cp_async16(&sh[nk % kStages][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)nk * chunk_stride);
             cp_async_commit();
         }
         const int cur = k % kStages;
 #pragma unroll
-        for (int t = 0; t < kPPT; t++) {
+        for (int t = 0; t < PPT; t++) {
             if (pk[t] < 0) continue;
             const int sa = (pk[t] >> 4) & 15, sb = pk[t] & 15;
             const u64 a0 = sh[cur][sa][0][x], a1 = sh[cur][sa][1][x];
             const u64 b0 = sh[cur][sb][0][x], b1 = sh[cur][sb][1][x];
             const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
-            mac128(s00[t], d0, d0);
-            mac128(s01[t], d0, d1);
-            mac128(s11[t], d1, d1);
-            if ((k & 7) == 7) {
-                fold(s00[t], m);
-                fold(s01[t], m);
-                fold(s11[t], m);
+            if (SPLIT) {
+                const unsigned h0 = (unsigned)(d0 >> 20), l0 = (unsigned)d0 & 0xFFFFFu;
+                const unsigned h1 = (unsigned)(d1 >> 20), l1 = (unsigned)d1 & 0xFFFFFu;
+                sq_split(t00[t], h0, l0);
+                mac_split(t01[t], h0, l0, h1, l1);
+                sq_split(t11[t], h1, l1);
+            } else {
+                mac128(s00[t], d0, d0);
+                mac128(s01[t], d0, d1);
+                mac128(s11[t], d1, d1);
+                if ((k & 7) == 7) {
+                    fold(s00[t], m);
+                    fold(s01[t], m);
+                    fold(s11[t], m);
+                }
             }
         }
     }
     cp_async_wait<0>();
 #pragma unroll
-    for (int t = 0; t < kPPT; t++) {
+    for (int t = 0; t < PPT; t++) {
         if (pk[t] < 0) continue;
         u64* o = out + (size_t)(pk[t] >> 8) * 3 * P + (size_t)limb * N + x0 + x;
-        o[0] = reduce128(s00[t], m);
-        const u64 d1 = reduce128(s01[t], m);
-        o[P] = add_mod(d1, d1, m.q);
-        o[2 * P] = reduce128(s11[t], m);
+        u64 r00, r01, r11;
+        if (SPLIT) {
+            r00 = acc3_reduce(t00[t], 21, m);
+            r01 = acc3_reduce(t01[t], 20, m);
+            r11 = acc3_reduce(t11[t], 21, m);
+        } else {
+            r00 = reduce128(s00[t], m);
+            r01 = reduce128(s01[t], m);
+            r11 = reduce128(s11[t], m);
+        }
+        o[0] = r00;
+        o[P] = add_mod(r01, r01, m.q);
+        o[2 * P] = r11;
     }
 }
 
 // grid: x = chunk (fastest; the masks are shared by every chunk), y = tile, z = limb
-__global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, int n, int chunks, int nl, int log_n,
-                                                 int k0, const u64* __restrict__ masks,
+template <bool SPLIT>
+__global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, int n, int chunks, int nl, int limb0,
+                                                 int log_n, int k0, const u64* __restrict__ masks,
                                                  const ModConst* __restrict__ mc, u64* __restrict__ out) {
     const int k = k0 + blockIdx.x;
-    const int limb = blockIdx.z;
+    const int limb = limb0 + blockIdx.z;
     const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
     const size_t N = (size_t)1 << log_n;
     const ModConst m = mc[limb];
     const size_t P = (size_t)nl * N;
     u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
+    Acc3 t00{0, 0, 0}, t01{0, 0, 0}, t11{0, 0, 0};
     for (int i = 0; i < n; i++) {
         const u64* a = cts + ((size_t)i * chunks + k) * 2 * P + (size_t)limb * N + x;
         const u64* w = masks + (size_t)i * 2 * P + (size_t)limb * N + x;
         const u64 a0 = __ldg(a), a1 = __ldg(a + P), m0 = __ldg(w), m1 = __ldg(w + P);
-        mac128(s00, a0, m0);
-        mac128(s01, a0, m1);
-        mac128(s01, a1, m0);
-        mac128(s11, a1, m1);
-        if ((i & 3) == 3) {
-            fold(s00, m);
-            fold(s01, m);
-            fold(s11, m);
+        if (SPLIT) {
+            const unsigned ah0 = (unsigned)(a0 >> 20), al0 = (unsigned)a0 & 0xFFFFFu;
+            const unsigned ah1 = (unsigned)(a1 >> 20), al1 = (unsigned)a1 & 0xFFFFFu;
+            const unsigned mh0 = (unsigned)(m0 >> 20), ml0 = (unsigned)m0 & 0xFFFFFu;
+            const unsigned mh1 = (unsigned)(m1 >> 20), ml1 = (unsigned)m1 & 0xFFFFFu;
+            mac_split(t00, ah0, al0, mh0, ml0);
+            mac_split(t01, ah0, al0, mh1, ml1);
+            mac_split(t01, ah1, al1, mh0, ml0);
+            mac_split(t11, ah1, al1, mh1, ml1);
+        } else {
+            mac128(s00, a0, m0);
+            mac128(s01, a0, m1);
+            mac128(s01, a1, m0);
+            mac128(s11, a1, m1);
+            if ((i & 3) == 3) {
+                fold(s00, m);
+                fold(s01, m);
+                fold(s11, m);
+            }
         }
     }
     u64* o = out + (size_t)blockIdx.x * 3 * P + (size_t)limb * N + x;
-    o[0] = reduce128(s00, m);
-    o[P] = reduce128(s01, m);
-    o[2 * P] = reduce128(s11, m);
+    if (SPLIT) {
+        o[0] = acc3_reduce(t00, 20, m);
+        o[P] = acc3_reduce(t01, 20, m);
+        o[2 * P] = acc3_reduce(t11, 20, m);
+    } else {
+        o[0] = reduce128(s00, m);
+        o[P] = reduce128(s01, m);
+        o[2 * P] = reduce128(s11, m);
+    }
 }
 
 // ---------------------------------------------------------------------------- multi-job items
 // tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
-__global__ void __launch_bounds__(kT) k_sq_acc_items(const PairItem* __restrict__ items, int nl, int log_n,
+template <bool SPLIT>
+__global__ void __launch_bounds__(kT) k_sq_acc_items(const PairItem* __restrict__ items, int nl, int limb0, int log_n,
                                                      const ModConst* __restrict__ mc, u64* __restrict__ out) {
     const PairItem it = items[blockIdx.x];
-    const int limb = blockIdx.z;
+    const int limb = limb0 + blockIdx.z;
     const size_t N = (size_t)1 << log_n;
     const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
     const ModConst m = mc[limb];
@@ -320,55 +395,78 @@ __global__ void __launch_bounds__(kT) k_sq_acc_items(const PairItem* __restrict_
     const u64* ai = it.a + (size_t)limb * N + x;
     const u64* aj = it.b + (size_t)limb * N + x;
     u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
+    Acc3 t00{0, 0, 0}, t01{0, 0, 0}, t11{0, 0, 0};
     for (int k = 0; k < it.chunks; k++) {
         const u64 a0 = __ldg(ai), a1 = __ldg(ai + P), b0 = __ldg(aj), b1 = __ldg(aj + P);
         ai += 2 * P;
         aj += 2 * P;
         const u64 x0 = sub_mod(a0, b0, m.q), x1 = sub_mod(a1, b1, m.q);
-        mac128(s00, x0, x0);
-        mac128(s01, x0, x1);
-        mac128(s11, x1, x1);
-        if ((k & 7) == 7) {
-            fold(s00, m);
-            fold(s01, m);
-            fold(s11, m);
+        if (SPLIT) {
+            const unsigned h0 = (unsigned)(x0 >> 20), l0 = (unsigned)x0 & 0xFFFFFu;
+            const unsigned h1 = (unsigned)(x1 >> 20), l1 = (unsigned)x1 & 0xFFFFFu;
+            sq_split(t00, h0, l0);
+            mac_split(t01, h0, l0, h1, l1);
+            sq_split(t11, h1, l1);
+        } else {
+            mac128(s00, x0, x0);
+            mac128(s01, x0, x1);
+            mac128(s11, x1, x1);
+            if ((k & 7) == 7) {
+                fold(s00, m);
+                fold(s01, m);
+                fold(s11, m);
+            }
         }
     }
     u64* o = out + (size_t)it.slot * 3 * P + (size_t)limb * N + x;
-    o[0] = reduce128(s00, m);
-    const u64 d1 = reduce128(s01, m);
+    const u64 d1 = SPLIT ? acc3_reduce(t01, 20, m) : reduce128(s01, m);
+    o[0] = SPLIT ? acc3_reduce(t00, 21, m) : reduce128(s00, m);
     o[P] = add_mod(d1, d1, m.q);
-    o[2 * P] = reduce128(s11, m);
+    o[2 * P] = SPLIT ? acc3_reduce(t11, 21, m) : reduce128(s11, m);
 }
 
 // masked accumulate of one chunk of one job per item.  grid: x = item, y = tile, z = limb
-__global__ void __launch_bounds__(kT) k_mask_acc_items(const AggItem* __restrict__ items, int nl, int log_n,
-                                                       const ModConst* __restrict__ mc, u64* __restrict__ out) {
+template <bool SPLIT>
+__global__ void __launch_bounds__(kT) k_mask_acc_items(const AggItem* __restrict__ items, int nl, int limb0,
+                                                       int log_n, const ModConst* __restrict__ mc,
+                                                       u64* __restrict__ out) {
     const AggItem it = items[blockIdx.x];
-    const int limb = blockIdx.z;
+    const int limb = limb0 + blockIdx.z;
     const size_t N = (size_t)1 << log_n;
     const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
     const ModConst m = mc[limb];
     const size_t P = (size_t)nl * N;
     u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
+    Acc3 t00{0, 0, 0}, t01{0, 0, 0}, t11{0, 0, 0};
     for (int i = 0; i < it.n; i++) {
         const u64* a = it.cts + ((size_t)i * it.chunks + it.k) * 2 * P + (size_t)limb * N + x;
         const u64* w = it.masks + (size_t)i * 2 * P + (size_t)limb * N + x;
         const u64 a0 = __ldg(a), a1 = __ldg(a + P), m0 = __ldg(w), m1 = __ldg(w + P);
-        mac128(s00, a0, m0);
-        mac128(s01, a0, m1);
-        mac128(s01, a1, m0);
-        mac128(s11, a1, m1);
-        if ((i & 3) == 3) {
-            fold(s00, m);
-            fold(s01, m);
-            fold(s11, m);
+        if (SPLIT) {
+            const unsigned ah0 = (unsigned)(a0 >> 20), al0 = (unsigned)a0 & 0xFFFFFu;
+            const unsigned ah1 = (unsigned)(a1 >> 20), al1 = (unsigned)a1 & 0xFFFFFu;
+            const unsigned mh0 = (unsigned)(m0 >> 20), ml0 = (unsigned)m0 & 0xFFFFFu;
+            const unsigned mh1 = (unsigned)(m1 >> 20), ml1 = (unsigned)m1 & 0xFFFFFu;
+            mac_split(t00, ah0, al0, mh0, ml0);
+            mac_split(t01, ah0, al0, mh1, ml1);
+            mac_split(t01, ah1, al1, mh0, ml0);
+            mac_split(t11, ah1, al1, mh1, ml1);
+        } else {
+            mac128(s00, a0, m0);
+            mac128(s01, a0, m1);
+            mac128(s01, a1, m0);
+            mac128(s11, a1, m1);
+            if ((i & 3) == 3) {
+                fold(s00, m);
+                fold(s01, m);
+                fold(s11, m);
+            }
         }
     }
     u64* o = out + (size_t)it.slot * 3 * P + (size_t)limb * N + x;
-    o[0] = reduce128(s00, m);
-    o[P] = reduce128(s01, m);
-    o[2 * P] = reduce128(s11, m);
+    o[0] = SPLIT ? acc3_reduce(t00, 20, m) : reduce128(s00, m);
+    o[P] = SPLIT ? acc3_reduce(t01, 20, m) : reduce128(s01, m);
+    o[2 * P] = SPLIT ? acc3_reduce(t11, 20, m) : reduce128(s11, m);
 }
 
 // words-per-item copy to per-item destinations.  grid: x = chunk of 2*kT words, y = item
@@ -954,18 +1052,48 @@ void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     g_lc_launches += 1;
 }
 
+// first limb of the range [split0, nl) whose primes are all below 2^40 (20-bit split products)
+static int split_start(lc_ctx* c, int nl) {
+    int s0 = nl;
+    while (s0 > 0 && c->mod[s0 - 1] < (1ull << 40)) s0--;
+    return s0;
+}
+
 void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p0, int np, u64* out) {
     const int cb = n <= 11 ? n : 8;  // one diagonal block up to 11 clients (55 pairs), else blocks of 8
     const int nb = (n + cb - 1) / cb;
-    dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), nl);
-    k_sq_acc_tiled<<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, c->log_n, cb, p0, np, c->mc, out);
-    g_lc_launches += 1;
+    // limbs [split0, nl) take the 20-bit split path (partial sums stay below 2^64 for < 2^20 chunks)
+    int split0 = split_start(c, nl);
+    if (chunks > (1 << 20)) split0 = nl;
+    if (split0 > 0) {
+        dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), split0);
+        k_sq_acc_tiled<8, 8, false><<<grid, 256, 0, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, cb, p0, np, c->mc,
+                                                                  out);
+        g_lc_launches += 1;
+    }
+    if (split0 < nl) {
+        dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), nl - split0);
+        k_sq_acc_tiled<16, 4, true><<<grid, 512, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0, np,
+                                                                  c->mc, out);
+        g_lc_launches += 1;
+    }
 }
 
 void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64* masks, int k0, int nk, u64* out) {
-    dim3 grid(nk, (unsigned)(c->N / kT), nl);
-    k_mask_acc<<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, c->log_n, k0, masks, c->mc, out);
-    g_lc_launches += 1;
+    // limbs [split0, nl): 20-bit split products (sum (h l' + l h') of n clients stays below 2^64
+    // for n < 2^21)
+    int split0 = split_start(c, nl);
+    if (n >= (1 << 21)) split0 = nl;
+    if (split0 > 0) {
+        dim3 grid(nk, (unsigned)(c->N / kT), split0);
+        k_mask_acc<false><<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, k0, masks, c->mc, out);
+        g_lc_launches += 1;
+    }
+    if (split0 < nl) {
+        dim3 grid(nk, (unsigned)(c->N / kT), nl - split0);
+        k_mask_acc<true><<<grid, kT, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, k0, masks, c->mc, out);
+        g_lc_launches += 1;
+    }
 }
 
 void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext) {
@@ -1198,16 +1326,32 @@ void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods, int nrow
 
 void op_sq_acc_items(lc_ctx* c, const PairItem* items_dev, int count, int nl, u64* out) {
     if (count <= 0) return;
-    dim3 grid(count, (unsigned)(c->N / kT), nl);
-    k_sq_acc_items<<<grid, kT, 0, c->stream>>>(items_dev, nl, c->log_n, c->mc, out);
-    g_lc_launches += 1;
+    const int s0 = split_start(c, nl);  // an item's chunks (< 2^20) fit the 64-bit partial sums
+    if (s0 > 0) {
+        dim3 grid(count, (unsigned)(c->N / kT), s0);
+        k_sq_acc_items<false><<<grid, kT, 0, c->stream>>>(items_dev, nl, 0, c->log_n, c->mc, out);
+        g_lc_launches += 1;
+    }
+    if (s0 < nl) {
+        dim3 grid(count, (unsigned)(c->N / kT), nl - s0);
+        k_sq_acc_items<true><<<grid, kT, 0, c->stream>>>(items_dev, nl, s0, c->log_n, c->mc, out);
+        g_lc_launches += 1;
+    }
 }
 
 void op_mask_acc_items(lc_ctx* c, const AggItem* items_dev, int count, int nl, u64* out) {
     if (count <= 0) return;
-    dim3 grid(count, (unsigned)(c->N / kT), nl);
-    k_mask_acc_items<<<grid, kT, 0, c->stream>>>(items_dev, nl, c->log_n, c->mc, out);
-    g_lc_launches += 1;
+    const int s0 = split_start(c, nl);  // a job's clients (< 2^21) fit the 64-bit partial sums
+    if (s0 > 0) {
+        dim3 grid(count, (unsigned)(c->N / kT), s0);
+        k_mask_acc_items<false><<<grid, kT, 0, c->stream>>>(items_dev, nl, 0, c->log_n, c->mc, out);
+        g_lc_launches += 1;
+    }
+    if (s0 < nl) {
+        dim3 grid(count, (unsigned)(c->N / kT), nl - s0);
+        k_mask_acc_items<true><<<grid, kT, 0, c->stream>>>(items_dev, nl, s0, c->log_n, c->mc, out);
+        g_lc_launches += 1;
+    }
 }
 
 void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level,
