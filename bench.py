@@ -204,8 +204,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- kernel micro case
 def run_micro(args):
     """Small isolated case for profiler captures (about 4 GB on the device, inputs larger than
-    L2): batched distances of 10 clients x 8 chunks (45 pairs, one-ModDown rotation groups), 960
-    limbs transformed forward and
+    L2): batched distances of 10 clients x 8 chunks (45 pairs, one-ModDown rotation groups) and
+    their masked aggregate (8 chunks), 960 limbs transformed forward and
     back, 16 degree-2 triples relinearised and rescaled at level 14, and 16 ciphertexts rotated
     at level 13.  Prints per-class timings."""
     import torch
@@ -233,13 +233,19 @@ def run_micro(args):
     for i, q in enumerate(g.q):
         dc[:, :, :, i] = rng.integers(0, q, size=(10, 8, 2, N), dtype=np.uint64)
     dcts = LC.u64_to_torch(dc)
-    del dc
+    dm = np.empty((10, 2, g.nq, N), dtype=np.uint64)
+    for i, q in enumerate(g.q):
+        dm[:, :, i] = rng.integers(0, q, size=(10, 2, N), dtype=np.uint64)
+    dmasks = LC.u64_to_torch(dm)
+    del dc, dm
     dout = g.empty(45, 2, g.L, N)
+    aout = g.empty(8, 2, g.L, N)
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             g.profile_start()
         g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
                     groups=SCHEDULES["g2qp"], out=dout)
+        g.masked_aggregate(evk, dcts, 10, 8, g.scale, dmasks, g.scale, out=aout)
         x = g.to_eval(limbs, g.L)
         g.to_coeff(x, g.L)
         r2 = g.relin(evk, ct3, g.L)
