@@ -98,6 +98,11 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload (GPU)
 SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7}
 
+# DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture of the
+# 960-limb case of `bench.py --micro` (profiles/ntt_micro_960limbs.md): forward 443.7 + 453.9 MB,
+# inverse 453.5 + 443.8 MB per 960 limbs.  Valid for the current ntt.cu only.
+NTT_DRAM_BYTES_PER_LIMB = (443.7e6 + 453.9e6 + 453.5e6 + 443.8e6) / (2 * 960)
+
 
 def build_workload(LC, g, w: S.Workload, sched_name: str = "g2qp"):
     N = g.N
@@ -222,7 +227,7 @@ def run_micro(args):
     gen = torch.Generator(device="cuda").manual_seed(7)
     ct3 = torch.randint(0, 1 << 40, (B, 3, g.nq, N), device="cuda", generator=gen)
     cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
-    limbs = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
+    xl = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
     # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input),
     # rotate-and-sum in 7 one-ModDown groups of 3 rotations (21 keys)
     for r in LC.rotations_of_schedule(SCHEDULES["g2qp"]):
@@ -240,18 +245,30 @@ def run_micro(args):
     del dc, dm
     dout = g.empty(45, 2, g.L, N)
     aout = g.empty(8, 2, g.L, N)
+    nvtx = torch.cuda.nvtx
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             g.profile_start()
+        # NVTX ranges name the phases for profiler filters (ncu --nvtx --nvtx-include "ntt/")
+        nvtx.range_push("distances")
         g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
                     groups=SCHEDULES["g2qp"], out=dout)
+        nvtx.range_pop()
+        nvtx.range_push("aggregate")
         g.masked_aggregate(evk, dcts, 10, 8, g.scale, dmasks, g.scale, out=aout)
-        x = g.to_eval(limbs, g.L)
-        g.to_coeff(x, g.L)
+        nvtx.range_pop()
+        nvtx.range_push("ntt")  # 960 limbs forward then inverse, in place
+        g.to_eval(xl, g.L, inplace=True)
+        g.to_coeff(xl, g.L, inplace=True)
+        nvtx.range_pop()
+        nvtx.range_push("relin_rescale")
         r2 = g.relin(evk, ct3, g.L)
         g.rescale(r2, g.L)
+        nvtx.range_pop()
+        nvtx.range_push("rotate")
         for b in range(B):
             g.rotate(evk, cts[b], g.L - 1, [1])
+        nvtx.range_pop()
     prof = g.profile_stop()
     print(json.dumps({"micro": {k: {"ms_per_iter": v["ms"] / args.steps, "GBps": v["bytes"] / v["ms"] / 1e6
                                     if v["ms"] else 0.0, "launches_per_iter": v["launches"] / args.steps}
@@ -388,6 +405,9 @@ def main():
         run_micro(args)
         return
     if args.serving:
+        # rounds of 0.1-75 GiB come and go: let the caching allocator grow segments instead of
+        # fragmenting the device into blocks too small for the next large round
+        os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
         run_serving(args)
         return
 
@@ -527,8 +547,16 @@ def main():
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic = None
+    if dom == "ntt" and d["launches"]:
+        # one "launch" = one batched transform call (column + row pass); algorithmic bytes are
+        # 2 N 8 per limb, so limbs per call = bytes / (16 N) / calls
+        limbs_per_call = d["bytes"] / (16.0 * g.N) / d["launches"]
+        traffic = NTT_DRAM_BYTES_PER_LIMB * limbs_per_call
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+            "frac": achieved / hbm, "peak_source": peak_kind, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes of the 960-limb transform case, per limb x limbs per call"
+            if traffic else None,
             "launches": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(1, d["launches"]),
             "share_of_step": d["ms"] / (ms if not use_graph else sum(v["ms"] for v in prof.values()) or 1.0),
             "measured_in": "timed region with per-launch CUDA events" + (" (eager replay of the graph's steps)"

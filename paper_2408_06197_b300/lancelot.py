@@ -423,15 +423,19 @@ class Context:
         return self.decode(m, scale)
 
     # ------------------------------------------------------------------ interchange
-    def to_coeff(self, data: torch.Tensor, level: int) -> torch.Tensor:
-        x = data.clone().contiguous()
+    def to_coeff(self, data: torch.Tensor, level: int, inplace: bool = False) -> torch.Tensor:
+        """Evaluation -> coefficient domain; a copy unless `inplace` (then `data` must be contiguous)."""
+        x = data if inplace else data.clone().contiguous()
         n_polys = _whole(x, (level + 1) * self.N, "to_coeff")
+        _need(x, n_polys * (level + 1) * self.N, "to_coeff")
         self._check(lib().lc_to_coeff(self.h, _t_ptr(x), n_polys, level), "lc_to_coeff")
         return x
 
-    def to_eval(self, data: torch.Tensor, level: int) -> torch.Tensor:
-        x = data.clone().contiguous()
+    def to_eval(self, data: torch.Tensor, level: int, inplace: bool = False) -> torch.Tensor:
+        """Coefficient -> evaluation domain; a copy unless `inplace` (then `data` must be contiguous)."""
+        x = data if inplace else data.clone().contiguous()
         n_polys = _whole(x, (level + 1) * self.N, "to_eval")
+        _need(x, n_polys * (level + 1) * self.N, "to_eval")
         self._check(lib().lc_to_eval(self.h, _t_ptr(x), n_polys, level), "lc_to_eval")
         return x
 

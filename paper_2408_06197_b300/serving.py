@@ -74,8 +74,12 @@ class Server:
     def __init__(self, ctx: "LC.Context", tenants: Sequence[Tenant], budget_bytes: float,
                  ingest: Callable[[Round], torch.Tensor],
                  mask_rand: Callable[[Round, int], tuple],
-                 groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM):
+                 groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM,
+                 keep_outputs: bool = False):
+        """keep_outputs: keep each finished round's device buffers (distances, masks, aggregate) on
+        its Job; otherwise they are released as soon as the round no longer needs them."""
         self.ctx, self.tenants, self.budget = ctx, list(tenants), float(budget_bytes)
+        self.keep = keep_outputs
         self.ingest, self.mask_rand = ingest, mask_rand
         self.groups = list(groups) if groups else [2] * ((ctx.log_n - 1) // 2) + [1] * ((ctx.log_n - 1) % 2)
         self.flags = flags
@@ -127,6 +131,8 @@ class Server:
                 d[i, j] = d[j, i] = vals[k]
                 k += 1
         r.distances = d
+        if not self.keep:
+            r.job.out_dist = None  # the KGC has read the distances out
         r.selected = kgc.krum_select(d, r.f, r.n_select)
         w = kgc.mask_weights(r.n, r.selected, average=r.average)
         m = np.zeros((r.n, c.N), dtype=np.int64)
@@ -153,8 +159,10 @@ class Server:
                 self.active.remove(r)
                 self.done.append(r)
                 self.used -= self.footprint(r)
-                r.cts = None  # the ciphertexts leave the device; outputs stay with the round
+                r.cts = None  # the round's ciphertexts leave the device
                 r.job.cts = None
+                if not self.keep:
+                    r.job.masks = r.job.out_agg = None
         if dist:
             LC.batch_distances(self.ctx, [r.job for r in dist], LC.LC_MODE_BATCHED | self.flags, self.groups)
             self.stats["distance_batches"] += 1

@@ -102,7 +102,7 @@ class _Feed:
     def server(self, budget):
         return self.SV.Server(self.env.g, self.tenants, budget, ingest=lambda r: self.cts[r.rid].clone(),
                               mask_rand=lambda r, i: S.enc_rand(3, S.CFG_SERVING, i, S.MASK_CHUNK, self.env.N,
-                                                                job=r.rid), groups=SCHED)
+                                                                job=r.rid), groups=SCHED, keep_outputs=True)
 
 
 @pytest.fixture(scope="module")
