@@ -96,7 +96,7 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- workload (GPU)
-SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7}
+SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7, "g3qp": [3, 3, 3, 3, 2]}
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture of the
 # 960-limb case of `bench.py --micro` (profiles/ntt_micro_960limbs.md): forward 443.7 + 453.9 MB,
@@ -209,7 +209,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- kernel micro case
 def run_micro(args):
     """Small isolated case for profiler captures (about 4 GB on the device, inputs larger than
-    L2): batched distances of 10 clients x 8 chunks (45 pairs, one-ModDown rotation groups) and
+    L2): batched distances of 10 clients x 8 chunks (45 pairs, rotation schedule --schedule) and
     their masked aggregate (8 chunks), 960 limbs transformed forward and
     back, 16 degree-2 triples relinearised and rescaled at level 14, and 16 ciphertexts rotated
     at level 13.  Prints per-class timings."""
@@ -229,8 +229,10 @@ def run_micro(args):
     cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
     xl = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
     # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input),
-    # rotate-and-sum in 7 one-ModDown groups of 3 rotations (21 keys)
-    for r in LC.rotations_of_schedule(SCHEDULES["g2qp"]):
+    # rotate-and-sum in one-ModDown groups of the chosen schedule
+    sched = SCHEDULES[args.schedule]
+    qpf = LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0
+    for r in LC.rotations_of_schedule(sched):
         if r != 1:
             evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
     rng = np.random.default_rng(5)
@@ -251,8 +253,7 @@ def run_micro(args):
             g.profile_start()
         # NVTX ranges name the phases for profiler filters (ncu --nvtx --nvtx-include "ntt/")
         nvtx.range_push("distances")
-        g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
-                    groups=SCHEDULES["g2qp"], out=dout)
+        g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | qpf, groups=sched, out=dout)
         nvtx.range_pop()
         nvtx.range_push("aggregate")
         g.masked_aggregate(evk, dcts, 10, 8, g.scale, dmasks, g.scale, out=aout)
@@ -276,11 +277,8 @@ def run_micro(args):
 
 
 # ----------------------------------------------------------------------------- serving
-SERVING_SCHED = [2] * 7
-
-
-def build_serving(LC, g, tenants: int, seed: int = 3, honest: int = 48, byz: int = 16):
-    """Tenants with resident keys (relin + 21 rotation keys of the one-ModDown schedule) and, per
+def build_serving(LC, g, tenants: int, sched, seed: int = 3, honest: int = 48, byz: int = 16):
+    """Tenants with resident keys (relin + the rotation keys of the schedule) and, per
     tenant, a device pool of encrypted update chunks (`honest` draws of N(0, 0.01^2) per slot and
     `byz` draws scaled by 5) from which arriving rounds are assembled."""
     import torch
@@ -294,7 +292,7 @@ def build_serving(LC, g, tenants: int, seed: int = 3, honest: int = 48, byz: int
         pk = g.pk_gen(s, pa, pe)
         evk = g.evk()
         evk.add(s, None, *S.swk_rand(seed, S.CFG_SERVING, qp, g.dnum, N, None, job=t))
-        for r in LC.rotations_of_schedule(SERVING_SCHED):
+        for r in LC.rotations_of_schedule(sched):
             evk.add(s, r, *S.swk_rand(seed, S.CFG_SERVING, qp, g.dnum, N, r, job=t))
         vals = [S.rng(seed, S.CFG_SERVING, t, i, 0, S.P_UPDATE).normal(0.0, 0.01, slots) for i in range(honest + byz)]
         vals = [v * (5.0 if i >= honest else 1.0) for i, v in enumerate(vals)]
@@ -320,7 +318,9 @@ def run_serving(args):
     honest, byz = 48, 16
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=local, stream=stream)
-        ten = build_serving(LC, g, args.tenants, honest=honest, byz=byz)
+        sched = SCHEDULES[args.schedule]
+        flags = LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0
+        ten = build_serving(LC, g, args.tenants, sched, honest=honest, byz=byz)
         tenants = [t for t, _ in ten]
         pools = [p for _, p in ten]
 
@@ -348,11 +348,12 @@ def run_serving(args):
 
         # warm-up: a few rounds of every size class, untimed
         warm = rounds_of(S.serving_rounds(seed=4, n_rounds=args.warmup, rate=1e9, tenants=args.tenants))
-        SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=SERVING_SCHED).run(warm, realtime=False)
+        SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags).run(
+            warm, realtime=False)
         torch.cuda.synchronize()
         for rate in [float(x) for x in args.rates.split(",")]:
             rounds = rounds_of(S.serving_rounds(seed=3, n_rounds=args.rounds, rate=rate, tenants=args.tenants))
-            srv = SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=SERVING_SCHED)
+            srv = SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags)
             clocks = Clocks(local)
             clocks.start()
             l0 = LC.launches()
@@ -370,7 +371,7 @@ def run_serving(args):
                     "clocks": ck, "dtype": "u64", "data": "synthetic",
                     "config": {"workload": "serving_N32768_4tenants_n{5,10,20,40}_d{2^16..2^22}_poisson",
                                "tenants": args.tenants, "budget_gb": args.budget_gb,
-                               "rotation_schedule": "g2qp", "seed": 3}}
+                               "rotation_schedule": args.schedule, "seed": 3}}
             print(json.dumps(line), flush=True)
 
 
@@ -381,9 +382,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mode", choices=["batched", "perop"], default="batched")
-    ap.add_argument("--schedule", choices=sorted(SCHEDULES), default="g2qp",
+    ap.add_argument("--schedule", choices=sorted(SCHEDULES), default="g3qp",
                     help="rotate-and-sum hoisting: log = 14 single rotations; g2qp = 7 groups of 3 rotations "
-                         "with one ModDown per group (21 rotation keys)")
+                         "with one ModDown per group (21 rotation keys); g3qp = 4 groups of 7 + 1 of 3 (31 keys)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -425,7 +426,7 @@ def main():
         g = LC.Context.production(device=local, stream=stream)
         evk, cts, masks, sched, s = build_workload(LC, g, w, args.schedule)
         mode = LC.LC_MODE_BATCHED if args.mode == "batched" else LC.LC_MODE_PER_OP
-        dmode = mode | (LC.LC_HOIST_QP_SUM if args.schedule == "g2qp" else 0)
+        dmode = mode | (LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0)
         out_d = g.empty(w.n_pairs, 2, g.L, g.N)
         out_a = g.empty(w.chunks, 2, g.L, g.N)
 

@@ -472,7 +472,7 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
             if (!keys[t - 1]) return fail(c, LC_EKEY, "rotation key " + std::to_string(t * stride) + " missing");
         }
         ks_modup(c, y + P, 2 * P, B, level, kb);
-        if (qp_sum && cnt > 1) {
+        if (qp_sum && cnt > 1 && cnt <= 7) {  // the fused group kernel takes up to 7 rotations
             const size_t vsz = (size_t)B * 2 * rows * N;
             u64* usum = wbase;      // [B][2][rows][N]
             u64* c0acc = usum + vsz;  // [B][nl][N]

@@ -713,22 +713,37 @@ __global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64
 // thread owns two coefficients and every gather is one 16-byte load plus a conditional swap.
 // grid: x = group of kBT items (fastest, so that consecutive blocks share the key tile in L2),
 // y = tile of 2 kTG coefficients, z = row r of Q_l U P.
-constexpr int kBT = 2;
 constexpr int kTG = 128;
+#ifndef LC_IG_BT_SPLIT
+#define LC_IG_BT_SPLIT 1
+#endif
+#ifndef LC_IG_BT_WIDE
+#define LC_IG_BT_WIDE 2
+#endif
+#ifndef LC_IG_MINB_SPLIT
+#define LC_IG_MINB_SPLIT 5
+#endif
 __device__ __forceinline__ ulonglong2 ld2_swap(const u64* p, unsigned s0, bool sw) {
     const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p + s0));
     return sw ? make_ulonglong2(v.y, v.x) : v;
 }
-template <int T, bool ITEMS>
-__global__ void __launch_bounds__(kTG) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+// the rows (of Q_l U P) one launch covers: [a0, a0 + na) then [b0, ...), in blockIdx.z order
+struct RowSel {
+    int a0, na, b0;
+};
+// SPLIT: every selected row's prime is below 2^40, so digits and keys split into 20-bit halves
+// (four 32x32 -> 64-bit products per 128-bit product, three 64-bit partial sums)
+template <int T, bool ITEMS, bool SPLIT, int kBT>
+__global__ void __launch_bounds__(kTG, SPLIT ? LC_IG_MINB_SPLIT : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
                                                      int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
-                                                     Galois gs, const ModConst* __restrict__ mc,
+                                                     Galois gs, RowSel sel, const ModConst* __restrict__ mc,
                                                      u64* __restrict__ usum, u64* __restrict__ c0acc) {
     const size_t N = (size_t)1 << log_n;
     const unsigned x = (blockIdx.y * kTG + threadIdx.x) * 2;
-    const int r = blockIdx.z;
+    const int z = blockIdx.z;
+    const int r = z < sel.na ? sel.a0 + z : sel.b0 + (z - sel.na);
     const int b0 = blockIdx.x * kBT;
     const int nb = min(kBT, B - b0);
     const int kt = r < nl ? r : nq + (r - nl);
@@ -746,9 +761,15 @@ __global__ void __launch_bounds__(kTG) k_inner_gather(const u64* __restrict__ ex
     int bi[kBT];
 #pragma unroll
     for (int i = 0; i < kBT; i++) bi[i] = b0 + min(i, nb - 1);
-    u128v a[kBT][2][2];
+    u128v a[SPLIT ? 1 : kBT][2][2];
+    Acc3 h[SPLIT ? kBT : 1][2][2];
 #pragma unroll
-    for (int i = 0; i < kBT; i++) a[i][0][0] = a[i][0][1] = a[i][1][0] = a[i][1][1] = u128v{0, 0};
+    for (int i = 0; i < kBT; i++) {
+        if (SPLIT)
+            h[i][0][0] = h[i][0][1] = h[i][1][0] = h[i][1][1] = Acc3{0, 0, 0};
+        else
+            a[i][0][0] = a[i][0][1] = a[i][1][0] = a[i][1][1] = u128v{0, 0};
+    }
     const size_t ka = (size_t)nqp * N;
     for (int j = 0; j < beta; j++) {
         const bool own = r < nl && r / alpha == j;
@@ -771,10 +792,19 @@ __global__ void __launch_bounds__(kTG) k_inner_gather(const u64* __restrict__ ex
                 const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
                                    : ext + (((size_t)b * beta + j) * rows + r) * N;
                 const ulonglong2 ev = ld2_swap(e, s0[t], sw[t]);
-                mac128(a[i][0][0], ev.x, k0.x);
-                mac128(a[i][0][1], ev.y, k0.y);
-                mac128(a[i][1][0], ev.x, k1.x);
-                mac128(a[i][1][1], ev.y, k1.y);
+                if (SPLIT) {
+                    const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
+                    const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
+                    mac_split(h[i][0][0], exh, exl, (unsigned)(k0.x >> 20), (unsigned)k0.x & 0xFFFFFu);
+                    mac_split(h[i][0][1], eyh, eyl, (unsigned)(k0.y >> 20), (unsigned)k0.y & 0xFFFFFu);
+                    mac_split(h[i][1][0], exh, exl, (unsigned)(k1.x >> 20), (unsigned)k1.x & 0xFFFFFu);
+                    mac_split(h[i][1][1], eyh, eyl, (unsigned)(k1.y >> 20), (unsigned)k1.y & 0xFFFFFu);
+                } else {
+                    mac128(a[i][0][0], ev.x, k0.x);
+                    mac128(a[i][0][1], ev.y, k0.y);
+                    mac128(a[i][1][0], ev.x, k1.x);
+                    mac128(a[i][1][1], ev.y, k1.y);
+                }
             }
         }
     }
@@ -783,9 +813,14 @@ __global__ void __launch_bounds__(kTG) k_inner_gather(const u64* __restrict__ ex
         if (i < nb) {
             const int b = b0 + i;
             u64* ub = usum + ((size_t)b * 2 * rows + r) * N + x;
-            st2(ub, reduce128c(a[i][0][0], q, r64, r64sh, osh), reduce128c(a[i][0][1], q, r64, r64sh, osh));
-            st2(ub + (size_t)rows * N, reduce128c(a[i][1][0], q, r64, r64sh, osh),
-                reduce128c(a[i][1][1], q, r64, r64sh, osh));
+            if (SPLIT) {
+                st2(ub, acc3_reduce(h[i][0][0], 20, mcr), acc3_reduce(h[i][0][1], 20, mcr));
+                st2(ub + (size_t)rows * N, acc3_reduce(h[i][1][0], 20, mcr), acc3_reduce(h[i][1][1], 20, mcr));
+            } else {
+                st2(ub, reduce128c(a[i][0][0], q, r64, r64sh, osh), reduce128c(a[i][0][1], q, r64, r64sh, osh));
+                st2(ub + (size_t)rows * N, reduce128c(a[i][1][0], q, r64, r64sh, osh),
+                    reduce128c(a[i][1][1], q, r64, r64sh, osh));
+            }
             if (r < nl) {
                 const u64* yb = y0 + (size_t)b * y0_stride + ((size_t)r << log_n);
                 const ulonglong2 self = ld2(yb + x);
@@ -1164,34 +1199,53 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
                      u64* usum, u64* c0acc) {
     const int beta = c->digits(level);
     const int nl = level + 1, rows = nl + c->np;
-    dim3 grid((unsigned)((B + kBT - 1) / kBT), (unsigned)(c->N / (2 * kTG)), rows);
     KeyPtrs kp{};
     Galois g{};
     for (int k = 0; k < T && k < 8; k++) {
         kp.p[k] = keys ? keys[k] : nullptr;
         g.g[k] = gs[k];
     }
-#define LC_IG(TT)                                                                                                    \
-    if (keys_dev)                                                                                                    \
-        k_inner_gather<TT, true><<<grid, kTG, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,    \
-                                                             c->alpha, c->nq, c->nq + c->np, c->log_n, kp, keys_dev, \
-                                                             g, c->mc, usum, c0acc);                                 \
-    else                                                                                                             \
-        k_inner_gather<TT, false><<<grid, kTG, 0, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows,   \
-                                                              c->alpha, c->nq, c->nq + c->np, c->log_n, kp, nullptr, \
-                                                              g, c->mc, usum, c0acc)
-    switch (T) {
-        case 1: LC_IG(1); break;
-        case 2: LC_IG(2); break;
-        case 3: LC_IG(3); break;
-        case 4: LC_IG(4); break;
-        case 5: LC_IG(5); break;
-        case 6: LC_IG(6); break;
-        case 7: LC_IG(7); break;
-        default: break;
+    // Q rows [k, nl) whose primes are all below 2^40 take the split-product kernel; rows [0, k)
+    // and the special primes take the 128-bit one
+    int k = nl;
+    while (k > 0 && c->mod[k - 1] < (1ull << 40)) k--;
+    const RowSel split{k, nl - k, 0}, wide{0, k, nl};
+    const int ns = nl - k, nw = k + c->np;
+    const unsigned gy = (unsigned)(c->N / (2 * kTG));
+#define LC_IG(TT, SPL, SEL, CNT)                                                                                    \
+    {                                                                                                               \
+        constexpr int BT = SPL ? LC_IG_BT_SPLIT : LC_IG_BT_WIDE;                                                    \
+        const dim3 grid((unsigned)((B + BT - 1) / BT), gy, CNT);                                                    \
+        if (keys_dev)                                                                                               \
+            k_inner_gather<TT, true, SPL, BT><<<grid, kTG, 0, c->stream>>>(                                         \
+                ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
+                keys_dev, g, SEL, c->mc, usum, c0acc);                                                              \
+        else                                                                                                        \
+            k_inner_gather<TT, false, SPL, BT><<<grid, kTG, 0, c->stream>>>(                                        \
+                ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
+                nullptr, g, SEL, c->mc, usum, c0acc);                                                               \
     }
+#define LC_IG_T(SPL, SEL, CNT)          \
+    switch (T) {                        \
+        case 1: LC_IG(1, SPL, SEL, CNT); break; \
+        case 2: LC_IG(2, SPL, SEL, CNT); break; \
+        case 3: LC_IG(3, SPL, SEL, CNT); break; \
+        case 4: LC_IG(4, SPL, SEL, CNT); break; \
+        case 5: LC_IG(5, SPL, SEL, CNT); break; \
+        case 6: LC_IG(6, SPL, SEL, CNT); break; \
+        case 7: LC_IG(7, SPL, SEL, CNT); break; \
+        default: break;                 \
+    }
+    if (ns) {
+        LC_IG_T(true, split, ns)
+        g_lc_launches += 1;
+    }
+    if (nw) {
+        LC_IG_T(false, wide, nw)
+        g_lc_launches += 1;
+    }
+#undef LC_IG_T
 #undef LC_IG
-    g_lc_launches += 1;
 }
 
 void op_gather_sum_qp(lc_ctx* c, const u64* src, size_t src_stride, u64* usum, int n_polys, int nl,

@@ -170,6 +170,26 @@ def test_qp_sum_hoisting_bit_exact_toy(toy):
     assert np.array_equal(toy.g_coeff(yg, toy.L), toy.o_coeff(yo))
 
 
+def test_qp_sum_groups_of_seven_bit_exact_toy():
+    """One-ModDown groups of 7 rotations ([3, 3, 3, 2] at 2^11 slots): the fused group kernel at
+    its largest size, against the oracle, for a single ciphertext and for batched distances."""
+    sched = [3, 3, 3, 2]
+    e = Env("toy", 11, S.CFG_TOY, extra_rot=O.rotations_of_schedule(sched))
+    X = np.random.default_rng(8).normal(0, 0.01, (1, 1, e.prm.slots))
+    ocs, gcs = e.encrypt_both(X, [0], [0])
+    need = O.rotations_of_schedule(sched)
+    yo = e.o.rotate_sum(ocs[0, 0], e.L, sched, {r: e.ork[r] for r in need}, qp_sum=True)
+    yg = e.g.rotate_sum(e.gevk, gcs[0, 0].contiguous(), e.L, sched, qp_sum=True)
+    assert np.array_equal(e.g_coeff(yg, e.L), e.o_coeff(yo))
+    w = S.Workload("t5g3", S.CFG_TOY, 12, 5, 2 * e.prm.slots - 9, 11, (4,), "scale10", 1, 1)
+    W = S.client_updates(w)
+    ocs, gcs = e.encrypt_both(S.split_chunks(W, e.prm.slots), range(5), range(2))
+    Dg, _ = e.g.distances(e.gevk, gcs, 5, 2, e.prm.scale, mode=e.LC.LC_MODE_BATCHED | e.LC.LC_HOIST_QP_SUM,
+                          groups=sched)
+    Do = e.o.distances(ocs, e.orlk, sched, e.ork, qp_sum=True)
+    assert np.array_equal(e.g_coeff(Dg, e.L - 1), e.o_coeff(Do))
+
+
 @pytest.fixture(scope="module")
 def prod_g2():
     """Production parameters with the rotation keys of the hoisting schedule [2]*7 (21 keys)."""
