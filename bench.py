@@ -104,11 +104,16 @@ SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7, "g3qp": [3, 3, 3, 3, 2]}
 NTT_DRAM_BYTES_PER_LIMB = (443.7e6 + 453.9e6 + 453.5e6 + 443.8e6) / (2 * 960)
 
 
-def build_workload(LC, g, w: S.Workload, sched_name: str = "g2qp"):
+def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):
     N = g.N
-    sched = SCHEDULES[sched_name]
-    # keys of the schedule plus the 14 log-step keys of the plain form
-    rots = sorted(set(LC.rotations_of_schedule(sched)) | set(LC.rotations_of_schedule([1] * (g.log_n - 1))))
+    # keys of the schedule (every candidate schedule for "auto") plus the 14 log-step keys of the
+    # plain form
+    names = sorted(SCHEDULES) if sched_name == "auto" else [sched_name]
+    rots = set(LC.rotations_of_schedule([1] * (g.log_n - 1)))
+    for nm in names:
+        rots |= set(LC.rotations_of_schedule(SCHEDULES[nm]))
+    rots = sorted(rots)
+    sched = SCHEDULES["g3qp" if sched_name == "auto" else sched_name]
     s = S.secret_key(w.seed, w.config, N)
     pa, pe = S.pk_rand(w.seed, w.config, g.q, N)
     pk = g.pk_gen(s, pa, pe)
@@ -230,8 +235,9 @@ def run_micro(args):
     xl = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
     # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input),
     # rotate-and-sum in one-ModDown groups of the chosen schedule
-    sched = SCHEDULES[args.schedule]
-    qpf = LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0
+    sname = "g3qp" if args.schedule == "auto" else args.schedule
+    sched = SCHEDULES[sname]
+    qpf = LC.LC_HOIST_QP_SUM if sname.endswith("qp") else 0
     for r in LC.rotations_of_schedule(sched):
         if r != 1:
             evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
@@ -318,8 +324,9 @@ def run_serving(args):
     honest, byz = 48, 16
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=local, stream=stream)
-        sched = SCHEDULES[args.schedule]
-        flags = LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0
+        sname = "g3qp" if args.schedule == "auto" else args.schedule
+        sched = SCHEDULES[sname]
+        flags = LC.LC_HOIST_QP_SUM if sname.endswith("qp") else 0
         ten = build_serving(LC, g, args.tenants, sched, honest=honest, byz=byz)
         tenants = [t for t, _ in ten]
         pools = [p for _, p in ten]
@@ -371,7 +378,7 @@ def run_serving(args):
                     "clocks": ck, "dtype": "u64", "data": "synthetic",
                     "config": {"workload": "serving_N32768_4tenants_n{5,10,20,40}_d{2^16..2^22}_poisson",
                                "tenants": args.tenants, "budget_gb": args.budget_gb,
-                               "rotation_schedule": args.schedule, "seed": 3}}
+                               "rotation_schedule": sname, "seed": 3}}
             print(json.dumps(line), flush=True)
 
 
@@ -382,9 +389,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mode", choices=["batched", "perop"], default="batched")
-    ap.add_argument("--schedule", choices=sorted(SCHEDULES), default="g3qp",
+    ap.add_argument("--schedule", choices=sorted(SCHEDULES) + ["auto"], default="auto",
                     help="rotate-and-sum hoisting: log = 14 single rotations; g2qp = 7 groups of 3 rotations "
-                         "with one ModDown per group (21 rotation keys); g3qp = 4 groups of 7 + 1 of 3 (31 keys)")
+                         "with one ModDown per group (21 rotation keys); g3qp = 4 groups of 7 + 1 of 3 (31 keys); "
+                         "auto = the autotuner picks among them (and the kernel tile shapes)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -426,9 +435,18 @@ def main():
         g = LC.Context.production(device=local, stream=stream)
         evk, cts, masks, sched, s = build_workload(LC, g, w, args.schedule)
         mode = LC.LC_MODE_BATCHED if args.mode == "batched" else LC.LC_MODE_PER_OP
-        dmode = mode | (LC.LC_HOIST_QP_SUM if args.schedule.endswith("qp") else 0)
         out_d = g.empty(w.n_pairs, 2, g.L, g.N)
         out_a = g.empty(w.chunks, 2, g.L, g.N)
+        sched_name = "g3qp" if args.schedule == "auto" else args.schedule
+        tuning = None
+        if args.mode == "batched" and not args.no_autotune:
+            from paper_2408_06197_b300 import autotune
+            t0 = time.perf_counter()
+            cand = dict(SCHEDULES) if args.schedule == "auto" else {args.schedule: SCHEDULES[args.schedule]}
+            tuning = autotune.tune(g, evk, cts, w.n_clients, w.chunks, g.scale, schedules=cand, out=out_d)
+            tuning["seconds"] = time.perf_counter() - t0
+            sched_name, sched = tuning["schedule"], tuning["groups"]
+        dmode = mode | (LC.LC_HOIST_QP_SUM if sched_name.endswith("qp") else 0)
 
         def step():
             g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d)
@@ -570,7 +588,9 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "n_clients": w.n_clients, "d": w.d,
                        "chunks": w.chunks, "pairs": w.n_pairs, "log_n": 15, "limbs_q": 15, "limbs_p": 4, "dnum": 4,
-                       "rotation_schedule": args.schedule, "rotation_keys": len(evk.rotations),
+                       "rotation_schedule": sched_name, "rotation_keys_loaded": len(evk.rotations),
+                       "tuning": ({"knobs": tuning["knobs"], "ms": tuning["ms"], "seconds": tuning["seconds"],
+                                   "trials": len(tuning["trials"])} if tuning else g.tuning()),
                        "launch": "cuda_graph_replay" if (args.mode == "batched" and not args.no_graph) else "eager",
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},

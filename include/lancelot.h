@@ -118,6 +118,26 @@ int lc_profile(lc_ctx* ctx, int start, double* ms, double* bytes, uint64_t* laun
  * results are identical for every setting. */
 int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
 
+/* Tile-shape knobs for an autotuner (no counterpart in the paper; the paper tunes nothing on
+ * the GPU).  Every option computes identical results; only speed differs.  Unknown knobs or
+ * options fail with LC_EINVAL and leave the setting unchanged.  Options (default first):
+ *   LC_TUNE_NTT_ROW_MINB       row pass of the NTT: minimum resident 128-thread blocks, i.e. a
+ *                              register cap: 5, 4, 6
+ *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 1 (no cap), 6, 8
+ *   LC_TUNE_GROUP_SPLIT_ITEMS  one-ModDown group kernel, rows with primes below 2^40: items per
+ *                              thread, 1 or 2
+ *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 2 or 1
+ *   LC_TUNE_TENSOR_WARPS       batched distance tensor (primes below 2^40): warps per block,
+ *                              16 (4 pair slots per thread), 8 (8 slots) or 12 (6 slots)
+ * The paper_2408_06197_b300.autotune module times the options on the caller's workload. */
+#define LC_TUNE_NTT_ROW_MINB 1
+#define LC_TUNE_NTT_COL_MINB 2
+#define LC_TUNE_GROUP_SPLIT_ITEMS 3
+#define LC_TUNE_GROUP_WIDE_ITEMS 4
+#define LC_TUNE_TENSOR_WARPS 5
+int lc_set_tuning(lc_ctx* ctx, uint32_t knob, int32_t value);
+int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
+
 /* CUDA-graph capture of a sequence of calls on the context's stream (no counterpart in the
  * paper; replaces per-call kernel launches with one graph launch).  Between lc_graph_begin and
  * lc_graph_end only device-pointer evaluation calls may be made; their scratch must already be

@@ -1,0 +1,91 @@
+"""Autotuner for the batched distance step: hoisting schedule and tile shapes.
+
+The library exposes tile-shape knobs (`lc_set_tuning`) whose options all compute identical
+results, and the rotate-and-sum schedule is a call argument (Section "Dynamic Hoisting": group
+sizes g trade key memory for fewer ModUp/ModDown rounds).  `tune` times one workload shape on the
+context's stream with CUDA events and keeps, by coordinate descent, the fastest schedule and then
+the fastest option of each knob in turn, leaving the context set to the winner.  Candidate
+schedules are those whose rotation keys are loaded in `evk` and whose key set fits
+`key_budget_bytes`.
+"""
+from __future__ import annotations
+
+import statistics
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from . import lancelot as LC
+
+
+def candidate_schedules(log_n: int) -> Dict[str, List[int]]:
+    """log: one rotation per group (log2(N/2) groups); gKqp: groups of 2^K - 1 rotations with one
+    ModDown per group, the remainder in a last smaller group."""
+    b = log_n - 1
+    out = {"log": [1] * b}
+    for g in (2, 3):
+        out[f"g{g}qp"] = [g] * (b // g) + ([b % g] if b % g else [])
+    return out
+
+
+def schedule_mode(name: str) -> int:
+    return LC.LC_MODE_BATCHED | (LC.LC_HOIST_QP_SUM if name.endswith("qp") else 0)
+
+
+def key_bytes(ctx: "LC.Context", n_keys: int) -> int:
+    """Device bytes of n switching keys at the top level: dnum x 2 x (L+1+K) limbs of N words."""
+    return n_keys * ctx.dnum * 2 * (ctx.nq + ctx.np_) * ctx.N * 8
+
+
+def _time_ms(ctx: "LC.Context", fn, reps: int) -> float:
+    fn()  # warm: scratch sized, kernels loaded
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(ctx.stream)
+    for k in range(reps):
+        fn()
+        ev[k + 1].record(ctx.stream)
+    torch.cuda.synchronize()
+    return statistics.median(ev[k].elapsed_time(ev[k + 1]) for k in range(reps))
+
+
+def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunks: int, scale: float,
+         reps: int = 3, schedules: Optional[Dict[str, Sequence[int]]] = None,
+         key_budget_bytes: Optional[float] = None, out: Optional[torch.Tensor] = None) -> dict:
+    """Returns {"schedule", "groups", "mode", "knobs", "ms", "trials"}; the context keeps the
+    chosen knob settings (the schedule is an argument of each distances call)."""
+    have = set(evk.rotations)
+    cands = {}
+    for name, sched in (schedules or candidate_schedules(ctx.log_n)).items():
+        rots = set(LC.rotations_of_schedule(sched))
+        if not rots <= have:
+            continue
+        if key_budget_bytes is not None and key_bytes(ctx, len(rots) + 1) > key_budget_bytes:
+            continue
+        cands[name] = list(sched)
+    if not cands:
+        raise LC.LancelotError("autotune: no candidate schedule has all its rotation keys loaded")
+    if out is None:
+        out = ctx.empty(n * (n - 1) // 2, 2, ctx.L, ctx.N)
+    trials = []
+
+    def run(name):
+        return lambda: ctx.distances(evk, cts, n, chunks, scale, mode=schedule_mode(name), groups=cands[name],
+                                     out=out)
+
+    best, best_ms = None, float("inf")
+    for name in cands:
+        ms = _time_ms(ctx, run(name), reps)
+        trials.append({"schedule": name, "ms": ms})
+        if ms < best_ms:
+            best, best_ms = name, ms
+    for knob, options in LC.TUNING_OPTIONS.items():
+        times = {}
+        for v in options:
+            ctx.set_tuning(knob, v)
+            times[v] = _time_ms(ctx, run(best), reps)
+            trials.append({LC.TUNING_NAMES[knob]: v, "ms": times[v]})
+        pick = min(times, key=times.get)
+        ctx.set_tuning(knob, pick)
+        best_ms = min(best_ms, times[pick])
+    return {"schedule": best, "groups": cands[best], "mode": schedule_mode(best), "knobs": ctx.tuning(),
+            "ms": best_ms, "trials": trials}

@@ -302,13 +302,13 @@ static int build_tables(lc_ctx* c) {
 static void ntt_fwd_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowMap& m) {
     const double limbs = (double)batch * m.n;
     PROF(c, PROF_NTT, limbs * c->N * 16.0, (uint64_t)limbs,
-         ntt_forward(base, stride, batch, m, c->log_n, c->tables(), c->stream));
+         ntt_forward(base, stride, batch, m, c->log_n, c->tables(), c->stream, c->ntt_tune()));
     if (c->debug && c->debug_err.size()) c->debug_err += " [forward NTT batch " + std::to_string(batch) + " rows " + std::to_string(m.n) + "]";
 }
 static void ntt_inv_p(lc_ctx* c, u64* base, size_t stride, int batch, const RowMap& m) {
     const double limbs = (double)batch * m.n;
     PROF(c, PROF_NTT, limbs * c->N * 16.0, (uint64_t)limbs,
-         ntt_inverse(base, stride, batch, m, c->log_n, c->tables(), c->stream));
+         ntt_inverse(base, stride, batch, m, c->log_n, c->tables(), c->stream, c->ntt_tune()));
 }
 static void ntt_polys(lc_ctx* c, u64* data, int n_polys, int nl, bool forward) {
     RowMap m = rows_seq(nl);
@@ -1166,6 +1166,29 @@ void lc_graph_free(lc_graph* g) {
 int lc_set_max_batch(lc_ctx* c, uint32_t max_items) {
     if (!c) return LC_EINVAL;
     c->max_batch = max_items;
+    return LC_OK;
+}
+
+int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
+    if (!c) return LC_EINVAL;
+    bool ok = false;
+    switch (knob) {
+        case LC_TUNE_NTT_ROW_MINB: ok = value == 4 || value == 5 || value == 6; break;
+        case LC_TUNE_NTT_COL_MINB: ok = value == 1 || value == 6 || value == 8; break;
+        case LC_TUNE_GROUP_SPLIT_ITEMS:
+        case LC_TUNE_GROUP_WIDE_ITEMS: ok = value == 1 || value == 2; break;
+        case LC_TUNE_TENSOR_WARPS: ok = value == 8 || value == 12 || value == 16; break;
+        default: break;
+    }
+    if (!ok) return fail(c, LC_EINVAL, "lc_set_tuning: knob " + std::to_string(knob) + " has no option " +
+                                           std::to_string(value));
+    c->tune[knob] = value;
+    return LC_OK;
+}
+
+int lc_get_tuning(const lc_ctx* c, uint32_t knob, int32_t* value) {
+    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_TENSOR_WARPS) return LC_EINVAL;
+    *value = c->tune[knob];
     return LC_OK;
 }
 

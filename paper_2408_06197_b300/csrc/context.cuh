@@ -96,6 +96,8 @@ struct lc_ctx {
     std::string err;
     uint64_t n_keyswitch = 0, n_modup = 0;
     uint32_t max_batch = 0;  // 0 = limited only by the scratch budget
+    // tile-shape choices (LC_TUNE_*, set by lc_set_tuning; results never depend on them)
+    int tune[8] = {0, 5, 1, 1, 2, 16, 0, 0};
     bool debug = false;      // LC_DEBUG set: check every launch, remember the first failure
     std::string debug_err;
     bool capturing = false;  // inside lc_graph_begin / lc_graph_end
@@ -107,6 +109,7 @@ struct lc_ctx {
     size_t ev_used = 0;
 
     NttTables tables() const { return NttTables{tw_fwd, tw_inv, mc}; }
+    NttTune ntt_tune() const { return NttTune{tune[LC_TUNE_NTT_ROW_MINB], tune[LC_TUNE_NTT_COL_MINB]}; }
     int digits(int level) const { return (level + 1 + alpha - 1) / alpha; }
     int qp_mod(int level, int t) const { return t <= level ? t : nq + (t - level - 1); }
 };

@@ -114,8 +114,8 @@ __device__ __forceinline__ void fwd_col_body(u64* a, u64* s, const ModConst& mc,
     }
 }
 
-template <int C>
-__global__ void __launch_bounds__(1 << C) ntt_fwd_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+template <int C, int MINB>
+__global__ void __launch_bounds__(1 << C, MINB) ntt_fwd_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
     constexpr int LOGN = C + 8;
     __shared__ u64 s[C > 4 ? (16 << C) : 1];
     int mi;
@@ -191,8 +191,8 @@ __device__ __forceinline__ void inv_col_body(u64* a, u64* s, const ModConst& mc,
     for (int u = 0; u < 16; u++) a[((size_t)(rg + RS * u) << 8) + col0 + c] = x[u];
 }
 
-template <int C>
-__global__ void __launch_bounds__(1 << C) ntt_inv_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
+template <int C, int MINB>
+__global__ void __launch_bounds__(1 << C, MINB) ntt_inv_col(u64* base, size_t batch_stride, RowMap map, NttTables tb) {
     constexpr int LOGN = C + 8;
     __shared__ u64 s[C > 4 ? (16 << C) : 1];
     int mi;
@@ -252,8 +252,9 @@ __device__ __forceinline__ void fwd_row_body(u64* a, u64* s, const ModConst& mc,
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];
 }
 
-__global__ void __launch_bounds__(kRowThreads, 5) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
-                                                           NttTables tb) {
+template <int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+                                                              NttTables tb) {
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
     int mi;
@@ -309,8 +310,9 @@ __device__ __forceinline__ void inv_row_body(u64* a, u64* s, const ModConst& mc,
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = x[u];
 }
 
-__global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
-                                                           NttTables tb) {
+template <int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+                                                              NttTables tb) {
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
     int mi;
@@ -325,34 +327,49 @@ __global__ void __launch_bounds__(kRowThreads, 5) ntt_inv_row(u64* base, size_t 
 
 }  // namespace
 
-#define LC_COL_DISPATCH(KERNEL, C_, GRID, S_)                                                       \
+// column pass: C = log_n - 8 in [4, 8]; MINB (minimum resident blocks, i.e. a register cap) is
+// a tuning choice: 1, 6 or 8
+#define LC_COL_C(KERNEL, MB, C_, GRID, S_)                                                          \
     switch (C_) {                                                                                   \
-        case 4: KERNEL<4><<<GRID, 1 << 4, 0, S_>>>(base, batch_stride, map, tb); break;             \
-        case 5: KERNEL<5><<<GRID, 1 << 5, 0, S_>>>(base, batch_stride, map, tb); break;             \
-        case 6: KERNEL<6><<<GRID, 1 << 6, 0, S_>>>(base, batch_stride, map, tb); break;             \
-        case 7: KERNEL<7><<<GRID, 1 << 7, 0, S_>>>(base, batch_stride, map, tb); break;             \
-        case 8: KERNEL<8><<<GRID, 1 << 8, 0, S_>>>(base, batch_stride, map, tb); break;             \
+        case 4: KERNEL<4, MB><<<GRID, 1 << 4, 0, S_>>>(base, batch_stride, map, tb); break;         \
+        case 5: KERNEL<5, MB><<<GRID, 1 << 5, 0, S_>>>(base, batch_stride, map, tb); break;         \
+        case 6: KERNEL<6, MB><<<GRID, 1 << 6, 0, S_>>>(base, batch_stride, map, tb); break;         \
+        case 7: KERNEL<7, MB><<<GRID, 1 << 7, 0, S_>>>(base, batch_stride, map, tb); break;         \
+        case 8: KERNEL<8, MB><<<GRID, 1 << 8, 0, S_>>>(base, batch_stride, map, tb); break;         \
         default: break;                                                                             \
+    }
+#define LC_COL_DISPATCH(KERNEL, MINB_, C_, GRID, S_)            \
+    switch (MINB_) {                                            \
+        case 6: LC_COL_C(KERNEL, 6, C_, GRID, S_) break;        \
+        case 8: LC_COL_C(KERNEL, 8, C_, GRID, S_) break;        \
+        default: LC_COL_C(KERNEL, 1, C_, GRID, S_) break;       \
+    }
+// row pass: MINB 4, 5 or 6
+#define LC_ROW_DISPATCH(KERNEL, MINB_, GRID, S_)                                                              \
+    switch (MINB_) {                                                                                          \
+        case 4: KERNEL<4><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;           \
+        case 6: KERNEL<6><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;           \
+        default: KERNEL<5><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;          \
     }
 
 void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n, const NttTables& tb,
-                 cudaStream_t s) {
+                 cudaStream_t s, NttTune tune) {
     const int limbs = batch * map.n;
     if (limbs == 0) return;
     const int C = log_n - 8;
     dim3 gc(16, limbs), gr((1 << log_n) / 2048, limbs);
-    LC_COL_DISPATCH(ntt_fwd_col, C, gc, s)
-    ntt_fwd_row<<<gr, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb);
+    LC_COL_DISPATCH(ntt_fwd_col, tune.col_minb, C, gc, s)
+    LC_ROW_DISPATCH(ntt_fwd_row, tune.row_minb, gr, s)
     g_lc_launches += 2;
 }
 
 void ntt_inverse(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n, const NttTables& tb,
-                 cudaStream_t s) {
+                 cudaStream_t s, NttTune tune) {
     const int limbs = batch * map.n;
     if (limbs == 0) return;
     const int C = log_n - 8;
     dim3 gc(16, limbs), gr((1 << log_n) / 2048, limbs);
-    ntt_inv_row<<<gr, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb);
-    LC_COL_DISPATCH(ntt_inv_col, C, gc, s)
+    LC_ROW_DISPATCH(ntt_inv_row, tune.row_minb, gr, s)
+    LC_COL_DISPATCH(ntt_inv_col, tune.col_minb, C, gc, s)
     g_lc_launches += 2;
 }

@@ -32,7 +32,13 @@ struct NttTables {
     const ModConst* mc;        // [n_mod]
 };
 
+// launch-shape choices (register caps) picked by the tuner; results do not depend on them
+struct NttTune {
+    int row_minb = 5;  // row pass: minimum resident blocks of 128 threads (4, 5 or 6)
+    int col_minb = 1;  // column pass: 1 (no cap), 6 or 8
+};
+
 void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n,
-                 const NttTables& t, cudaStream_t s);
+                 const NttTables& t, cudaStream_t s, NttTune tune = NttTune{});
 void ntt_inverse(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n,
-                 const NttTables& t, cudaStream_t s);
+                 const NttTables& t, cudaStream_t s, NttTune tune = NttTune{});

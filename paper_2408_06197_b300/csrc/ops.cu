@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
                                                                 u64* __restrict__ out) {
     constexpr int NT = WARPS * 32;
     constexpr int UPT = (kMaxSlots * 2 * (kTX / 2) + NT - 1) / NT;  // 16-byte copy units per thread
+    static_assert(WARPS * PPT >= 64, "pair slots must cover a block pair (8 x 8, or 55 pairs of 11 clients)");
     __shared__ __align__(16) u64 sh[kStages][kMaxSlots][2][kTX];
     const int nb = (n + cb - 1) / cb;
     int bp = blockIdx.x, I = 0;
@@ -714,15 +715,6 @@ __global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64
 // grid: x = group of kBT items (fastest, so that consecutive blocks share the key tile in L2),
 // y = tile of 2 kTG coefficients, z = row r of Q_l U P.
 constexpr int kTG = 128;
-#ifndef LC_IG_BT_SPLIT
-#define LC_IG_BT_SPLIT 1
-#endif
-#ifndef LC_IG_BT_WIDE
-#define LC_IG_BT_WIDE 2
-#endif
-#ifndef LC_IG_MINB_SPLIT
-#define LC_IG_MINB_SPLIT 5
-#endif
 __device__ __forceinline__ ulonglong2 ld2_swap(const u64* p, unsigned s0, bool sw) {
     const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p + s0));
     return sw ? make_ulonglong2(v.y, v.x) : v;
@@ -734,7 +726,7 @@ struct RowSel {
 // SPLIT: every selected row's prime is below 2^40, so digits and keys split into 20-bit halves
 // (four 32x32 -> 64-bit products per 128-bit product, three 64-bit partial sums)
 template <int T, bool ITEMS, bool SPLIT, int kBT>
-__global__ void __launch_bounds__(kTG, SPLIT ? LC_IG_MINB_SPLIT : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+__global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
                                                      int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
@@ -1106,10 +1098,22 @@ void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
                                                                   out);
         g_lc_launches += 1;
     }
-    if (split0 < nl) {
+    if (split0 < nl) {  // warps per block: LC_TUNE_TENSOR_WARPS (pair slots per thread = 64 / warps, rounded up)
         dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), nl - split0);
-        k_sq_acc_tiled<16, 4, true><<<grid, 512, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0, np,
-                                                                  c->mc, out);
+        switch (c->tune[LC_TUNE_TENSOR_WARPS]) {
+            case 8:
+                k_sq_acc_tiled<8, 8, true><<<grid, 256, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
+                                                                         np, c->mc, out);
+                break;
+            case 12:
+                k_sq_acc_tiled<12, 6, true><<<grid, 384, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
+                                                                          np, c->mc, out);
+                break;
+            default:
+                k_sq_acc_tiled<16, 4, true><<<grid, 512, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
+                                                                          np, c->mc, out);
+                break;
+        }
         g_lc_launches += 1;
     }
 }
@@ -1212,9 +1216,8 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
     const RowSel split{k, nl - k, 0}, wide{0, k, nl};
     const int ns = nl - k, nw = k + c->np;
     const unsigned gy = (unsigned)(c->N / (2 * kTG));
-#define LC_IG(TT, SPL, SEL, CNT)                                                                                    \
+#define LC_IG(TT, SPL, BT, SEL, CNT)                                                                                \
     {                                                                                                               \
-        constexpr int BT = SPL ? LC_IG_BT_SPLIT : LC_IG_BT_WIDE;                                                    \
         const dim3 grid((unsigned)((B + BT - 1) / BT), gy, CNT);                                                    \
         if (keys_dev)                                                                                               \
             k_inner_gather<TT, true, SPL, BT><<<grid, kTG, 0, c->stream>>>(                                         \
@@ -1225,23 +1228,31 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
                 ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
                 nullptr, g, SEL, c->mc, usum, c0acc);                                                               \
     }
-#define LC_IG_T(SPL, SEL, CNT)          \
-    switch (T) {                        \
-        case 1: LC_IG(1, SPL, SEL, CNT); break; \
-        case 2: LC_IG(2, SPL, SEL, CNT); break; \
-        case 3: LC_IG(3, SPL, SEL, CNT); break; \
-        case 4: LC_IG(4, SPL, SEL, CNT); break; \
-        case 5: LC_IG(5, SPL, SEL, CNT); break; \
-        case 6: LC_IG(6, SPL, SEL, CNT); break; \
-        case 7: LC_IG(7, SPL, SEL, CNT); break; \
-        default: break;                 \
+#define LC_IG_T(SPL, BT, SEL, CNT)                 \
+    switch (T) {                                   \
+        case 1: LC_IG(1, SPL, BT, SEL, CNT); break; \
+        case 2: LC_IG(2, SPL, BT, SEL, CNT); break; \
+        case 3: LC_IG(3, SPL, BT, SEL, CNT); break; \
+        case 4: LC_IG(4, SPL, BT, SEL, CNT); break; \
+        case 5: LC_IG(5, SPL, BT, SEL, CNT); break; \
+        case 6: LC_IG(6, SPL, BT, SEL, CNT); break; \
+        case 7: LC_IG(7, SPL, BT, SEL, CNT); break; \
+        default: break;                            \
     }
-    if (ns) {
-        LC_IG_T(true, split, ns)
+    if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS
+        if (c->tune[LC_TUNE_GROUP_SPLIT_ITEMS] == 2) {
+            LC_IG_T(true, 2, split, ns)
+        } else {
+            LC_IG_T(true, 1, split, ns)
+        }
         g_lc_launches += 1;
     }
-    if (nw) {
-        LC_IG_T(false, wide, nw)
+    if (nw) {  // LC_TUNE_GROUP_WIDE_ITEMS
+        if (c->tune[LC_TUNE_GROUP_WIDE_ITEMS] == 1) {
+            LC_IG_T(false, 1, wide, nw)
+        } else {
+            LC_IG_T(false, 2, wide, nw)
+        }
         g_lc_launches += 1;
     }
 #undef LC_IG_T

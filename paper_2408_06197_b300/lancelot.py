@@ -25,6 +25,22 @@ LC_OK = 0
 LC_MODE_PER_OP = 0
 LC_MODE_BATCHED = 1
 LC_HOIST_QP_SUM = 2
+# tile-shape knobs (lc_set_tuning); options listed default first
+LC_TUNE_NTT_ROW_MINB = 1
+LC_TUNE_NTT_COL_MINB = 2
+LC_TUNE_GROUP_SPLIT_ITEMS = 3
+LC_TUNE_GROUP_WIDE_ITEMS = 4
+LC_TUNE_TENSOR_WARPS = 5
+TUNING_OPTIONS = {
+    LC_TUNE_NTT_ROW_MINB: (5, 4, 6),
+    LC_TUNE_NTT_COL_MINB: (1, 6, 8),
+    LC_TUNE_GROUP_SPLIT_ITEMS: (1, 2),
+    LC_TUNE_GROUP_WIDE_ITEMS: (2, 1),
+    LC_TUNE_TENSOR_WARPS: (16, 8, 12),
+}
+TUNING_NAMES = {LC_TUNE_NTT_ROW_MINB: "ntt_row_minb", LC_TUNE_NTT_COL_MINB: "ntt_col_minb",
+                LC_TUNE_GROUP_SPLIT_ITEMS: "group_split_items", LC_TUNE_GROUP_WIDE_ITEMS: "group_wide_items",
+                LC_TUNE_TENSOR_WARPS: "tensor_warps"}
 _ERRS = {-1: "LC_EINVAL", -2: "LC_ELEVEL", -3: "LC_ESCALE", -4: "LC_ENOMEM", -5: "LC_ECUDA",
          -6: "LC_ETIMEOUT", -7: "LC_EBUSY", -8: "LC_EKEY"}
 
@@ -111,6 +127,8 @@ def lib() -> ctypes.CDLL:
             "lc_launches": [vp],
             "lc_profile": [vp, ctypes.c_int, vp, vp, vp],
             "lc_set_max_batch": [vp, u32],
+            "lc_set_tuning": [vp, u32, ctypes.c_int32],
+            "lc_get_tuning": [vp, u32, vp],
             "lc_graph_begin": [vp],
             "lc_graph_end": [vp, vp],
             "lc_graph_launch": [vp, vp],
@@ -314,6 +332,18 @@ class Context:
 
     def set_max_batch(self, max_items: int):
         self._check(lib().lc_set_max_batch(self.h, int(max_items)), "lc_set_max_batch")
+
+    def set_tuning(self, knob: int, value: int):
+        """Select a tile-shape option (LC_TUNE_*; see TUNING_OPTIONS).  Results do not change."""
+        self._check(lib().lc_set_tuning(self.h, int(knob), int(value)), "lc_set_tuning")
+
+    def get_tuning(self, knob: int) -> int:
+        v = ctypes.c_int32()
+        self._check(lib().lc_get_tuning(self.h, int(knob), ctypes.byref(v)), "lc_get_tuning")
+        return int(v.value)
+
+    def tuning(self) -> Dict[str, int]:
+        return {TUNING_NAMES[k]: self.get_tuning(k) for k in TUNING_OPTIONS}
 
     def sync(self):
         self._check(lib().lc_sync(self.h), "lc_sync")

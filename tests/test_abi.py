@@ -52,3 +52,23 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     lib.lc_distances.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_uint32] * 2 + [ctypes.c_double] + \
         [ctypes.c_uint32] * 2 + [ctypes.c_void_p] * 3
     assert lib.lc_distances(None, None, None, 0, 0, 1.0, 0, 0, None, None, None) == -1
+
+
+def test_tuning_entry_points_reject_bad_arguments_without_gpu(lib):
+    lib.lc_set_tuning.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32]
+    lib.lc_get_tuning.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+    v = ctypes.c_int32()
+    assert lib.lc_set_tuning(None, 1, 5) == -1
+    assert lib.lc_get_tuning(None, 1, ctypes.byref(v)) == -1
+
+
+def test_autotune_candidate_schedules_cover_every_rotation_bit():
+    """Each candidate hoisting schedule sums to log2(N/2) and needs exactly the keys of its
+    groups (2^g - 1 per group)."""
+    from paper_2408_06197_b300 import autotune
+    from paper_2408_06197_b300 import lancelot as LC
+    for log_n in (12, 15, 16):
+        for name, sched in autotune.candidate_schedules(log_n).items():
+            assert sum(sched) == log_n - 1
+            assert len(LC.rotations_of_schedule(sched)) == sum((1 << g) - 1 for g in sched)
+    assert autotune.candidate_schedules(15)["g3qp"] == [3, 3, 3, 3, 2]

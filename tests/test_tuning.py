@@ -1,0 +1,70 @@
+"""Every tile-shape option computes the same bits, and the autotuner leaves the context on a
+valid setting (GPU)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from test_gpu_parity import Env
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2408_06197_b300 import autotune
+    sched = autotune.candidate_schedules(12)
+    rots = set()
+    for s in sched.values():
+        rots |= set(O.rotations_of_schedule(s))
+    return Env("toy", 12, S.CFG_TOY, extra_rot=sorted(rots))
+
+
+def _inputs(env, n=6, chunks=3):
+    w = S.Workload("tune", S.CFG_TOY, 12, n, chunks * env.prm.slots - 3, 12, (n - 1,), "scale10", 1, 1)
+    X = S.split_chunks(S.client_updates(w), env.prm.slots)
+    return env.encrypt_both(X, range(n), range(chunks))  # (oracle cts, GPU cts) of the same inputs
+
+
+def test_every_tuning_option_gives_identical_distances(env):
+    LC = env.LC
+    g = env.g
+    _, gcs = _inputs(env)
+    sched = [3, 3, 3, 2]
+    mode = LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM
+    ref, _ = g.distances(env.gevk, gcs, 6, 3, env.prm.scale, mode=mode, groups=sched)
+    for knob, options in LC.TUNING_OPTIONS.items():
+        for v in options:
+            g.set_tuning(knob, v)
+            assert g.get_tuning(knob) == v
+            got, _ = g.distances(env.gevk, gcs, 6, 3, env.prm.scale, mode=mode, groups=sched)
+            assert torch.equal(got, ref), (LC.TUNING_NAMES[knob], v)
+        g.set_tuning(knob, options[0])
+    with pytest.raises(LC.LancelotError):
+        g.set_tuning(LC.LC_TUNE_TENSOR_WARPS, 7)
+    assert g.get_tuning(LC.LC_TUNE_TENSOR_WARPS) == LC.TUNING_OPTIONS[LC.LC_TUNE_TENSOR_WARPS][0]
+
+
+def test_autotune_picks_a_loaded_schedule_and_valid_knobs(env):
+    from paper_2408_06197_b300 import autotune
+    LC = env.LC
+    g = env.g
+    ocs, gcs = _inputs(env)
+    res = autotune.tune(g, env.gevk, gcs, 6, 3, env.prm.scale, reps=2)
+    assert res["schedule"] in autotune.candidate_schedules(12)
+    for knob, name in LC.TUNING_NAMES.items():
+        assert res["knobs"][name] in LC.TUNING_OPTIONS[knob]
+        assert g.get_tuning(knob) == res["knobs"][name]
+    n_opts = sum(len(o) for o in LC.TUNING_OPTIONS.values())
+    assert len(res["trials"]) == len(autotune.candidate_schedules(12)) + n_opts
+    # the tuned setting computes the oracle's bits
+    ref = env.o.distances(ocs, env.orlk, res["groups"], env.ork, qp_sum=res["schedule"].endswith("qp"))
+    got, _ = g.distances(env.gevk, gcs, 6, 3, env.prm.scale, mode=res["mode"], groups=res["groups"])
+    assert np.array_equal(env.g_coeff(got, env.L - 1), env.o_coeff(ref))
+    # a key budget below one key set leaves no candidate
+    with pytest.raises(LC.LancelotError):
+        autotune.tune(g, env.gevk, gcs, 6, 3, env.prm.scale, reps=1, key_budget_bytes=1)
+    for knob, options in LC.TUNING_OPTIONS.items():
+        g.set_tuning(knob, options[0])
+
