@@ -208,6 +208,28 @@ def prod_g2():
     return e
 
 
+G3QP = [3, 3, 3, 3, 2]  # the benchmark's rotation schedule at N = 2^15 (autotuner's pick)
+
+
+@pytest.fixture(scope="module")
+def prod_g3():
+    """Production parameters with the keys of the benchmark's schedule [3,3,3,3,2] (31 keys, a
+    superset of the 14 log-step keys)."""
+    e = Env.__new__(Env)
+    from paper_2408_06197_b300 import lancelot as LC
+    e.LC, e.kind = LC, "prod"
+    e.prm = O.params_production()
+    e.o = O.Context(e.prm)
+    e.g = _ctx("prod")
+    e.sched = G3QP
+    e.keys = KeySet(e.prm, 0, S.CFG_PLAIN, O.rotations_of_schedule(G3QP))
+    e.opk, e.orlk, e.ork = e.keys.oracle_keys(e.o)
+    e.gpk, e.gevk = e.keys.gpu_keys(e.g)
+    e.seed, e.config = 0, S.CFG_PLAIN
+    e.N, e.L = e.prm.N, e.prm.L
+    return e
+
+
 def test_qp_sum_distances_production_bit_exact(prod_g2):
     e = prod_g2
     w = S.Workload("p3g2", S.CFG_PLAIN, 15, 3, e.prm.slots, 4, (2,), "flip5", 1, 0)
@@ -420,10 +442,13 @@ def test_production_distances_small_bit_exact(prod):
 
 
 @pytest.mark.slow
-def test_production_full_size_sampled(prod):
-    """Config of the benchmark (n=10, d=2^20, 64 chunks, batched launches): every pair against
-    FP64 and two sampled pairs + two sampled aggregate chunks bit-exact against the oracle."""
+def test_production_full_size_sampled(prod_g3):
+    """Config of the benchmark in its launch configuration (n=10, d=2^20, 64 chunks, batched
+    launches, one-ModDown groups [3,3,3,3,2]): every pair against FP64 and two sampled pairs + two
+    sampled aggregate chunks bit-exact against the oracle."""
     from paper_2408_06197_b300 import kgc
+    prod = prod_g3
+    mode = prod.LC.LC_MODE_BATCHED | prod.LC.LC_HOIST_QP_SUM
     w = S.PLAIN
     W = S.client_updates(w)
     X = S.split_chunks(W, prod.prm.slots)
@@ -431,7 +456,7 @@ def test_production_full_size_sampled(prod):
     r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), range(w.chunks), prod.N)
     gcs = prod.g.encrypt(prod.gpk, m.reshape(-1, prod.N), r, e0, e1).reshape(w.n_clients, w.chunks, 2, prod.L + 1,
                                                                                prod.N)
-    Dg, sc = prod.g.distances(prod.gevk, gcs, w.n_clients, w.chunks, prod.prm.scale)
+    Dg, sc = prod.g.distances(prod.gevk, gcs, w.n_clients, w.chunks, prod.prm.scale, mode=mode, groups=G3QP)
     dist = np.zeros((w.n_clients, w.n_clients))
     ref = np.zeros_like(dist)
     k = 0
@@ -450,7 +475,7 @@ def test_production_full_size_sampled(prod):
     ocs = np.stack([np.stack([prod.o.encrypt(prod.opk, m[c, k], r[c * w.chunks + k], e0[c * w.chunks + k],
                                              e1[c * w.chunks + k]) for k in range(w.chunks)]) for c in clients])
     pairs = [(0, 1), (7, 9)]
-    Do = prod.o.distances(ocs, prod.orlk, prod.sched, prod.ork, pairs=[(idx[i], idx[j]) for i, j in pairs])
+    Do = prod.o.distances(ocs, prod.orlk, G3QP, prod.ork, pairs=[(idx[i], idx[j]) for i, j in pairs], qp_sum=True)
 
     def pidx(i, j):
         return i * w.n_clients - i * (i + 1) // 2 + (j - i - 1)
@@ -472,3 +497,52 @@ def test_production_full_size_sampled(prod):
                                        e1[c * w.chunks + k]) for c in range(w.n_clients)])[:, None]
         Ao = prod.o.masked_aggregate(np.ascontiguousarray(ock), om, prod.orlk)
         assert np.array_equal(prod.g_coeff(Ag[k].contiguous(), prod.L - 1), prod.o_coeff(Ao[0]))
+
+
+@pytest.mark.slow
+def test_batched_config_full_size_sampled(prod_g3):
+    """The batched configuration at full size (n=50, d=2^22: 256 ciphertexts per client, 94 GB
+    resident, 1,225 pairs in waves) in the benchmark's launch configuration: every pair's
+    read-out against FP64, Multi-Krum selection, and two sampled pairs bit-exact against the
+    oracle (an honest pair and an honest/noisy pair)."""
+    from paper_2408_06197_b300 import kgc
+    e = prod_g3
+    LC = e.LC
+    w = S.BATCHED
+    chunks, n = w.chunks, w.n_clients
+    gcs = e.g.empty(n, chunks, 2, e.L + 1, e.N)
+    sq = np.zeros((n, n))
+    Ws = {}
+    for i in range(n):
+        Wi = S.client_updates(w, [i])[0]
+        Ws[i] = Wi
+        m = plaintexts(e.o, e.prm, S.split_chunks(Wi, e.prm.slots))
+        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [i], range(chunks), e.N)
+        e.g.encrypt(e.gpk, m, r, e0, e1, out=gcs[i].view(chunks, 2, e.L + 1, e.N))
+    for i in range(n):
+        for j in range(i + 1, n):
+            sq[i, j] = sq[j, i] = np.sum((Ws[i] - Ws[j]) ** 2)
+    Dg, sc = e.g.distances(e.gevk, gcs, n, chunks, e.prm.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
+                           groups=G3QP)
+    got = e.g.decrypt_const(e.keys.s, Dg, e.L - 1, sc)
+    dist = np.zeros((n, n))
+    k = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            assert abs(got[k] - sq[i, j]) / sq[i, j] < 1e-5
+            dist[i, j] = dist[j, i] = got[k]
+            k += 1
+    sel = kgc.krum_select(dist, w.f, w.n_select)
+    assert sel == kgc.krum_select(sq, w.f, w.n_select) and not (set(sel) & set(w.byzantine))
+    pairs = [(2, 17), (5, 44)]
+    clients = sorted({c for p in pairs for c in p})
+    idx = {c: t for t, c in enumerate(clients)}
+    ocs = []
+    for c in clients:
+        m = plaintexts(e.o, e.prm, S.split_chunks(Ws[c], e.prm.slots))
+        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [c], range(chunks), e.N)
+        ocs.append(np.stack([e.o.encrypt(e.opk, m[k], r[k], e0[k], e1[k]) for k in range(chunks)]))
+    Do = e.o.distances(np.stack(ocs), e.orlk, G3QP, e.ork, pairs=[(idx[i], idx[j]) for i, j in pairs], qp_sum=True)
+    for t, (i, j) in enumerate(pairs):
+        p = i * n - i * (i + 1) // 2 + (j - i - 1)
+        assert np.array_equal(e.g_coeff(Dg[p].contiguous(), e.L - 1), e.o_coeff(Do[t]))
