@@ -274,6 +274,15 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
         else
             s00[k] = s01[k] = s11[k] = u128v{0, 0};
     }
+    // word offsets of each pair's two client slots inside one ring stage
+    constexpr int STAGE = kMaxSlots * 2 * kTX;
+    int oa[PPT], ob[PPT];
+#pragma unroll
+    for (int t = 0; t < PPT; t++) {
+        oa[t] = ((pk[t] >> 4) & 15) * 2 * kTX + x;
+        ob[t] = (pk[t] & 15) * 2 * kTX + x;
+    }
+    const u64* shf = &sh[0][0][0][0];
     for (int k = 0; k < chunks; k++) {
         cp_async_wait<kStages - 2>();
         __syncthreads();
@@ -285,21 +294,23 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
                     cp_async16(&sh[nk % kStages][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)nk * chunk_stride);
             cp_async_commit();
         }
-        const int cur = k % kStages;
+        const u64* st = shf + (k % kStages) * STAGE;
 #pragma unroll
         for (int t = 0; t < PPT; t++) {
             if (pk[t] < 0) continue;
-            const int sa = (pk[t] >> 4) & 15, sb = pk[t] & 15;
-            const u64 a0 = sh[cur][sa][0][x], a1 = sh[cur][sa][1][x];
-            const u64 b0 = sh[cur][sb][0][x], b1 = sh[cur][sb][1][x];
-            const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
+            const u64 a0 = st[oa[t]], a1 = st[oa[t] + kTX];
+            const u64 b0 = st[ob[t]], b1 = st[ob[t] + kTX];
             if (SPLIT) {
+                // a + q - b in [1, 2q): congruent to the difference, halves below 2^21, so every
+                // partial product stays below 2^42 and < 2^20 chunks cannot overflow
+                const u64 d0 = a0 + m.q - b0, d1 = a1 + m.q - b1;
                 const unsigned h0 = (unsigned)(d0 >> 20), l0 = (unsigned)d0 & 0xFFFFFu;
                 const unsigned h1 = (unsigned)(d1 >> 20), l1 = (unsigned)d1 & 0xFFFFFu;
                 sq_split(t00[t], h0, l0);
                 mac_split(t01[t], h0, l0, h1, l1);
                 sq_split(t11[t], h1, l1);
             } else {
+                const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
                 mac128(s00[t], d0, d0);
                 mac128(s01[t], d0, d1);
                 mac128(s11[t], d1, d1);
