@@ -105,6 +105,17 @@ int lc_counters(lc_ctx* ctx, uint64_t* out, int reset);
  * dst/src: device pointer on the device side; host side pageable or pinned. */
 int lc_memcpy_h2d(lc_ctx* ctx, uint64_t* dst_dev, const void* src_host, size_t bytes);
 int lc_memcpy_d2h(lc_ctx* ctx, void* dst_host, const uint64_t* src_dev, size_t bytes);
+/* Overlapped host transfers (no counterpart in the paper).  The context keeps one copy stream
+ * per direction.  lc_copy_async enqueues a copy on the stream of its direction (LC_H2D or
+ * LC_D2H), ordered after all work enqueued on the context's stream so far, so a device buffer
+ * that earlier calls still read is not overwritten and a result is read only once computed;
+ * *ticket names the copy.  lc_copy_wait makes the context's stream wait for that copy.  Host
+ * memory must be pinned for the copy to overlap with computation.  Not allowed inside a graph
+ * capture (LC_EBUSY).  Tickets stay valid until lc_ctx_destroy (one event each). */
+#define LC_H2D 0
+#define LC_D2H 1
+int lc_copy_async(lc_ctx* ctx, void* dst, const void* src, size_t bytes, int dir, uint64_t* ticket);
+int lc_copy_wait(lc_ctx* ctx, uint64_t ticket);
 /* Kernel launches issued by the library in this process so far (*out). */
 int lc_launches(uint64_t* out);
 /* Per-kernel-class device timing with CUDA events on the context stream (measurement only).

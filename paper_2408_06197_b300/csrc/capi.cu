@@ -645,6 +645,13 @@ void lc_ctx_destroy(lc_ctx* c) {
     lc_dev_free(c, c->scratch);
     lc_dev_free(c, c->stage);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (int d = 0; d < 2; d++)
+        if (c->copy_stream[d]) {
+            cudaStreamSynchronize(c->copy_stream[d]);
+            cudaStreamDestroy(c->copy_stream[d]);
+        }
+    if (c->compute_mark) cudaEventDestroy(c->compute_mark);
+    for (cudaEvent_t e : c->copy_events) cudaEventDestroy(e);
     delete c;
 }
 
@@ -1065,6 +1072,31 @@ int lc_memcpy_h2d(lc_ctx* c, uint64_t* dst, const void* src, size_t bytes) {
 int lc_memcpy_d2h(lc_ctx* c, void* dst, const uint64_t* src, size_t bytes) {
     if (!c || (!dst && bytes) || (!src && bytes)) return fail(c, LC_EINVAL, "lc_memcpy_d2h: null argument");
     LC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return LC_OK;
+}
+
+int lc_copy_async(lc_ctx* c, void* dst, const void* src, size_t bytes, int dir, uint64_t* ticket) {
+    if (!c || !ticket || (dir != LC_H2D && dir != LC_D2H) || (bytes && (!dst || !src)))
+        return fail(c, LC_EINVAL, "lc_copy_async: bad argument");
+    if (c->capturing) return fail(c, LC_EBUSY, "lc_copy_async: not inside a graph capture");
+    if (!c->copy_stream[dir]) LC_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream[dir], cudaStreamNonBlocking));
+    if (!c->compute_mark) LC_CUDA(c, cudaEventCreateWithFlags(&c->compute_mark, cudaEventDisableTiming));
+    cudaEvent_t done;
+    LC_CUDA(c, cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    c->copy_events.push_back(done);
+    // ordered after everything enqueued on the context's stream so far
+    LC_CUDA(c, cudaEventRecord(c->compute_mark, c->stream));
+    LC_CUDA(c, cudaStreamWaitEvent(c->copy_stream[dir], c->compute_mark, 0));
+    LC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, dir == LC_H2D ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                               c->copy_stream[dir]));
+    LC_CUDA(c, cudaEventRecord(done, c->copy_stream[dir]));
+    *ticket = c->copy_events.size() - 1;
+    return LC_OK;
+}
+
+int lc_copy_wait(lc_ctx* c, uint64_t ticket) {
+    if (!c || ticket >= c->copy_events.size()) return fail(c, LC_EINVAL, "lc_copy_wait: unknown ticket");
+    LC_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_events[ticket], 0));
     return LC_OK;
 }
 

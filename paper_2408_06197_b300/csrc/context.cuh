@@ -102,6 +102,10 @@ struct lc_ctx {
     std::string debug_err;
     bool capturing = false;  // inside lc_graph_begin / lc_graph_end
     uint64_t capture_launches0 = 0;
+    // overlapped host transfers: one copy stream per direction, one event per ticket
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};
+    cudaEvent_t compute_mark = nullptr;
+    std::vector<cudaEvent_t> copy_events;
     // profiling
     bool prof_on = false;
     std::vector<ProfRec> prof;

@@ -25,6 +25,8 @@ LC_OK = 0
 LC_MODE_PER_OP = 0
 LC_MODE_BATCHED = 1
 LC_HOIST_QP_SUM = 2
+LC_H2D = 0
+LC_D2H = 1
 # tile-shape knobs (lc_set_tuning); options listed default first
 LC_TUNE_NTT_ROW_MINB = 1
 LC_TUNE_NTT_COL_MINB = 2
@@ -128,6 +130,8 @@ def lib() -> ctypes.CDLL:
             "lc_profile": [vp, ctypes.c_int, vp, vp, vp],
             "lc_set_max_batch": [vp, u32],
             "lc_set_tuning": [vp, u32, ctypes.c_int32],
+            "lc_copy_async": [vp, vp, vp, ctypes.c_size_t, ctypes.c_int, vp],
+            "lc_copy_wait": [vp, ctypes.c_uint64],
             "lc_get_tuning": [vp, u32, vp],
             "lc_graph_begin": [vp],
             "lc_graph_end": [vp, vp],
@@ -380,6 +384,25 @@ class Context:
             raise LancelotError("d2h: source must be a contiguous CUDA tensor of the same byte size")
         self._check(lib().lc_memcpy_d2h(self.h, ctypes.c_void_p(dst.ctypes.data), _t_ptr(src), dst.nbytes),
                     "lc_memcpy_d2h")
+
+    def copy_async(self, dst, src) -> int:
+        """Overlapped copy between a device tensor and a pinned host array (either direction),
+        ordered after the work enqueued so far; returns a ticket for copy_wait."""
+        t = ctypes.c_uint64()
+        if isinstance(dst, torch.Tensor) and isinstance(src, np.ndarray):
+            _need(dst, src.size, "copy_async: dst")
+            args = (_t_ptr(dst), _np_ptr(src), src.nbytes, LC_H2D)
+        elif isinstance(dst, np.ndarray) and isinstance(src, torch.Tensor):
+            _need(src, dst.size, "copy_async: src")
+            args = (_np_ptr(dst), _t_ptr(src), dst.nbytes, LC_D2H)
+        else:
+            raise LancelotError("copy_async: one side must be a device tensor and the other a host array")
+        self._check(lib().lc_copy_async(self.h, *args, ctypes.byref(t)), "lc_copy_async")
+        return int(t.value)
+
+    def copy_wait(self, ticket: int):
+        """The context's stream waits for the copy `ticket`."""
+        self._check(lib().lc_copy_wait(self.h, int(ticket)), "lc_copy_wait")
 
     def empty(self, *shape) -> torch.Tensor:
         return torch.empty(shape, dtype=torch.int64, device=f"cuda:{self.device}")

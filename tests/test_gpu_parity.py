@@ -546,3 +546,33 @@ def test_batched_config_full_size_sampled(prod_g3):
     for t, (i, j) in enumerate(pairs):
         p = i * n - i * (i + 1) // 2 + (j - i - 1)
         assert np.array_equal(e.g_coeff(Dg[p].contiguous(), e.L - 1), e.o_coeff(Do[t]))
+
+
+def test_overlapped_copies_match_stream_ordered_copies(toy):
+    """lc_copy_async / lc_copy_wait: an input copied in on the copy stream, transformed, and
+    copied out after the transform gives the same words as the stream-ordered path; a copy
+    into a buffer that queued work still reads waits for that work."""
+    LC = toy.LC
+    g = toy.g
+    rng = np.random.default_rng(21)
+    a = np.stack([rng.integers(0, q, size=toy.N, dtype=np.uint64) for q in toy.prm.q])
+    ha = LC.pinned_empty(a.shape)
+    ha[...] = a
+    d = g.empty(*a.shape)
+    t = g.copy_async(d, ha)
+    g.copy_wait(t)
+    g.to_eval(d, toy.L, inplace=True)
+    hb = LC.pinned_empty(a.shape)
+    t2 = g.copy_async(hb, d)  # ordered after the transform
+    # overwrite the device buffer only after the read-out above has been queued
+    g.copy_wait(t2)
+    zero = LC.pinned_empty(a.shape)
+    zero[...] = 0
+    g.copy_wait(g.copy_async(d, zero))
+    g.sync()
+    torch.cuda.synchronize()
+    ref = LC.torch_to_u64(g.to_eval(LC.u64_to_torch(a), toy.L))
+    assert np.array_equal(np.asarray(hb), ref)
+    assert not LC.torch_to_u64(d).any()
+    with pytest.raises(LC.LancelotError):
+        g.copy_wait(10 ** 9)
