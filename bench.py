@@ -282,6 +282,76 @@ def run_micro(args):
                                 for k, v in prof.items()}}), flush=True)
 
 
+# ----------------------------------------------------------------------------- packing-size sweep
+def run_sweep(args):
+    """Packing-size sweep (the paper's cryptographic-hyperparameter analysis): the same round
+    (n = 10 clients, d = 2^20, 45 distances + masked aggregate) at N = 2^13 .. 2^16 with the
+    production modulus chain at each N; chunks = d / (N/2) shrink as N grows.  One JSON line per N
+    (device time per round, CUDA events, autotuned schedule and tiles)."""
+    import torch
+    from paper_2408_06197_b300 import autotune
+    from paper_2408_06197_b300 import lancelot as LC
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    for log_n in [int(x) for x in args.sweep_log_n.split(",")]:
+        with torch.cuda.stream(stream):
+            g = LC.Context.production(log_n, device=local, stream=stream)
+            w = S.Workload(f"sweep_N2^{log_n}_n10_d2^20", S.CFG_PLAIN, log_n, 10, 1 << 20, 0, (8, 9), "flip5", 6, 2)
+            N = g.N
+            cands = autotune.candidate_schedules(log_n)
+            rots = set()
+            for sc in cands.values():
+                rots |= set(LC.rotations_of_schedule(sc))
+            s = S.secret_key(w.seed, w.config, N)
+            pk = g.pk_gen(s, *S.pk_rand(w.seed, w.config, g.q, N))
+            evk = g.evk()
+            qp = g.q + g.p
+            evk.add(s, None, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, None))
+            for r in sorted(rots):
+                evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
+            X = S.split_chunks(S.client_updates(w), g.slots)
+            cts = g.empty(w.n_clients, w.chunks, 2, g.nq, N)
+            flat = cts.view(-1, 2, g.nq, N)
+            for i in range(w.n_clients):
+                m = np.stack([g.encode(X[i, k], g.scale) for k in range(w.chunks)])
+                r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [i], range(w.chunks), N)
+                g.encrypt(pk, m, r, e0, e1, out=flat[i * w.chunks:(i + 1) * w.chunks])
+            mm = np.zeros((w.n_clients, N), dtype=np.int64)
+            mm[:, 0] = int(round(g.scale / w.n_select))
+            r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), [S.MASK_CHUNK], N)
+            masks = g.encrypt(pk, mm, r, e0, e1)
+            out_d = g.empty(w.n_pairs, 2, g.L, N)
+            out_a = g.empty(w.chunks, 2, g.L, N)
+            tun = autotune.tune(g, evk, cts, w.n_clients, w.chunks, g.scale, schedules=cands, out=out_d)
+
+            def step():
+                g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=tun["mode"], groups=tun["groups"],
+                            out=out_d)
+                g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, out=out_a)
+
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                step()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / args.steps
+            print(json.dumps({"metric": "round time vs packing size (45 distances + masked aggregate)",
+                              "impl": "ours", "log_n": log_n, "slots": g.slots, "chunks": w.chunks,
+                              "ms_per_round": ms, "pairs_per_s": w.n_pairs / (ms / 1e3),
+                              "rotation_schedule": tun["schedule"], "tuning": tun["knobs"], "dtype": "u64",
+                              "data": "synthetic", "config": {"workload": w.name, "limbs_q": 15, "limbs_p": 4,
+                                                              "dnum": 4}}), flush=True)
+            del g, evk, cts, masks, out_d, out_a
+            torch.cuda.empty_cache()
+
+
 # ----------------------------------------------------------------------------- serving
 def build_serving(LC, g, tenants: int, sched, seed: int = 3, honest: int = 48, byz: int = 16):
     """Tenants with resident keys (relin + the rotation keys of the schedule) and, per
@@ -405,6 +475,8 @@ def main():
     ap.add_argument("--rounds", type=int, default=100, help="serving rounds per rate")
     ap.add_argument("--tenants", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
+    ap.add_argument("--sweep", action="store_true", help="packing-size sweep; one line per N")
+    ap.add_argument("--sweep-log-n", default="13,14,15,16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -413,6 +485,9 @@ def main():
         return
     if args.micro:
         run_micro(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.serving:
         # rounds of 0.1-75 GiB come and go: let the caching allocator grow segments instead of

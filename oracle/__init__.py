@@ -121,12 +121,13 @@ class Params:
         return self.N // 2
 
 
-def params_production() -> Params:
-    """N=2^15; q0 largest 60-bit prime = 1 mod 2N, p the next four, q1..q14 the largest 40-bit."""
-    q0 = gen_primes(15, 60, 0, 1)
-    p = gen_primes(15, 60, 1, 4)
-    q = q0 + gen_primes(15, 40, 0, 14)
-    return Params(15, q, p, 4, float(2 ** 40))
+def params_production(log_n: int = 15) -> Params:
+    """N=2^log_n (2^15 by default); q0 largest 60-bit prime = 1 mod 2N, p the next four, q1..q14
+    the largest 40-bit."""
+    q0 = gen_primes(log_n, 60, 0, 1)
+    p = gen_primes(log_n, 60, 1, 4)
+    q = q0 + gen_primes(log_n, 40, 0, 14)
+    return Params(log_n, q, p, 4, float(2 ** 40))
 
 
 def params_toy() -> Params:

@@ -214,11 +214,12 @@ def gen_primes(log_n: int, bits: int, skip: int, count: int) -> List[int]:
     return [int(x) for x in out[:count]]
 
 
-def production_primes():
-    """N = 2^15: q0 = largest 60-bit, p = next four 60-bit, q1..q14 = largest 40-bit (descending)."""
-    q0 = gen_primes(15, 60, 0, 1)
-    p = gen_primes(15, 60, 1, 4)
-    return 15, q0 + gen_primes(15, 40, 0, 14), p, 4, float(2 ** 40)
+def production_primes(log_n: int = 15):
+    """N = 2^log_n (2^15 by default): q0 = largest 60-bit prime = 1 mod 2N, p = the next four
+    60-bit ones, q1..q14 = the largest 40-bit ones (descending); dnum 4, scale 2^40."""
+    q0 = gen_primes(log_n, 60, 0, 1)
+    p = gen_primes(log_n, 60, 1, 4)
+    return log_n, q0 + gen_primes(log_n, 40, 0, 14), p, 4, float(2 ** 40)
 
 
 def toy_primes():
@@ -284,8 +285,10 @@ class Context:
         _LIVE.add(self)
 
     @classmethod
-    def production(cls, **kw):
-        log_n, q, p, dnum, scale = production_primes()
+    def production(cls, log_n: int = 15, **kw):
+        """The production modulus chain (60 + 14 x 40 bits, 4 x 60-bit special primes) at
+        N = 2^log_n (the packing-size sweep varies log_n; 15 is the evaluated setting)."""
+        log_n, q, p, dnum, scale = production_primes(log_n)
         return cls(log_n, q, p, dnum, scale, **kw)
 
     @classmethod

@@ -576,3 +576,29 @@ def test_overlapped_copies_match_stream_ordered_copies(toy):
     assert not LC.torch_to_u64(d).any()
     with pytest.raises(LC.LancelotError):
         g.copy_wait(10 ** 9)
+
+
+@pytest.mark.parametrize("log_n", [13, pytest.param(16, marks=pytest.mark.slow)])
+def test_other_ring_degrees_bit_exact(log_n):
+    """The packing-size sweep's rings (production primes at N = 2^13 and 2^16): distances of three
+    clients in one-ModDown groups of 7 rotations, bit-exact against the oracle."""
+    from paper_2408_06197_b300 import autotune
+    from paper_2408_06197_b300 import lancelot as LC
+    prm = O.params_production(log_n)
+    o = O.Context(prm)
+    g = LC.Context.production(log_n)
+    sched = autotune.candidate_schedules(log_n)["g3qp"]
+    keys = KeySet(prm, 5, S.CFG_PLAIN, O.rotations_of_schedule(sched))
+    opk, orlk, ork = keys.oracle_keys(o)
+    gpk, gevk = keys.gpu_keys(g)
+    w = S.Workload(f"ring{log_n}", S.CFG_PLAIN, log_n, 3, prm.slots + 11, 5, (2,), "flip5", 1, 0)
+    X = S.split_chunks(S.client_updates(w), prm.slots)
+    m = plaintexts(o, prm, X).reshape(-1, prm.N)
+    r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(3), range(w.chunks), prm.N)
+    ocs = np.stack([o.encrypt(opk, m[k], r[k], e0[k], e1[k]) for k in range(m.shape[0])]).reshape(
+        3, w.chunks, 2, prm.L + 1, prm.N)
+    gcs = g.encrypt(gpk, m, r, e0, e1).reshape(3, w.chunks, 2, prm.L + 1, prm.N)
+    Dg, _ = g.distances(gevk, gcs, 3, w.chunks, prm.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
+                        groups=sched)
+    Do = o.distances(ocs, orlk, sched, ork, qp_sum=True)
+    assert np.array_equal(LC.torch_to_u64(g.to_coeff(Dg, prm.L - 1)), o.to_coeff(Do))
