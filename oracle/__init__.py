@@ -31,6 +31,8 @@ def lib():
         L = ctypes.CDLL(path)
         vp = ctypes.c_void_p
         L.or_gen_primes.argtypes = [ctypes.c_int] * 4 + [vp]
+        L.or_philox4x64.argtypes = [vp, vp, vp]
+        L.or_sample_enc.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         L.or_ctx_new.restype = vp
         L.or_ctx_new.argtypes = [ctypes.c_int] * 4 + [vp, vp]
         L.or_ctx_free.argtypes = [vp]
@@ -94,6 +96,26 @@ def gen_primes(log_n: int, bits: int, skip: int, count: int) -> List[int]:
     if lib().or_gen_primes(log_n, bits, skip, count, _p(out)) != 0:
         raise ValueError("not enough primes")
     return [int(x) for x in out[:count]]
+
+
+def philox4x64(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
+    """One Philox4x64-10 block (four 64-bit words) for a 256-bit counter and 128-bit key."""
+    c = np.array(ctr, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    o = np.zeros(4, dtype=np.uint64)
+    lib().or_philox4x64(_p(c), _p(k), _p(o))
+    return [int(x) for x in o]
+
+
+def sample_enc(seed: int, first: int, count: int, n: int):
+    """Device-randomness mode: (r int8, e0 int32, e1 int32), each [count][n], of ciphertexts
+    first .. first+count-1 (Philox4x64-10; ternary r by multiply-shift, centred-binomial errors
+    with eta = 21)."""
+    r = np.zeros((count, n), dtype=np.int8)
+    e0 = np.zeros((count, n), dtype=np.int32)
+    e1 = np.zeros((count, n), dtype=np.int32)
+    lib().or_sample_enc(seed, first, count, n, _p(r), _p(e0), _p(e1))
+    return r, e0, e1
 
 
 @dataclasses.dataclass

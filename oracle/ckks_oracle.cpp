@@ -449,7 +449,67 @@ static int rotate_sum(OrCtx& c, u64* ct, int level, int n_groups, const int* gro
 }
 
 // ------------------------------------------------------------------ C API
+// ---------------------------------------------------------------------------------------
+// Device-randomness mode: the counter-based generator Philox4x64-10 (Salmon, Moraes, Dror,
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011), written from its definition:
+// ten rounds of two 64x64 -> 128-bit multiplications and a Weyl-sequence key schedule.
+// Sampling rules (shared by definition with the library, not by code):
+//   key = (seed, 0); counter = (coefficient k, ciphertext index c, purpose p, 0), p = 0 for the
+//   ephemeral r, 1 for e0, 2 for e1; one block of four words per (k, c, p);
+//   r = floor(3 * (word0 >> 32) / 2^32) - 1  in {-1, 0, 1};
+//   e = popcount(word0 mod 2^21) - popcount(word1 mod 2^21)  (centred binomial, eta = 21).
+static void philox4x64_10(const u64 ctr[4], const u64 key[2], u64 out[4]) {
+    const u64 M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const u64 W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    u64 x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const u128 p0 = (u128)M0 * x0, p1 = (u128)M1 * x2;
+        const u64 hi0 = (u64)(p0 >> 64), lo0 = (u64)p0, hi1 = (u64)(p1 >> 64), lo1 = (u64)p1;
+        const u64 y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+static int popcount64(u64 v) {
+    int n = 0;
+    for (; v; v &= v - 1) n++;
+    return n;
+}
+
 extern "C" {
+
+void or_philox4x64(const u64* ctr, const u64* key, u64* out) { philox4x64_10(ctr, key, out); }
+
+// encryption randomness of ciphertexts first .. first+count-1 (rows of n coefficients)
+void or_sample_enc(u64 seed, u64 first, int count, int n, int8_t* r, int32_t* e0, int32_t* e1) {
+    const u64 key[2] = {seed, 0};
+    const u64 m21 = (1ull << 21) - 1;
+    for (int b = 0; b < count; b++)
+        for (int k = 0; k < n; k++) {
+            u64 o[4];
+            const size_t i = (size_t)b * n + k;
+            u64 ctr[4] = {(u64)k, first + (u64)b, 0, 0};
+            philox4x64_10(ctr, key, o);
+            r[i] = (int8_t)((int)(((o[0] >> 32) * 3) >> 32) - 1);
+            ctr[2] = 1;
+            philox4x64_10(ctr, key, o);
+            e0[i] = popcount64(o[0] & m21) - popcount64(o[1] & m21);
+            ctr[2] = 2;
+            philox4x64_10(ctr, key, o);
+            e1[i] = popcount64(o[0] & m21) - popcount64(o[1] & m21);
+        }
+}
 
 int or_gen_primes(int log_n, int bits, int skip, int count, u64* out) {
     const u64 M = (u64)2 << log_n;  // 2N

@@ -438,3 +438,53 @@ def test_production_parameters_square_relin_rescale_rotate():
     assert np.abs(ctx.decrypt(s, sq, prm.L - 1, sc) - z * z).max() < 1e-6
     rot = ctx.rotate_hoisted(sq, prm.L - 1, [5], [rk5])[0]
     assert np.abs(ctx.decrypt(s, rot, prm.L - 1, sc) - np.roll(z * z, -5)).max() < 1e-6
+
+
+# ------------------------------------------------------------------------- device-randomness mode
+
+def _numpy_philox_block(ctr, key):
+    """numpy's Philox4x64-10 bit generator advances its counter before each block, so the block
+    of counter c is the first output of a generator started at c - 1 (256-bit little-endian)."""
+    c = list(ctr)
+    for i in range(4):  # c - 1 with borrow
+        if c[i] > 0:
+            c[i] -= 1
+            break
+        c[i] = (1 << 64) - 1
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(c, dtype=np.uint64))
+    return [int(v) for v in bg.random_raw(4)]
+
+
+def test_philox_matches_numpy_bit_generator():
+    g = np.random.default_rng(31)
+    cases = [([0, 0, 0, 0], [0, 0]), ([1, 0, 0, 0], [0, 0]), ([0, 0, 0, 1], [2 ** 64 - 1, 5])]
+    for _ in range(20):
+        cases.append(([int(v) for v in g.integers(0, 2 ** 63, 4)], [int(v) for v in g.integers(0, 2 ** 63, 2)]))
+    for ctr, key in cases:
+        assert O.philox4x64(ctr, key) == _numpy_philox_block(ctr, key)
+
+
+def test_encryption_sampler_follows_its_rule_and_distribution():
+    seed, first, count, n = 77, 1000, 3, 4096
+    r, e0, e1 = O.sample_enc(seed, first, count, n)
+    # the rule, recomputed from numpy's generator for a few coefficients
+    m21 = (1 << 21) - 1
+    for b, k in [(0, 0), (1, 17), (2, n - 1)]:
+        w = _numpy_philox_block([k, first + b, 0, 0], [seed, 0])
+        assert r[b, k] == (((w[0] >> 32) * 3) >> 32) - 1
+        for p, e in ((1, e0), (2, e1)):
+            w = _numpy_philox_block([k, first + b, p, 0], [seed, 0])
+            assert e[b, k] == bin(w[0] & m21).count("1") - bin(w[1] & m21).count("1")
+    # distributions: ternary uniform, centred binomial with variance 21/2
+    vals, counts = np.unique(r, return_counts=True)
+    assert list(vals) == [-1, 0, 1]
+    expect = r.size / 3
+    assert ((counts - expect) ** 2 / expect).sum() < 20  # chi-square, 2 dof
+    e = np.concatenate([e0.ravel(), e1.ravel()])
+    assert np.abs(e).max() <= 21
+    assert abs(e.mean()) < 0.05 and abs(e.var() - 10.5) < 0.3
+    # ciphertext index and seed change the draws
+    r2, _, _ = O.sample_enc(seed, first + 1, 1, n)
+    assert np.array_equal(r2[0], r[1]) and not np.array_equal(r2[0], r[0])
+    r3, _, _ = O.sample_enc(seed + 1, first, 1, n)
+    assert not np.array_equal(r3[0], r[0])
