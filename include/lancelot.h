@@ -198,6 +198,25 @@ int lc_decode(lc_ctx* ctx, const double* m, double scale, double* z_out);
 int lc_encrypt(lc_ctx* ctx, const uint64_t* pk, const int64_t* m, const int8_t* r, const int32_t* e0,
                const int32_t* e1, uint32_t count, uint64_t* out);
 
+/* Device-randomness mode (no counterpart in the paper, which leaves the sampler open): the
+ * encryption randomness is drawn on the GPU from the counter-based generator Philox4x64-10
+ * (Salmon et al., SC 2011) instead of being supplied by the caller.  Key (seed, 0); counter
+ * (coefficient k, ciphertext index c, purpose p, 0) with p = 0 for r, 1 for e0, 2 for e1;
+ * r = floor(3 (word0 >> 32) / 2^32) - 1; e = popcount(word0 mod 2^21) - popcount(word1 mod
+ * 2^21) (centred binomial, eta = 21, sigma = 3.24).  Ciphertext b of a call has index
+ * first + b, so disjoint index ranges give independent randomness for one seed.
+ * lc_sample_enc returns the draws ([count][N] each, host memory) for checking.
+ * lc_encrypt_seeded: Section "CKKS Scheme Description" Enc with these draws; m_dev = device
+ * plaintexts [count][N] int64 (centred integers); out as lc_encrypt.
+ * lc_encrypt_const_seeded: the same for constant-slot plaintexts (coefficient 0 =
+ * round(w_dev[b] * scale), the others 0): the KGC's mask ciphertexts (Section "Masked-based
+ * Encrypted Sorting").  Neither call synchronises the host, so both can be graph-captured. */
+int lc_sample_enc(lc_ctx* ctx, uint64_t seed, uint64_t first, uint32_t count, int8_t* r, int32_t* e0, int32_t* e1);
+int lc_encrypt_seeded(lc_ctx* ctx, const uint64_t* pk, const int64_t* m_dev, uint32_t count, uint64_t seed,
+                      uint64_t first, uint64_t* out);
+int lc_encrypt_const_seeded(lc_ctx* ctx, const uint64_t* pk, const double* w_dev, uint32_t count, double scale,
+                            uint64_t seed, uint64_t first, uint64_t* out);
+
 /* CKKS.Dec (Section "CKKS Scheme Description", Decryption): residues of c0 + c1 s (+ c2 s^2)
  * mod Q_level.  ct: device [deg][level+1][N] (deg 2 or 3); s: host int8[N];
  * res_out: host uint64[level+1][N], coefficient domain. */
@@ -209,6 +228,27 @@ int lc_decrypt(lc_ctx* ctx, const int8_t* s, const uint64_t* ct, uint32_t deg, u
  * [count][2][level+1][N]; out: host double[count]. */
 int lc_decrypt_const(lc_ctx* ctx, const int8_t* s, const uint64_t* cts, uint32_t count, uint32_t level, double scale,
                      double* out);
+/* KGC step on the device (Alg. 2 and the mask of Section "Masked-based Encrypted Sorting"; no
+ * counterpart in the paper's GPU design, whose KGC runs on the host).  A resident KGC key keeps
+ * the secret mod q0 on the device:
+ *   lc_kgc_create: s = ternary secret [N] (host); lc_kgc_free releases it (before its context).
+ *   lc_kgc_readout: as lc_decrypt_const, but the `count` values go to out_dev (device doubles)
+ *                   and the host is not synchronised.
+ *   lc_kgc_krum:    Krum / Multi-Krum on n <= 256 clients from pair distances dist_dev
+ *                   (n(n-1)/2 doubles, i < j lexicographic): score_i = sum of the n - f - 2
+ *                   smallest d(i, j); the n_select lowest scores are kept (ties to the lower
+ *                   index); w_dev[i] = 1/n_select (average) or 1 for kept clients, 0 otherwise;
+ *                   sel_dev = kept indices in score order.
+ * With lc_encrypt_const_seeded for the masks, a whole round (distances, read-out, selection,
+ * masks, aggregate) runs without a host round trip and can be captured in one graph. */
+typedef struct lc_kgc lc_kgc;
+int lc_kgc_create(lc_ctx* ctx, const int8_t* s, lc_kgc** out);
+void lc_kgc_free(lc_kgc* kgc);
+int lc_kgc_readout(lc_ctx* ctx, const lc_kgc* kgc, const uint64_t* cts, uint32_t count, uint32_t level, double scale,
+                   double* out_dev);
+int lc_kgc_krum(lc_ctx* ctx, const double* dist_dev, uint32_t n, uint32_t f, uint32_t n_select, int average,
+                double* w_dev, int32_t* sel_dev);
+
 /* Centred CRT of residues[level+1][N] (host) to doubles m_out[N] (host), exact big-integer. */
 int lc_crt_to_double(lc_ctx* ctx, const uint64_t* res, uint32_t level, double* m_out);
 

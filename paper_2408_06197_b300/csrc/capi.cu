@@ -882,6 +882,85 @@ int lc_encrypt(lc_ctx* c, const uint64_t* pk, const int64_t* m, const int8_t* r,
     return check_launch(c, "lc_encrypt");
 }
 
+int lc_sample_enc(lc_ctx* c, uint64_t seed, uint64_t first, uint32_t count, int8_t* r, int32_t* e0, int32_t* e1) {
+    clear_prior_error();
+    if (!c || (count && (!r || !e0 || !e1))) return fail(c, LC_EINVAL, "lc_sample_enc: null argument");
+    if (count == 0) return LC_OK;
+    const size_t n = (size_t)count * c->N;
+    unsigned char* t = reinterpret_cast<unsigned char*>(lc_scratch(c, n * 9 + 64));
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    int32_t* d0 = reinterpret_cast<int32_t*>(t);
+    int32_t* d1 = d0 + n;
+    int8_t* dr = reinterpret_cast<int8_t*>(d1 + n);
+    op_sample_enc(c, seed, first, (int)count, dr, d0, d1);
+    LC_CUDA(c, cudaMemcpyAsync(r, dr, n, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaMemcpyAsync(e0, d0, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaMemcpyAsync(e1, d1, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "lc_sample_enc");
+}
+
+// encryption of `count` device plaintexts (m_dev, [count][N] int64) or constant-slot values
+// (w_dev, [count] doubles, coefficient 0 = round(w scale)) with device randomness; no host
+// synchronisation, so it may be captured in a graph (scratch must be sized beforehand).
+static int encrypt_seeded(lc_ctx* c, const uint64_t* pk, const int64_t* m_dev, const double* w_dev, double scale,
+                          uint32_t count, uint64_t seed, uint64_t first, uint64_t* out) {
+    const size_t N = c->N;
+    const int nq = c->nq;
+    const size_t P = (size_t)nq * N;
+    const uint32_t slice = std::max<uint32_t>(1, std::min<uint32_t>(count, 64));
+    // 4 RNS regions + int64 plaintexts (N words) + two int32 error rows (N words) + ternary bytes
+    const size_t words = (size_t)4 * slice * P + (size_t)slice * N * 3 + 64;
+    u64* t = lc_scratch(c, words * 8);
+    if (!t) return fail(c, LC_ENOMEM, "scratch");
+    std::vector<int> mods(nq);
+    for (int i = 0; i < nq; i++) mods[i] = i;
+    for (uint32_t b0 = 0; b0 < count; b0 += slice) {
+        const int B = (int)std::min(slice, count - b0);
+        u64* mr = t;
+        u64* rr = mr + (size_t)slice * P;
+        u64* x0 = rr + (size_t)slice * P;
+        u64* x1 = x0 + (size_t)slice * P;
+        int64_t* mplain = reinterpret_cast<int64_t*>(x1 + (size_t)slice * P);  // [slice][N]
+        int32_t* de0 = reinterpret_cast<int32_t*>(mplain + (size_t)slice * N);
+        int32_t* de1 = de0 + (size_t)slice * N;
+        int8_t* dr = reinterpret_cast<int8_t*>(de1 + (size_t)slice * N);
+        const int64_t* mb = m_dev ? m_dev + (size_t)b0 * N : mplain;
+        if (!m_dev) op_const_plain(c, w_dev + b0, B, scale, mplain);
+        op_to_rns_i64(c, mb, B, mods.data(), nq, mr);
+        op_sample_enc(c, seed, first + b0, B, dr, de0, de1);
+        op_to_rns_i8(c, dr, B, mods.data(), nq, rr);
+        op_to_rns_i32(c, de0, B, mods.data(), nq, x0);
+        op_to_rns_i32(c, de1, B, mods.data(), nq, x1);
+        if (B == (int)slice) {
+            ntt_polys(c, mr, 4 * B, nq, true);
+        } else {
+            ntt_polys(c, mr, B, nq, true);
+            ntt_polys(c, rr, B, nq, true);
+            ntt_polys(c, x0, B, nq, true);
+            ntt_polys(c, x1, B, nq, true);
+        }
+        op_enc_combine(c, mr, rr, x0, x1, pk, B, nq, out + (size_t)b0 * 2 * P);
+    }
+    return check_launch(c, "encrypt (device randomness)");
+}
+
+int lc_encrypt_seeded(lc_ctx* c, const uint64_t* pk, const int64_t* m_dev, uint32_t count, uint64_t seed,
+                      uint64_t first, uint64_t* out) {
+    clear_prior_error();
+    if (!c || !pk || !out || (count && !m_dev)) return fail(c, LC_EINVAL, "lc_encrypt_seeded: null argument");
+    if (count == 0) return LC_OK;
+    return encrypt_seeded(c, pk, m_dev, nullptr, 0.0, count, seed, first, out);
+}
+
+int lc_encrypt_const_seeded(lc_ctx* c, const uint64_t* pk, const double* w_dev, uint32_t count, double scale,
+                            uint64_t seed, uint64_t first, uint64_t* out) {
+    clear_prior_error();
+    if (!c || !pk || !out || (count && !w_dev)) return fail(c, LC_EINVAL, "lc_encrypt_const_seeded: null argument");
+    if (count == 0) return LC_OK;
+    return encrypt_seeded(c, pk, nullptr, w_dev, scale, count, seed, first, out);
+}
+
 int lc_decrypt(lc_ctx* c, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out) {
     clear_prior_error();
     if (!c || !s || !ct || !res_out || deg < 2 || deg > 3) return fail(c, LC_EINVAL, "lc_decrypt: bad argument");
@@ -931,6 +1010,61 @@ int lc_decrypt_const(lc_ctx* c, const int8_t* s, const uint64_t* cts, uint32_t c
         out[k] = v / scale;
     }
     return check_launch(c, "lc_decrypt_const");
+}
+
+// ------------------------------------------------------------------------------- KGC on the device
+struct lc_kgc {
+    lc_ctx* c = nullptr;
+    u64* s0 = nullptr;  // secret mod q0, evaluation domain (limb 0)
+};
+
+int lc_kgc_create(lc_ctx* c, const int8_t* s, lc_kgc** out) {
+    clear_prior_error();
+    if (!c || !s || !out) return fail(c, LC_EINVAL, "lc_kgc_create: null argument");
+    const size_t N = c->N;
+    auto* k = new lc_kgc;
+    k->c = c;
+    k->s0 = static_cast<u64*>(lc_dev_alloc(c, N * 8));
+    u64* raw = lc_scratch(c, N * 8);
+    if (!k->s0 || !raw) {
+        if (k->s0) lc_dev_free(c, k->s0);
+        delete k;
+        return fail(c, LC_ENOMEM, "lc_kgc_create");
+    }
+    const int mods[1] = {0};
+    LC_CUDA(c, cudaMemcpyAsync(raw, s, N, cudaMemcpyHostToDevice, c->stream));
+    op_to_rns_i8(c, reinterpret_cast<const int8_t*>(raw), 1, mods, 1, k->s0);
+    RowMap m = rows_seq(1);
+    ntt_fwd_p(c, k->s0, N, 1, m);
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = k;
+    return check_launch(c, "lc_kgc_create");
+}
+
+void lc_kgc_free(lc_kgc* k) {
+    if (!k) return;
+    cudaStreamSynchronize(k->c->stream);
+    lc_dev_free(k->c, k->s0);
+    delete k;
+}
+
+int lc_kgc_readout(lc_ctx* c, const lc_kgc* k, const uint64_t* cts, uint32_t count, uint32_t level, double scale,
+                   double* out_dev) {
+    if (!c || !k || !cts || !out_dev || (int)level >= c->nq) return fail(c, LC_EINVAL, "lc_kgc_readout: bad argument");
+    if (count == 0) return LC_OK;
+    u64* res = lc_scratch(c, ((size_t)count + 8) * 8);
+    if (!res) return fail(c, LC_ENOMEM, "scratch");
+    op_const_coef0(c, cts, (size_t)2 * (level + 1) * c->N, (int)count, k->s0, res);
+    op_readout_finish(c, res, (int)count, scale, out_dev);
+    return check_launch(c, "lc_kgc_readout");
+}
+
+int lc_kgc_krum(lc_ctx* c, const double* dist_dev, uint32_t n, uint32_t f, uint32_t n_select, int average,
+                double* w_dev, int32_t* sel_dev) {
+    if (!c || !dist_dev || !w_dev || !sel_dev || n < 1 || n > 256 || n_select < 1 || n_select > n)
+        return fail(c, LC_EINVAL, "lc_kgc_krum: bad argument (1 <= n_select <= n <= 256)");
+    op_krum(c, dist_dev, (int)n, (int)f, (int)n_select, average ? 1 : 0, w_dev, sel_dev);
+    return check_launch(c, "lc_kgc_krum");
 }
 
 int lc_crt_to_double(lc_ctx* c, const uint64_t* res, uint32_t level, double* m_out) {

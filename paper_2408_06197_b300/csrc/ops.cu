@@ -409,6 +409,127 @@ __global__ void __launch_bounds__(kT) k_mask_acc(const u64* __restrict__ cts, in
     }
 }
 
+// ---------------------------------------------------------------------------- device randomness
+// Philox4x64-10 (Salmon et al., SC 2011) from its definition; sampling rules: key = (seed, 0),
+// counter = (coefficient, ciphertext index, purpose, 0); ternary r from the top 32 bits of word 0
+// by multiply-shift; errors centred binomial with eta = 21 from words 0 and 1.
+__device__ __forceinline__ void philox4x64_10(u64& x0, u64& x1, u64& x2, u64& x3, u64 k0, u64 k1) {
+    const u64 M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const u64 W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const u64 hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+        const u64 hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+        const u64 y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+}
+
+__global__ void k_sample_enc(u64 seed, u64 first, int count, int log_n, int8_t* __restrict__ r,
+                             int32_t* __restrict__ e0, int32_t* __restrict__ e1) {
+    const size_t N = (size_t)1 << log_n;
+    const size_t total = (size_t)count * N;
+    const u64 m21 = (1ull << 21) - 1;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const u64 k = i & (N - 1), c = first + (i >> log_n);
+        u64 a = k, b = c, d = 0, e = 0;
+        philox4x64_10(a, b, d, e, seed, 0);
+        r[i] = (int8_t)((int)(((a >> 32) * 3) >> 32) - 1);
+        a = k, b = c, d = 1, e = 0;
+        philox4x64_10(a, b, d, e, seed, 0);
+        e0[i] = __popcll(a & m21) - __popcll(b & m21);
+        a = k, b = c, d = 2, e = 0;
+        philox4x64_10(a, b, d, e, seed, 0);
+        e1[i] = __popcll(a & m21) - __popcll(b & m21);
+    }
+}
+
+// constant-slot plaintexts: m[b] = (round(w[b] * scale), 0, ..., 0)
+__global__ void k_const_plain(const double* __restrict__ w, int count, int log_n, double scale,
+                              int64_t* __restrict__ m) {
+    const size_t N = (size_t)1 << log_n;
+    const size_t total = (size_t)count * N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        m[i] = (i & (N - 1)) ? 0 : __double2ll_rn(w[i >> log_n] * scale);
+}
+
+// ---------------------------------------------------------------------------- KGC step on the device
+// read-out values: centred residue mod q0 divided by the scale
+__global__ void k_readout_finish(const u64* __restrict__ res, int count, const ModConst* __restrict__ mc,
+                                 double scale, double* __restrict__ out) {
+    const u64 q0 = mc[0].q;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+        const u64 v = res[b];
+        out[b] = (v > q0 / 2 ? -(double)(q0 - v) : (double)v) / scale;
+    }
+}
+
+// Krum / Multi-Krum (Algorithm 2) on n <= 256 clients from the pair distances d (i < j,
+// lexicographic): score_i = sum of the n - f - 2 smallest d(i, j), j != i; the l lowest scores are
+// kept (stable: ties go to the lower index); w_i = 1 / l (average) or 1 for kept clients, else 0.
+// One block of at least n threads.
+__global__ void k_krum(const double* __restrict__ d, int n, int f, int l, int average, double* __restrict__ w,
+                       int* __restrict__ sel) {
+    __shared__ double score[256];
+    const int i = threadIdx.x;
+    const int k = max(0, n - f - 2);
+    if (i < n) {
+        // the k smallest of row i by repeated minimum (n <= 256, k < n): ascending order, summed
+        // in that order
+        double last = -1.0;
+        int last_j = -1;
+        double sum = 0.0;
+        for (int t = 0; t < k; t++) {
+            double best = 0.0;
+            int bj = -1;
+            for (int j = 0; j < n; j++) {
+                if (j == i) continue;
+                const int a = min(i, j), b = max(i, j);
+                const double v = d[a * n - a * (a + 1) / 2 + (b - a - 1)];
+                // strictly after (last, last_j) in (value, index) order
+                const bool after = v > last || (v == last && j > last_j);
+                if (after && (bj < 0 || v < best || (v == best && j < bj))) {
+                    best = v;
+                    bj = j;
+                }
+            }
+            sum += best;
+            last = best;
+            last_j = bj;
+        }
+        score[i] = sum;
+        w[i] = 0.0;
+    }
+    __syncthreads();
+    if (i == 0) {
+        int lastc = -1;
+        double lasts = 0.0;
+        for (int t = 0; t < l; t++) {
+            int bc = -1;
+            double bs = 0.0;
+            for (int c2 = 0; c2 < n; c2++) {
+                const double v = score[c2];
+                const bool after = lastc < 0 || v > lasts || (v == lasts && c2 > lastc);
+                if (after && (bc < 0 || v < bs)) {
+                    bs = v;
+                    bc = c2;
+                }
+            }
+            sel[t] = bc;
+            w[bc] = average ? 1.0 / l : 1.0;
+            lastc = bc;
+            lasts = bs;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------- multi-job items
 // tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
 template <bool SPLIT>
@@ -1413,6 +1534,29 @@ void op_dec_combine(lc_ctx* c, const u64* ct, const u64* s, int deg, int nl, u64
 void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods, int nrows) {
     ModList ml = make_list(mods, nrows);
     k_square_rows<<<grid_for((size_t)nrows * c->N), kT, 0, c->stream>>>(s, out, ml, c->log_n, c->mc);
+    g_lc_launches += 1;
+}
+
+void op_readout_finish(lc_ctx* c, const u64* res, int count, double scale, double* out) {
+    if (count <= 0) return;
+    k_readout_finish<<<(count + kT - 1) / kT, kT, 0, c->stream>>>(res, count, c->mc, scale, out);
+    g_lc_launches += 1;
+}
+
+void op_krum(lc_ctx* c, const double* d, int n, int f, int l, int average, double* w, int* sel) {
+    k_krum<<<1, 256, 0, c->stream>>>(d, n, f, l, average, w, sel);
+    g_lc_launches += 1;
+}
+
+void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1) {
+    if (count <= 0) return;
+    k_sample_enc<<<grid_for((size_t)count * c->N), kT, 0, c->stream>>>(seed, first, count, c->log_n, r, e0, e1);
+    g_lc_launches += 1;
+}
+
+void op_const_plain(lc_ctx* c, const double* w, int count, double scale, int64_t* m) {
+    if (count <= 0) return;
+    k_const_plain<<<grid_for((size_t)count * c->N), kT, 0, c->stream>>>(w, count, c->log_n, scale, m);
     g_lc_launches += 1;
 }
 

@@ -86,6 +86,13 @@ void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, in
                     const u64* const* keys_dev, int T, u64* v, size_t v_key_stride);
 // dst_dev[b] <- src + b * words (words per item)
 void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev, int B);
+// KGC step: read-out values (centred residue mod q0 / scale) and Krum / Multi-Krum selection
+void op_readout_finish(lc_ctx* c, const u64* res, int count, double scale, double* out);
+void op_krum(lc_ctx* c, const double* d, int n, int f, int l, int average, double* w, int* sel);
+// device randomness (Philox4x64-10): r, e0, e1 [count][N] of ciphertexts first .. first+count-1
+void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1);
+// constant-slot plaintexts m[b] = (round(w[b] scale), 0, ..., 0), [count][N]
+void op_const_plain(lc_ctx* c, const double* w, int count, double scale, int64_t* m);
 // coefficient 0 (mod q0) of c0 + c1 s for `count` ciphertexts (stride ct_stride words), s0 = s in
 // the evaluation domain of limb 0
 void op_const_coef0(lc_ctx* c, const u64* cts, size_t ct_stride, int count, const u64* s0, u64* out);

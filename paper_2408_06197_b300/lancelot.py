@@ -65,7 +65,7 @@ _LIVE = weakref.WeakSet()  # contexts, key sets and graphs still holding library
 def _close_all():
     """Releases every live handle at interpreter exit, while torch and CUDA are still up."""
     objs = list(_LIVE)
-    for kind in (Graph, EvalKeys, Context):
+    for kind in (Graph, KgcKey, EvalKeys, Context):
         for o in objs:
             if isinstance(o, kind):
                 try:
@@ -140,6 +140,13 @@ def lib() -> ctypes.CDLL:
             "lc_batch_distances": [vp, vp, u32, u32, u32, vp],
             "lc_batch_aggregate": [vp, vp, u32],
             "lc_decrypt_const": [vp, vp, vp, u32, u32, ctypes.c_double, vp],
+            "lc_sample_enc": [vp, ctypes.c_uint64, ctypes.c_uint64, u32, vp, vp, vp],
+            "lc_encrypt_seeded": [vp, vp, vp, u32, ctypes.c_uint64, ctypes.c_uint64, vp],
+            "lc_encrypt_const_seeded": [vp, vp, vp, u32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, vp],
+            "lc_kgc_create": [vp, vp, vp],
+            "lc_kgc_free": [vp],
+            "lc_kgc_readout": [vp, vp, vp, u32, u32, ctypes.c_double, vp],
+            "lc_kgc_krum": [vp, vp, u32, u32, u32, ctypes.c_int, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -472,6 +479,44 @@ class Context:
                                            level, scale, _np_ptr(out)), "lc_decrypt_const")
         return out
 
+    # ------------------------------------------------------------------ device randomness
+    def sample_enc(self, seed: int, first: int, count: int):
+        """The device-randomness draws (r int8, e0 int32, e1 int32; [count][N]) of ciphertexts
+        first .. first+count-1."""
+        r = np.zeros((count, self.N), dtype=np.int8)
+        e0 = np.zeros((count, self.N), dtype=np.int32)
+        e1 = np.zeros((count, self.N), dtype=np.int32)
+        self._check(lib().lc_sample_enc(self.h, int(seed), int(first), int(count), _np_ptr(r), _np_ptr(e0),
+                                        _np_ptr(e1)), "lc_sample_enc")
+        return r, e0, e1
+
+    def encrypt_seeded(self, pk: torch.Tensor, m: torch.Tensor, seed: int, first: int,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Encrypt device plaintexts m ([count][N] int64 tensor) with device randomness."""
+        count = _whole(m, self.N, "encrypt_seeded: m")
+        _need(pk, 2 * self.nq * self.N, "encrypt_seeded: pk")
+        if out is None:
+            out = self.empty(count, 2, self.nq, self.N)
+        _need(out, count * 2 * self.nq * self.N, "encrypt_seeded: out")
+        self._check(lib().lc_encrypt_seeded(self.h, _t_ptr(pk), _t_ptr(m), count, int(seed), int(first),
+                                            _t_ptr(out)), "lc_encrypt_seeded")
+        return out
+
+    def encrypt_const_seeded(self, pk: torch.Tensor, w: torch.Tensor, scale: float, seed: int, first: int,
+                             out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Constant-slot ciphertexts (coefficient 0 = round(w[b] scale)) from device doubles w."""
+        if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous():
+            raise LancelotError("encrypt_const_seeded: w must be a contiguous float64 CUDA tensor")
+        count = w.numel()
+        _need(pk, 2 * self.nq * self.N, "encrypt_const_seeded: pk")
+        if out is None:
+            out = self.empty(count, 2, self.nq, self.N)
+        _need(out, count * 2 * self.nq * self.N, "encrypt_const_seeded: out")
+        self._check(lib().lc_encrypt_const_seeded(self.h, _t_ptr(pk), ctypes.c_void_p(w.data_ptr()), count,
+                                                  float(scale), int(seed), int(first), _t_ptr(out)),
+                    "lc_encrypt_const_seeded")
+        return out
+
     def decrypt(self, s: np.ndarray, ct: torch.Tensor, level: int, scale: float) -> np.ndarray:
         res = self.decrypt_residues(s, ct, level)
         m = np.zeros(self.N, dtype=np.float64)
@@ -695,6 +740,62 @@ class EvalKeys:
         if getattr(self, "h", None):
             if getattr(self.ctx, "h", None):  # the keys are freed through their (live) context
                 lib().lc_evk_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KgcKey:
+    """The KGC's secret resident on the device (mod q0) for the device-side KGC step: read-out
+    of the distance ciphertexts and Krum / Multi-Krum selection, without host round trips."""
+
+    def __init__(self, ctx: Context, s: np.ndarray):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._check(lib().lc_kgc_create(ctx.h, _np_ptr(np.ascontiguousarray(s, np.int8)), ctypes.byref(h)),
+                   "lc_kgc_create")
+        self.h = h
+        ctx._deps.add(self)
+        _LIVE.add(self)
+
+    def readout(self, cts: torch.Tensor, level: int, scale: float,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Slot value of each constant-slot ciphertext, into a device float64 tensor."""
+        c = self.ctx
+        count = _whole(cts, 2 * (level + 1) * c.N, "kgc readout")
+        if out is None:
+            out = torch.empty(count, dtype=torch.float64, device=cts.device)
+        if out.dtype != torch.float64 or out.numel() != count or not out.is_contiguous():
+            raise LancelotError("kgc readout: out must be a contiguous float64 tensor of one value per ciphertext")
+        c._check(lib().lc_kgc_readout(c.h, self.h, _t_ptr(cts), count, level, float(scale),
+                                      ctypes.c_void_p(out.data_ptr())), "lc_kgc_readout")
+        return out
+
+    def krum(self, dist: torch.Tensor, n: int, f: int, n_select: int, average: bool = True,
+             w: Optional[torch.Tensor] = None, sel: Optional[torch.Tensor] = None):
+        """(weights [n] float64, kept indices [n_select] int32), both on the device (pass w and
+        sel to reuse buffers, e.g. inside a graph capture)."""
+        c = self.ctx
+        if dist.dtype != torch.float64 or dist.numel() != n * (n - 1) // 2 or not dist.is_contiguous():
+            raise LancelotError("kgc krum: dist must hold n(n-1)/2 contiguous float64 values")
+        if w is None:
+            w = torch.empty(n, dtype=torch.float64, device=dist.device)
+        if sel is None:
+            sel = torch.empty(n_select, dtype=torch.int32, device=dist.device)
+        if w.dtype != torch.float64 or w.numel() != n or sel.dtype != torch.int32 or sel.numel() != n_select:
+            raise LancelotError("kgc krum: w must hold n float64 values and sel n_select int32 values")
+        c._check(lib().lc_kgc_krum(c.h, ctypes.c_void_p(dist.data_ptr()), n, f, n_select, 1 if average else 0,
+                                   ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(sel.data_ptr())), "lc_kgc_krum")
+        return w, sel
+
+    def close(self):
+        if getattr(self, "h", None):
+            if getattr(self.ctx, "h", None):
+                lib().lc_kgc_free(self.h)
             self.h = None
 
     def __del__(self):

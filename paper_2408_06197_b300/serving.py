@@ -192,3 +192,35 @@ def latency_summary(done: Sequence[Round]) -> Dict[str, float]:
     kg = np.array([r.kgc_seconds for r in done]) * 1e3
     return {"rounds": len(done), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "kgc_p50_ms": float(np.percentile(kg, 50)), "pairs": int(sum(r.pairs for r in done))}
+
+
+def round_on_device(ctx: "LC.Context", evk: "LC.EvalKeys", pk: torch.Tensor, kgc_key: "LC.KgcKey",
+                    cts: torch.Tensor, n: int, chunks: int, f: int, n_select: int, seed: int, first: int,
+                    groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM,
+                    average: bool = True, out: Optional[dict] = None) -> dict:
+    """One aggregation round with the KGC step on the device (Algorithm 1 with Algorithm 2 in
+    between): encrypted distances, read-out of the distances with the resident KGC key, Krum /
+    Multi-Krum selection, mask ciphertexts encrypted with device randomness (ciphertext indices
+    first .. first+n-1 of `seed`), masked aggregate.  Nothing synchronises the host, so the whole
+    round can be captured in one CUDA graph (pass preallocated buffers in `out`)."""
+    out = dict(out or {})
+    L = ctx.L
+    if "dist" not in out:
+        out["dist"] = ctx.empty(n * (n - 1) // 2, 2, L, ctx.N)
+    if "agg" not in out:
+        out["agg"] = ctx.empty(chunks, 2, L, ctx.N)
+    if "masks" not in out:
+        out["masks"] = ctx.empty(n, 2, ctx.nq, ctx.N)
+    if "values" not in out:
+        out["values"] = torch.empty(n * (n - 1) // 2, dtype=torch.float64, device=cts.device)
+    if "weights" not in out:
+        out["weights"] = torch.empty(n, dtype=torch.float64, device=cts.device)
+    if "selected" not in out:
+        out["selected"] = torch.empty(n_select, dtype=torch.int32, device=cts.device)
+    _, sc = ctx.distances(evk, cts, n, chunks, ctx.scale, mode=LC.LC_MODE_BATCHED | flags, groups=groups,
+                          out=out["dist"])
+    kgc_key.readout(out["dist"], L - 1, sc, out=out["values"])
+    kgc_key.krum(out["values"], n, f, n_select, average, w=out["weights"], sel=out["selected"])
+    ctx.encrypt_const_seeded(pk, out["weights"], ctx.scale, seed, first, out=out["masks"])
+    ctx.masked_aggregate(evk, cts, n, chunks, ctx.scale, out["masks"], ctx.scale, out=out["agg"])
+    return out
