@@ -425,12 +425,14 @@ def run_serving(args):
 
         # warm-up: a few rounds of every size class, untimed
         warm = rounds_of(S.serving_rounds(seed=4, n_rounds=args.warmup, rate=1e9, tenants=args.tenants))
-        SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags).run(
-            warm, realtime=False)
+        dkgc = None if args.host_kgc else 3
+        SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags,
+                  device_kgc_seed=dkgc).run(warm, realtime=False)
         torch.cuda.synchronize()
         for rate in [float(x) for x in args.rates.split(",")]:
             rounds = rounds_of(S.serving_rounds(seed=3, n_rounds=args.rounds, rate=rate, tenants=args.tenants))
-            srv = SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags)
+            srv = SV.Server(g, tenants, args.budget_gb * 1e9, ingest, mask_rand, groups=sched, flags=flags,
+                            device_kgc_seed=dkgc)
             clocks = Clocks(local)
             clocks.start()
             l0 = LC.launches()
@@ -448,7 +450,8 @@ def run_serving(args):
                     "clocks": ck, "dtype": "u64", "data": "synthetic",
                     "config": {"workload": "serving_N32768_4tenants_n{5,10,20,40}_d{2^16..2^22}_poisson",
                                "tenants": args.tenants, "budget_gb": args.budget_gb,
-                               "rotation_schedule": sname, "seed": 3}}
+                               "rotation_schedule": sname, "seed": 3,
+                               "kgc": "host" if args.host_kgc else "device"}}
             print(json.dumps(line), flush=True)
 
 
@@ -475,6 +478,8 @@ def main():
     ap.add_argument("--rounds", type=int, default=100, help="serving rounds per rate")
     ap.add_argument("--tenants", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
+    ap.add_argument("--host-kgc", action="store_true",
+                    help="serving: KGC step on the host (default: on the device, no host round trip)")
     ap.add_argument("--sweep", action="store_true", help="packing-size sweep; one line per N")
     ap.add_argument("--sweep-log-n", default="13,14,15,16")
     args = ap.parse_args()

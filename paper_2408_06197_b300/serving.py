@@ -75,11 +75,16 @@ class Server:
                  ingest: Callable[[Round], torch.Tensor],
                  mask_rand: Callable[[Round, int], tuple],
                  groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM,
-                 keep_outputs: bool = False):
+                 keep_outputs: bool = False, device_kgc_seed: Optional[int] = None):
         """keep_outputs: keep each finished round's device buffers (distances, masks, aggregate) on
-        its Job; otherwise they are released as soon as the round no longer needs them."""
+        its Job; otherwise they are released as soon as the round no longer needs them.
+        device_kgc_seed: run the KGC step on the device (resident KGC keys, device read-out and
+        Krum, masks encrypted with device randomness of this seed, ciphertext indices
+        rid * 2^20 + client) instead of on the host with `mask_rand`."""
         self.ctx, self.tenants, self.budget = ctx, list(tenants), float(budget_bytes)
         self.keep = keep_outputs
+        self.device_kgc_seed = device_kgc_seed
+        self._kgc_keys: Dict[int, "LC.KgcKey"] = {}
         self.ingest, self.mask_rand = ingest, mask_rand
         self.groups = list(groups) if groups else [2] * ((ctx.log_n - 1) // 2) + [1] * ((ctx.log_n - 1) % 2)
         self.flags = flags
@@ -117,9 +122,29 @@ class Server:
             r.state, r.t_admit = DIST, self.now()
             self.active.append(r)
 
+    def _kgc_device(self, r: Round):
+        """The KGC step without a host round trip: read-out and selection on the device, masks
+        encrypted with device randomness; the selection is read back after the aggregate."""
+        t = time.perf_counter()
+        c, ten = self.ctx, self.tenants[r.tenant]
+        if r.tenant not in self._kgc_keys:
+            self._kgc_keys[r.tenant] = LC.KgcKey(c, ten.s)
+        key = self._kgc_keys[r.tenant]
+        sc = c.scale * c.scale / c.q[c.L]
+        vals = key.readout(r.job.out_dist, c.L - 1, sc)
+        w, sel = key.krum(vals, r.n, r.f, r.n_select, r.average)
+        r.job.masks = c.encrypt_const_seeded(ten.pk, w, c.scale, self.device_kgc_seed, r.rid << 20)
+        r._device_kgc = (vals, sel)
+        if not self.keep:
+            r.job.out_dist = None
+        r.kgc_seconds = time.perf_counter() - t
+        r.state, r.t_kgc = AGG, self.now()
+
     def _kgc(self, r: Round):
         """Decrypt the pair distances, select the clients, encrypt the mask (one ciphertext per
         client holding its weight in every slot)."""
+        if self.device_kgc_seed is not None:
+            return self._kgc_device(r)
         t = time.perf_counter()
         c, ten = self.ctx, self.tenants[r.tenant]
         sc = c.scale * c.scale / c.q[c.L]
@@ -156,6 +181,15 @@ class Server:
             now = self.now()
             for r in agg:
                 r.state, r.t_done = DONE, now
+                if getattr(r, "_device_kgc", None) is not None:  # selection record from the device
+                    vals, sel = r._device_kgc
+                    r.selected = [int(x) for x in sel.cpu().tolist()]
+                    v = vals.cpu().numpy()
+                    d = np.zeros((r.n, r.n))
+                    iu = np.triu_indices(r.n, 1)
+                    d[iu] = v
+                    r.distances = d + d.T
+                    r._device_kgc = None
                 self.active.remove(r)
                 self.done.append(r)
                 self.used -= self.footprint(r)

@@ -99,10 +99,11 @@ class _Feed:
                                          average=True))
         return out
 
-    def server(self, budget):
+    def server(self, budget, device_kgc_seed=None):
         return self.SV.Server(self.env.g, self.tenants, budget, ingest=lambda r: self.cts[r.rid].clone(),
                               mask_rand=lambda r, i: S.enc_rand(3, S.CFG_SERVING, i, S.MASK_CHUNK, self.env.N,
-                                                                job=r.rid), groups=SCHED, keep_outputs=True)
+                                                                job=r.rid), groups=SCHED, keep_outputs=True,
+                              device_kgc_seed=device_kgc_seed)
 
 
 @pytest.fixture(scope="module")
@@ -157,3 +158,23 @@ def test_serving_results_match_fp64(feed, toy):
             want = np.tensordot(wts, X[:, k], axes=1)
             # toy parameters (scale 2^30): about 7e-6 rms per slot, so 1e-4 is about 14 sigma
             assert np.abs(got - want).max() < 1e-4
+
+
+def test_serving_with_device_kgc(feed, toy):
+    """KGC step on the device: same selections as the host KGC, every round identical alone and
+    in the mix, aggregates decrypt to the weighted sums."""
+    from paper_2408_06197_b300 import kgc
+    host = _by_rid(feed.server(1e12).run(feed.rounds(), realtime=False))
+    dev = _by_rid(feed.server(1e12, device_kgc_seed=77).run(feed.rounds(), realtime=False))
+    sc = toy.prm.scale * toy.prm.scale / toy.prm.q[toy.L]
+    for rid, ten, n, chunks in feed.specs:
+        assert dev[rid].selected == host[rid].selected
+        assert np.array_equal(dev[rid].distances, host[rid].distances)
+        alone = _by_rid(feed.server(1e12, device_kgc_seed=77).run(feed.rounds([rid]), realtime=False))[rid]
+        assert torch.equal(alone.job.masks, dev[rid].job.masks)
+        assert torch.equal(alone.job.out_agg, dev[rid].job.out_agg)
+        wts = kgc.mask_weights(n, dev[rid].selected, average=True)
+        X = S.split_chunks(feed.W[rid], toy.prm.slots)
+        for k in range(chunks):
+            got = toy.g.decrypt(feed.tenants[ten].s, dev[rid].job.out_agg[k].contiguous(), toy.L - 1, sc)
+            assert np.abs(got - np.tensordot(wts, X[:, k], axes=1)).max() < 1e-4
