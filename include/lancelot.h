@@ -212,6 +212,16 @@ int lc_encrypt(lc_ctx* ctx, const uint64_t* pk, const int64_t* m, const int8_t* 
  * round(w_dev[b] * scale), the others 0): the KGC's mask ciphertexts (Section "Masked-based
  * Encrypted Sorting").  Neither call synchronises the host, so both can be graph-captured. */
 int lc_sample_enc(lc_ctx* ctx, uint64_t seed, uint64_t first, uint32_t count, int8_t* r, int32_t* e0, int32_t* e1);
+/* Client-side batched encode on the GPU (FP64; N = 2^15 only, other N give LC_EINVAL): z_dev =
+ * [count][N/2] real slot values (device doubles), m_dev = [count][N] integer plaintexts
+ * (device int64), m = round(2/N Re FFT_2N(A)) with A[5^j mod 2N] = scale z_j -- the map of
+ * lc_encode computed with a different FFT, so an integer may differ by one where the FP64 value
+ * is within rounding error of a half-integer.  lc_encode_encrypt_seeded encodes and encrypts
+ * with device randomness (ciphertext indices first ..) in one call: the clients' step of
+ * Algorithm 1 for many clients and chunks without host arrays. */
+int lc_encode_dev(lc_ctx* ctx, const double* z_dev, uint32_t count, double scale, int64_t* m_dev);
+int lc_encode_encrypt_seeded(lc_ctx* ctx, const uint64_t* pk, const double* z_dev, uint32_t count, double scale,
+                             uint64_t seed, uint64_t first, uint64_t* out);
 int lc_encrypt_seeded(lc_ctx* ctx, const uint64_t* pk, const int64_t* m_dev, uint32_t count, uint64_t seed,
                       uint64_t first, uint64_t* out);
 int lc_encrypt_const_seeded(lc_ctx* ctx, const uint64_t* pk, const double* w_dev, uint32_t count, double scale,

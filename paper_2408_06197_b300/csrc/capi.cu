@@ -644,6 +644,10 @@ void lc_ctx_destroy(lc_ctx* c) {
     lc_dev_free(c, c->rescale);
     lc_dev_free(c, c->scratch);
     lc_dev_free(c, c->stage);
+    lc_dev_free(c, c->enc_pos);
+    lc_dev_free(c, c->enc_w256);
+    lc_dev_free(c, c->enc_wbig);
+    lc_dev_free(c, c->enc_buf);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (int d = 0; d < 2; d++)
         if (c->copy_stream[d]) {
@@ -882,6 +886,57 @@ int lc_encrypt(lc_ctx* c, const uint64_t* pk, const int64_t* m, const int8_t* r,
     return check_launch(c, "lc_encrypt");
 }
 
+// encoder tables (first use) and a work buffer of at least `bytes`
+static int encoder_ready(lc_ctx* c, size_t bytes) {
+    const size_t N = c->N, M = 2 * N;
+    if (!c->enc_pos) {
+        std::vector<unsigned> pos(N / 2);
+        u64 e = 1;
+        for (size_t j = 0; j < N / 2; j++) {
+            pos[j] = (unsigned)e;
+            e = (e * 5) % M;
+        }
+        std::vector<double2> w256(256), wbig(M);
+        for (int k = 0; k < 256; k++) w256[k] = make_double2(std::cos(2 * M_PI * k / 256), -std::sin(2 * M_PI * k / 256));
+        for (size_t t = 0; t < M; t++)
+            wbig[t] = make_double2(std::cos(2 * M_PI * (double)t / M), -std::sin(2 * M_PI * (double)t / M));
+        c->enc_pos = static_cast<unsigned*>(lc_dev_alloc(c, pos.size() * 4));
+        c->enc_w256 = static_cast<double2*>(lc_dev_alloc(c, 256 * sizeof(double2)));
+        c->enc_wbig = static_cast<double2*>(lc_dev_alloc(c, M * sizeof(double2)));
+        if (!c->enc_pos || !c->enc_w256 || !c->enc_wbig) return fail(c, LC_ENOMEM, "encoder tables");
+        LC_CUDA(c, cudaMemcpy(c->enc_pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice));
+        LC_CUDA(c, cudaMemcpy(c->enc_w256, w256.data(), 256 * sizeof(double2), cudaMemcpyHostToDevice));
+        LC_CUDA(c, cudaMemcpy(c->enc_wbig, wbig.data(), M * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    if (c->enc_buf_bytes < bytes) {
+        if (c->capturing) return fail(c, LC_ENOMEM, "encoder buffer must be sized before a graph capture");
+        LC_CUDA(c, cudaStreamSynchronize(c->stream));
+        lc_dev_free(c, c->enc_buf);
+        c->enc_buf = lc_dev_alloc(c, bytes);
+        c->enc_buf_bytes = c->enc_buf ? bytes : 0;
+        if (!c->enc_buf) return fail(c, LC_ENOMEM, "encoder buffer");
+    }
+    return LC_OK;
+}
+
+static const uint32_t kEncSlice = 64;
+
+int lc_encode_dev(lc_ctx* c, const double* z_dev, uint32_t count, double scale, int64_t* m_dev) {
+    clear_prior_error();
+    if (!c || (count && (!z_dev || !m_dev))) return fail(c, LC_EINVAL, "lc_encode_dev: null argument");
+    if (c->log_n != 15) return fail(c, LC_EINVAL, "lc_encode_dev: implemented for N = 2^15");
+    if (count == 0) return LC_OK;
+    const size_t N = c->N;
+    const uint32_t slice = std::min(count, kEncSlice);
+    if (int st = encoder_ready(c, (size_t)slice * 2 * N * sizeof(double2))) return st;
+    for (uint32_t b0 = 0; b0 < count; b0 += slice) {
+        const int B = (int)std::min(slice, count - b0);
+        op_encode(c, z_dev + (size_t)b0 * (N / 2), B, scale, c->enc_pos, c->enc_w256, c->enc_wbig,
+                  static_cast<double2*>(c->enc_buf), m_dev + (size_t)b0 * N);
+    }
+    return check_launch(c, "lc_encode_dev");
+}
+
 int lc_sample_enc(lc_ctx* c, uint64_t seed, uint64_t first, uint32_t count, int8_t* r, int32_t* e0, int32_t* e1) {
     clear_prior_error();
     if (!c || (count && (!r || !e0 || !e1))) return fail(c, LC_EINVAL, "lc_sample_enc: null argument");
@@ -959,6 +1014,27 @@ int lc_encrypt_const_seeded(lc_ctx* c, const uint64_t* pk, const double* w_dev, 
     if (!c || !pk || !out || (count && !w_dev)) return fail(c, LC_EINVAL, "lc_encrypt_const_seeded: null argument");
     if (count == 0) return LC_OK;
     return encrypt_seeded(c, pk, nullptr, w_dev, scale, count, seed, first, out);
+}
+
+int lc_encode_encrypt_seeded(lc_ctx* c, const uint64_t* pk, const double* z_dev, uint32_t count, double scale,
+                             uint64_t seed, uint64_t first, uint64_t* out) {
+    clear_prior_error();
+    if (!c || !pk || !out || (count && !z_dev)) return fail(c, LC_EINVAL, "lc_encode_encrypt_seeded: null argument");
+    if (c->log_n != 15) return fail(c, LC_EINVAL, "lc_encode_encrypt_seeded: implemented for N = 2^15");
+    if (count == 0) return LC_OK;
+    const size_t N = c->N, P = (size_t)c->nq * N;
+    const uint32_t slice = std::min(count, kEncSlice);
+    // work buffer: the FFT array, then the integer plaintexts of one slice
+    const size_t fft_bytes = (size_t)slice * 2 * N * sizeof(double2);
+    if (int st = encoder_ready(c, fft_bytes + (size_t)slice * N * 8)) return st;
+    int64_t* m = reinterpret_cast<int64_t*>(static_cast<char*>(c->enc_buf) + fft_bytes);
+    for (uint32_t b0 = 0; b0 < count; b0 += slice) {
+        const uint32_t B = std::min(slice, count - b0);
+        op_encode(c, z_dev + (size_t)b0 * (N / 2), (int)B, scale, c->enc_pos, c->enc_w256, c->enc_wbig,
+                  static_cast<double2*>(c->enc_buf), m);
+        if (int st = encrypt_seeded(c, pk, m, nullptr, 0.0, B, seed, first + b0, out + (size_t)b0 * 2 * P)) return st;
+    }
+    return check_launch(c, "lc_encode_encrypt_seeded");
 }
 
 int lc_decrypt(lc_ctx* c, const int8_t* s, const uint64_t* ct, uint32_t deg, uint32_t level, uint64_t* res_out) {

@@ -102,6 +102,12 @@ struct lc_ctx {
     std::string debug_err;
     bool capturing = false;  // inside lc_graph_begin / lc_graph_end
     uint64_t capture_launches0 = 0;
+    // FP64 encoder (created on first use): slot positions 5^j mod 2N, FFT twiddles, work buffer
+    unsigned* enc_pos = nullptr;
+    double2* enc_w256 = nullptr;
+    double2* enc_wbig = nullptr;
+    void* enc_buf = nullptr;
+    size_t enc_buf_bytes = 0;
     // overlapped host transfers: one copy stream per direction, one event per ticket
     cudaStream_t copy_stream[2] = {nullptr, nullptr};
     cudaEvent_t compute_mark = nullptr;

@@ -530,6 +530,88 @@ __global__ void k_krum(const double* __restrict__ d, int n, int f, int l, int av
     }
 }
 
+// ---------------------------------------------------------------------------- encoding (FP64)
+// Canonical-embedding encode of real slot vectors (Section "CKKS Scheme Description"):
+//   A[5^j mod 2N] = scale z_j (j < N/2, other entries 0), X = FFT_2N(A) with e^{-2 pi i/2N},
+//   m_k = round(2/N Re X_k) for k < N  (ties to even).
+// The 2N-point FFT is done as 256 x (2N/256) four-step: column FFTs of length 256 over the high
+// index bits with the twist e^{-2 pi i t2 k1 / 2N}, then row FFTs over the low bits.
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ unsigned brev8(unsigned v) { return __brev(v) >> 24; }
+
+// in-place radix-2 FFT of NF interleaved 256-point sequences s[f][256] (bit-reversed input,
+// natural output), 128 threads
+template <int NF>
+__device__ __forceinline__ void fft256_block(double2 (*s)[256], const double2* __restrict__ w256) {
+    for (int len = 2; len <= 256; len <<= 1) {
+        const int half = len >> 1, step = 256 / len;
+        for (int b = threadIdx.x; b < 128 * NF; b += 128) {
+            const int f = b >> 7, bb = b & 127;
+            const int grp = bb / half, pos = bb - grp * half;
+            const int i = grp * len + pos, j = i + half;
+            const double2 u = s[f][i], v = cmul(s[f][j], __ldg(w256 + pos * step));
+            s[f][i] = make_double2(u.x + v.x, u.y + v.y);
+            s[f][j] = make_double2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+    }
+}
+
+// A[b][2N] <- 0, then A[b][pos[j]] = (scale z[b][j], 0)
+__global__ void k_enc_scatter(const double* __restrict__ z, int count, int log_n, const unsigned* __restrict__ pos,
+                              double scale, double2* __restrict__ A) {
+    const size_t N = (size_t)1 << log_n, half = N / 2;
+    const size_t total = (size_t)count * half;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / half, j = i - b * half;
+        A[b * 2 * N + pos[j]] = make_double2(scale * z[i], 0.0);
+    }
+}
+
+// column pass: 8 columns t2 per block; x[t1][t2] with t1 < 256 -> Y[k1][t2] = FFT_t1 * w^{t2 k1}
+__global__ void __launch_bounds__(128) k_fft_cols(double2* __restrict__ A, int log_2n, const double2* __restrict__ w256,
+                                                  const double2* __restrict__ wbig) {
+    __shared__ double2 s[8][256];
+    const size_t M = (size_t)1 << log_2n, cols = M >> 8;
+    double2* a = A + (size_t)blockIdx.y * M;
+    const int c0 = blockIdx.x * 8;
+    for (int e = threadIdx.x; e < 2048; e += 128) {
+        const int t1 = e >> 3, c = e & 7;
+        s[c][brev8(t1)] = a[(size_t)t1 * cols + c0 + c];
+    }
+    __syncthreads();
+    fft256_block<8>(s, w256);
+    for (int e = threadIdx.x; e < 2048; e += 128) {
+        const int k1 = e >> 3, c = e & 7;
+        a[(size_t)k1 * cols + c0 + c] = cmul(s[c][k1], __ldg(wbig + (size_t)(c0 + c) * k1));
+    }
+}
+
+// row pass for 2N = 256 * 256 (log_n = 15): 8 rows k1 per block, FFT over t2, output
+// m[k1 + 256 k2] = round(2/N Re X) for k2 < N / 256
+__global__ void __launch_bounds__(128) k_fft_rows_out(const double2* __restrict__ A, int log_n,
+                                                      const double2* __restrict__ w256, int64_t* __restrict__ m) {
+    __shared__ double2 s[8][256];
+    const size_t N = (size_t)1 << log_n, M = 2 * N, cols = M >> 8;  // cols = 256 here
+    const double2* a = A + (size_t)blockIdx.y * M;
+    int64_t* mb = m + (size_t)blockIdx.y * N;
+    const int r0 = blockIdx.x * 8;
+    for (int e = threadIdx.x; e < 2048; e += 128) {
+        const int r = e >> 8, t2 = e & 255;
+        s[r][brev8(t2)] = a[(size_t)(r0 + r) * cols + t2];
+    }
+    __syncthreads();
+    fft256_block<8>(s, w256);
+    const double f = 2.0 / (double)N;
+    const int k2max = (int)(N >> 8);
+    for (int e = threadIdx.x; e < 8 * k2max; e += 128) {
+        const int k2 = e >> 3, r = e & 7;
+        mb[(size_t)(r0 + r) + 256 * (size_t)k2] = __double2ll_rn(f * s[r][k2].x);
+    }
+}
+
 // ---------------------------------------------------------------------------- multi-job items
 // tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
 template <bool SPLIT>
@@ -1546,6 +1628,20 @@ void op_readout_finish(lc_ctx* c, const u64* res, int count, double scale, doubl
 void op_krum(lc_ctx* c, const double* d, int n, int f, int l, int average, double* w, int* sel) {
     k_krum<<<1, 256, 0, c->stream>>>(d, n, f, l, average, w, sel);
     g_lc_launches += 1;
+}
+
+// encode `count` slot vectors z [count][N/2] (device doubles) into m [count][N] (device int64);
+// A = scratch of count * 2N double2; tables: pos [N/2], w256 [256], wbig [2N]
+void op_encode(lc_ctx* c, const double* z, int count, double scale, const unsigned* pos, const double2* w256,
+               const double2* wbig, double2* A, int64_t* m) {
+    if (count <= 0) return;
+    const size_t N = c->N;
+    cudaMemsetAsync(A, 0, (size_t)count * 2 * N * sizeof(double2), c->stream);
+    k_enc_scatter<<<grid_for((size_t)count * N / 2), kT, 0, c->stream>>>(z, count, c->log_n, pos, scale, A);
+    const int log_2n = c->log_n + 1;
+    k_fft_cols<<<dim3((unsigned)((2 * N >> 8) / 8), count), 128, 0, c->stream>>>(A, log_2n, w256, wbig);
+    k_fft_rows_out<<<dim3(256 / 8, count), 128, 0, c->stream>>>(A, c->log_n, w256, m);
+    g_lc_launches += 3;
 }
 
 void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1) {

@@ -89,6 +89,9 @@ void op_copy_items(lc_ctx* c, const u64* src, size_t words, u64* const* dst_dev,
 // KGC step: read-out values (centred residue mod q0 / scale) and Krum / Multi-Krum selection
 void op_readout_finish(lc_ctx* c, const u64* res, int count, double scale, double* out);
 void op_krum(lc_ctx* c, const double* d, int n, int f, int l, int average, double* w, int* sel);
+// FP64 encode of count slot vectors (log_n = 15 only: 2N = 256 x 256), see ops.cu
+void op_encode(lc_ctx* c, const double* z, int count, double scale, const unsigned* pos, const double2* w256,
+               const double2* wbig, double2* A, int64_t* m);
 // device randomness (Philox4x64-10): r, e0, e1 [count][N] of ciphertexts first .. first+count-1
 void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1);
 // constant-slot plaintexts m[b] = (round(w[b] scale), 0, ..., 0), [count][N]

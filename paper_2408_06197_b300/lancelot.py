@@ -141,6 +141,8 @@ def lib() -> ctypes.CDLL:
             "lc_batch_aggregate": [vp, vp, u32],
             "lc_decrypt_const": [vp, vp, vp, u32, u32, ctypes.c_double, vp],
             "lc_sample_enc": [vp, ctypes.c_uint64, ctypes.c_uint64, u32, vp, vp, vp],
+            "lc_encode_dev": [vp, vp, u32, ctypes.c_double, vp],
+            "lc_encode_encrypt_seeded": [vp, vp, vp, u32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, vp],
             "lc_encrypt_seeded": [vp, vp, vp, u32, ctypes.c_uint64, ctypes.c_uint64, vp],
             "lc_encrypt_const_seeded": [vp, vp, vp, u32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, vp],
             "lc_kgc_create": [vp, vp, vp],
@@ -500,6 +502,34 @@ class Context:
         _need(out, count * 2 * self.nq * self.N, "encrypt_seeded: out")
         self._check(lib().lc_encrypt_seeded(self.h, _t_ptr(pk), _t_ptr(m), count, int(seed), int(first),
                                             _t_ptr(out)), "lc_encrypt_seeded")
+        return out
+
+    def _slots_arg(self, z: torch.Tensor, what: str) -> int:
+        if z.dtype != torch.float64 or not z.is_cuda or not z.is_contiguous() or z.numel() % self.slots:
+            raise LancelotError(f"{what}: z must be a contiguous float64 CUDA tensor of whole slot vectors")
+        return z.numel() // self.slots
+
+    def encode_dev(self, z: torch.Tensor, scale: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """GPU encode of real slot vectors z ([count][N/2] float64 CUDA tensor) -> int64 [count][N]."""
+        count = self._slots_arg(z, "encode_dev")
+        if out is None:
+            out = torch.empty(count, self.N, dtype=torch.int64, device=z.device)
+        _need(out, count * self.N, "encode_dev: out")
+        self._check(lib().lc_encode_dev(self.h, ctypes.c_void_p(z.data_ptr()), count, float(scale), _t_ptr(out)),
+                    "lc_encode_dev")
+        return out
+
+    def encode_encrypt_seeded(self, pk: torch.Tensor, z: torch.Tensor, scale: float, seed: int, first: int,
+                              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Encode on the GPU and encrypt with device randomness (the clients' batched step)."""
+        count = self._slots_arg(z, "encode_encrypt_seeded")
+        _need(pk, 2 * self.nq * self.N, "encode_encrypt_seeded: pk")
+        if out is None:
+            out = self.empty(count, 2, self.nq, self.N)
+        _need(out, count * 2 * self.nq * self.N, "encode_encrypt_seeded: out")
+        self._check(lib().lc_encode_encrypt_seeded(self.h, _t_ptr(pk), ctypes.c_void_p(z.data_ptr()), count,
+                                                   float(scale), int(seed), int(first), _t_ptr(out)),
+                    "lc_encode_encrypt_seeded")
         return out
 
     def encrypt_const_seeded(self, pk: torch.Tensor, w: torch.Tensor, scale: float, seed: int, first: int,

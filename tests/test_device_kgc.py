@@ -138,3 +138,31 @@ def test_device_kgc_round_in_one_graph(toy):
         key.close()
         evk.close()
         g.close()
+
+
+@pytest.fixture(scope="module")
+def prod():
+    return Env("prod", 14, S.CFG_PLAIN)
+
+
+def test_gpu_encoder_matches_oracle_encoder(prod):
+    z = np.random.default_rng(41).normal(0, 0.01, (6, prod.prm.slots))
+    z[0] = 0.0
+    z[1, :] = np.linspace(-1, 1, prod.prm.slots)
+    mg = prod.g.encode_dev(torch.tensor(z, device="cuda"), prod.prm.scale).cpu().numpy()
+    mo = plaintexts(prod.o, prod.prm, z)
+    diff = np.abs(mg - mo)
+    assert diff.max() <= 1 and np.count_nonzero(diff) <= 12  # FP64 near-ties only
+    assert not mg[0].any()
+
+
+def test_gpu_encode_encrypt_decrypts_and_composes(prod):
+    z = np.random.default_rng(42).normal(0, 0.01, (3, prod.prm.slots))
+    zt = torch.tensor(z, device="cuda")
+    ct = prod.g.encode_encrypt_seeded(prod.gpk, zt, prod.prm.scale, 8, 100)
+    m = prod.g.encode_dev(zt, prod.prm.scale)
+    ref = prod.g.encrypt_seeded(prod.gpk, m, 8, 100)
+    assert torch.equal(ct, ref)
+    for b in range(3):
+        got = prod.g.decrypt(prod.keys.s, ct[b].contiguous(), prod.L, prod.prm.scale)
+        assert np.abs(got - z[b]).max() < 1e-6
