@@ -138,7 +138,7 @@ def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):
     mm = np.stack([g.encode(np.full(g.slots, wts[i]), g.scale) for i in range(w.n_clients)])
     r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(w.n_clients), [S.MASK_CHUNK], N)
     masks = g.encrypt(pk, mm, r, e0, e1)
-    return evk, cts, masks, sched, s
+    return evk, cts, masks, sched, s, pk
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
@@ -471,6 +471,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-operation reference measurement")
+    ap.add_argument("--no-client", action="store_true", help="skip the client-side encode+encrypt measurement")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels eagerly instead of replaying a CUDA graph")
     ap.add_argument("--micro", action="store_true", help="small isolated kernel case for profiler captures")
     ap.add_argument("--serving", action="store_true", help="Poisson-arrival serving loop; one line per rate")
@@ -513,7 +514,7 @@ def main():
     w = S.PLAIN
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=local, stream=stream)
-        evk, cts, masks, sched, s = build_workload(LC, g, w, args.schedule)
+        evk, cts, masks, sched, s, evk_pk = build_workload(LC, g, w, args.schedule)
         mode = LC.LC_MODE_BATCHED if args.mode == "batched" else LC.LC_MODE_PER_OP
         out_d = g.empty(w.n_pairs, 2, g.L, g.N)
         out_a = g.empty(w.chunks, 2, g.L, g.N)
@@ -658,6 +659,28 @@ def main():
                    "serial": e2e_serial}
             del bufs
 
+    # the clients' step on the device: GPU encode + encryption with device randomness of all
+    # n x chunks update chunks (beside the server metric; not part of a step)
+    client = None
+    if not args.no_client:
+        with torch.cuda.stream(stream):
+            X = S.split_chunks(S.client_updates(w), g.slots)
+            zt = torch.tensor(X.reshape(-1, g.slots), device=f"cuda:{local}")
+            dst = torch.empty_like(cts)
+            g.encode_encrypt_seeded(evk_pk, zt, g.scale, 1, 0, out=dst)  # warm
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                g.encode_encrypt_seeded(evk_pk, zt, g.scale, 1, 0, out=dst)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cms = e0.elapsed_time(e1) / 3
+            client = {"ciphertexts": int(zt.shape[0]), "ms": cms, "ciphertexts_per_s": zt.shape[0] / (cms / 1e3),
+                      "form": "GPU FP64 encode + encryption with device randomness (Philox4x64-10)"}
+            del zt, dst
+
     # the plain per-operation form on the same inputs (reference point of the batched form)
     plain = None
     if args.mode == "batched" and not args.no_plain:
@@ -710,6 +733,7 @@ def main():
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},
             "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e, "plain_form": plain,
+            "client_step": client,
             "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                  "definition": "one round = 45 pair distances + masked aggregate of 64 chunks, "
                                                "device time per step (rank 0)"}}
