@@ -479,7 +479,7 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
             std::vector<const u64*> kp(cnt);
             std::vector<uint64_t> gs(cnt);
             for (int t = 0; t < cnt; t++) {
-                kp[t] = keys[t]->data;
+                kp[t] = keys[t]->qp;  // group-kernel layout
                 gs[t] = keys[t]->galois;
             }
             PROF(c, PROF_INNER, inner_gather_bytes(c, B, level, cnt), (uint64_t)B,
@@ -720,7 +720,10 @@ int lc_evk_create(lc_ctx* c, lc_evk** out) {
 void lc_evk_free(lc_evk* k) {
     if (!k) return;
     cudaStreamSynchronize(k->ctx->stream);
-    for (auto& kv : k->keys) lc_dev_free(k->ctx, kv.second.data);
+    for (auto& kv : k->keys) {
+        lc_dev_free(k->ctx, kv.second.data);
+        lc_dev_free(k->ctx, kv.second.qp);
+    }
     delete k;
 }
 
@@ -777,18 +780,27 @@ int lc_evk_add(lc_ctx* c, lc_evk* evk, const int8_t* s, int32_t rotation, const 
         ntt_fwd_p(c, er, 0, 1, m);
         op_key_combine(c, ka, sr, er, st, Pmod.data(), mods.data(), rows, kb);
     }
+    u64* qpkey = nullptr;
     if (id >= 0) {
         // store phi_g^-1(key): a hoisted rotation then permutes only its two output polys
         const uint64_t ginv = hpow(g, (u64)c->N / 2 - 1, 2 * (u64)c->N);  // g^(N/2-1) = g^-1 mod 2N
         op_permute_rows(c, tmpkey, key, c->dnum * 2 * rows, ginv);
+        // and the un-permuted key, packed, for the one-ModDown group kernel
+        qpkey = static_cast<u64*>(lc_dev_alloc(c, keywords * 8));
+        if (!qpkey) {
+            lc_dev_free(c, key);
+            return fail(c, LC_ENOMEM, "key allocation");
+        }
+        op_pack_key(c, tmpkey, qpkey, keywords);
     }
     LC_CUDA(c, cudaStreamSynchronize(c->stream));
     int st_ = check_launch(c, "lc_evk_add");
     if (st_ != LC_OK) {
         lc_dev_free(c, key);
+        lc_dev_free(c, qpkey);
         return st_;
     }
-    evk->keys[id] = SwKey{key, g};
+    evk->keys[id] = SwKey{key, g, qpkey};
     return LC_OK;
 }
 
@@ -1671,7 +1683,8 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
                 gt[gi] = cnt;
                 for (int tt = 1; tt <= cnt; tt++) {
                     const SwKey* key = find_key(J.evk, (int32_t)(tt * stride));
-                    gk[gi].push_back(key->data);
+                    // the one-ModDown group kernel reads the group-kernel layout
+                    gk[gi].push_back(qp && cnt > 1 ? key->qp : key->data);
                     if (k == 0) gal[gi].push_back(key->galois);
                 }
                 stride <<= sched[gi];

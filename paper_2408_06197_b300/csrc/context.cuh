@@ -63,6 +63,9 @@ struct ProfRec {
 struct SwKey {
     u64* data;          // device [dnum][2][n_q+n_p][N], evaluation domain (rotations pre-permuted)
     uint64_t galois;    // 0 for relinearisation
+    // rotation keys only: the layout of the one-ModDown group kernel -- not permuted, and rows
+    // whose prime is below 2^40 stored as packed 20-bit halves ((v >> 20) << 32 | v mod 2^20)
+    u64* qp = nullptr;
 };
 
 struct lc_evk {

@@ -612,6 +612,16 @@ __global__ void __launch_bounds__(128) k_fft_rows_out(const double2* __restrict_
     }
 }
 
+// group-kernel key layout: rows (of all n_q + n_p) with primes below 2^40 as packed halves
+__global__ void k_pack_key(const u64* __restrict__ in, u64* __restrict__ out, int rows, int log_n,
+                           const ModConst* __restrict__ mc, size_t total) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)((i >> log_n) % rows);
+        const u64 v = in[i];
+        out[i] = mc[m].q < (1ull << 40) ? (((v >> 20) << 32) | (v & 0xFFFFFu)) : v;
+    }
+}
+
 // ---------------------------------------------------------------------------- multi-job items
 // tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
 template <bool SPLIT>
@@ -933,10 +943,11 @@ __global__ void k_gather_sum(const u64* __restrict__ src, size_t src_stride, u64
 }
 
 // One hoisted group with a single ModDown, fused: for the T rotations g_t of the group,
-//   usum[b][p][r][x]  = sum_t sum_j E_j[b][r][s_t] * key_t[j][p][r][s_t],   s_t = perm_{g_t}(x)
+//   usum[b][p][r][x]  = sum_t sum_j E_j[b][r][s_t] * k'_t[j][p][r][s_t],   s_t = perm_{g_t}(x)
 //   c0acc[b][r][x]    = y0[b][r][x] + sum_t y0[b][r][s_t]                    (rows r < nl)
-// i.e. sum_t phi_{g_t}(<E, key_t>) with the keys stored pre-permuted by phi_{g_t}^-1, without
-// writing the per-rotation products.  E_j is the j-th extended digit (own rows from d).  All
+// i.e. sum_t phi_{g_t}(<E, k'_t>) with k'_t the keys pre-permuted by phi_{g_t}^-1, without
+// writing the per-rotation products.  k'_t[s_t(x)] is the un-permuted key at x, so the keys are
+// read in their group-kernel layout (SwKey::qp: un-permuted, 40-bit rows as packed halves).  E_j is the j-th extended digit (own rows from d).  All
 // products of one output sum in 128 bits (T * beta < 64 terms below q^2 < 2^120) and reduce
 // once, so the result equals the per-rotation reduction exactly.
 // perm_g maps the aligned pair {2m, 2m+1} onto an aligned pair {s, s^1} (the pair bit is the top
@@ -998,18 +1009,19 @@ __global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gath
         const size_t ko = ((size_t)j * 2 * nqp + kt) * N;
 #pragma unroll
         for (int t = 0; t < T; t++) {
+            // keys in the group-kernel layout: read at x (no permutation), 40-bit rows packed
             ulonglong2 k0, k1;
             if (!ITEMS) {
-                k0 = ld2_swap(keys.p[t] + ko, s0[t], sw[t]);
-                k1 = ld2_swap(keys.p[t] + ko + ka, s0[t], sw[t]);
+                k0 = ld2(keys.p[t] + ko + x);
+                k1 = ld2(keys.p[t] + ko + ka + x);
             }
 #pragma unroll
             for (int i = 0; i < kBT; i++) {
                 const int b = bi[i];
                 if (ITEMS) {
                     const u64* kp = keys_dev[(size_t)b * T + t];
-                    k0 = ld2_swap(kp + ko, s0[t], sw[t]);
-                    k1 = ld2_swap(kp + ko + ka, s0[t], sw[t]);
+                    k0 = ld2(kp + ko + x);
+                    k1 = ld2(kp + ko + ka + x);
                 }
                 const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
                                    : ext + (((size_t)b * beta + j) * rows + r) * N;
@@ -1017,10 +1029,10 @@ __global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gath
                 if (SPLIT) {
                     const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
                     const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
-                    mac_split(h[i][0][0], exh, exl, (unsigned)(k0.x >> 20), (unsigned)k0.x & 0xFFFFFu);
-                    mac_split(h[i][0][1], eyh, eyl, (unsigned)(k0.y >> 20), (unsigned)k0.y & 0xFFFFFu);
-                    mac_split(h[i][1][0], exh, exl, (unsigned)(k1.x >> 20), (unsigned)k1.x & 0xFFFFFu);
-                    mac_split(h[i][1][1], eyh, eyl, (unsigned)(k1.y >> 20), (unsigned)k1.y & 0xFFFFFu);
+                    mac_split(h[i][0][0], exh, exl, (unsigned)(k0.x >> 32), (unsigned)k0.x);
+                    mac_split(h[i][0][1], eyh, eyl, (unsigned)(k0.y >> 32), (unsigned)k0.y);
+                    mac_split(h[i][1][0], exh, exl, (unsigned)(k1.x >> 32), (unsigned)k1.x);
+                    mac_split(h[i][1][1], eyh, eyl, (unsigned)(k1.y >> 32), (unsigned)k1.y);
                 } else {
                     mac128(a[i][0][0], ev.x, k0.x);
                     mac128(a[i][0][1], ev.y, k0.y);
@@ -1642,6 +1654,11 @@ void op_encode(lc_ctx* c, const double* z, int count, double scale, const unsign
     k_fft_cols<<<dim3((unsigned)((2 * N >> 8) / 8), count), 128, 0, c->stream>>>(A, log_2n, w256, wbig);
     k_fft_rows_out<<<dim3(256 / 8, count), 128, 0, c->stream>>>(A, c->log_n, w256, m);
     g_lc_launches += 3;
+}
+
+void op_pack_key(lc_ctx* c, const u64* in, u64* out, size_t words) {
+    k_pack_key<<<grid_for(words), kT, 0, c->stream>>>(in, out, c->nq + c->np, c->log_n, c->mc, words);
+    g_lc_launches += 1;
 }
 
 void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1) {

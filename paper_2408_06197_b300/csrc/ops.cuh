@@ -92,6 +92,8 @@ void op_krum(lc_ctx* c, const double* d, int n, int f, int l, int average, doubl
 // FP64 encode of count slot vectors (log_n = 15 only: 2N = 256 x 256), see ops.cu
 void op_encode(lc_ctx* c, const double* z, int count, double scale, const unsigned* pos, const double2* w256,
                const double2* wbig, double2* A, int64_t* m);
+// group-kernel key layout (SwKey::qp) of `words` key words
+void op_pack_key(lc_ctx* c, const u64* in, u64* out, size_t words);
 // device randomness (Philox4x64-10): r, e0, e1 [count][N] of ciphertexts first .. first+count-1
 void op_sample_enc(lc_ctx* c, u64 seed, u64 first, int count, int8_t* r, int32_t* e0, int32_t* e1);
 // constant-slot plaintexts m[b] = (round(w[b] scale), 0, ..., 0), [count][N]
