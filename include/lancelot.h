@@ -111,7 +111,9 @@ int lc_memcpy_d2h(lc_ctx* ctx, void* dst_host, const uint64_t* src_dev, size_t b
  * that earlier calls still read is not overwritten and a result is read only once computed;
  * *ticket names the copy.  lc_copy_wait makes the context's stream wait for that copy.  Host
  * memory must be pinned for the copy to overlap with computation.  Not allowed inside a graph
- * capture (LC_EBUSY).  Tickets stay valid until lc_ctx_destroy (one event each). */
+ * capture (LC_EBUSY).  A ticket is consumed by its lc_copy_wait (waiting twice is LC_EINVAL) and
+ * its event is reused by later copies; tickets never waited on hold one event each until
+ * lc_ctx_destroy. */
 #define LC_H2D 0
 #define LC_D2H 1
 int lc_copy_async(lc_ctx* ctx, void* dst, const void* src, size_t bytes, int dir, uint64_t* ticket);

@@ -1303,22 +1303,35 @@ int lc_copy_async(lc_ctx* c, void* dst, const void* src, size_t bytes, int dir, 
     if (c->capturing) return fail(c, LC_EBUSY, "lc_copy_async: not inside a graph capture");
     if (!c->copy_stream[dir]) LC_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream[dir], cudaStreamNonBlocking));
     if (!c->compute_mark) LC_CUDA(c, cudaEventCreateWithFlags(&c->compute_mark, cudaEventDisableTiming));
-    cudaEvent_t done;
-    LC_CUDA(c, cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-    c->copy_events.push_back(done);
+    size_t slot;
+    if (!c->copy_free.empty()) {
+        slot = c->copy_free.back();
+        c->copy_free.pop_back();
+    } else {
+        cudaEvent_t ev;
+        LC_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->copy_events.push_back(ev);
+        c->copy_busy.push_back(0);
+        slot = c->copy_events.size() - 1;
+    }
     // ordered after everything enqueued on the context's stream so far
     LC_CUDA(c, cudaEventRecord(c->compute_mark, c->stream));
     LC_CUDA(c, cudaStreamWaitEvent(c->copy_stream[dir], c->compute_mark, 0));
     LC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, dir == LC_H2D ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
                                c->copy_stream[dir]));
-    LC_CUDA(c, cudaEventRecord(done, c->copy_stream[dir]));
-    *ticket = c->copy_events.size() - 1;
+    LC_CUDA(c, cudaEventRecord(c->copy_events[slot], c->copy_stream[dir]));
+    c->copy_busy[slot] = 1;
+    *ticket = slot;
     return LC_OK;
 }
 
 int lc_copy_wait(lc_ctx* c, uint64_t ticket) {
-    if (!c || ticket >= c->copy_events.size()) return fail(c, LC_EINVAL, "lc_copy_wait: unknown ticket");
+    if (!c || ticket >= c->copy_events.size() || !c->copy_busy[ticket])
+        return fail(c, LC_EINVAL, "lc_copy_wait: unknown or already waited ticket");
     LC_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_events[ticket], 0));
+    // the wait binds to the record made by lc_copy_async, so the slot can be recorded again
+    c->copy_busy[ticket] = 0;
+    c->copy_free.push_back(ticket);
     return LC_OK;
 }
 

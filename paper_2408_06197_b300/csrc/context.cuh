@@ -114,7 +114,9 @@ struct lc_ctx {
     // overlapped host transfers: one copy stream per direction, one event per ticket
     cudaStream_t copy_stream[2] = {nullptr, nullptr};
     cudaEvent_t compute_mark = nullptr;
-    std::vector<cudaEvent_t> copy_events;
+    std::vector<cudaEvent_t> copy_events;  // one per ticket slot
+    std::vector<uint8_t> copy_busy;         // slot holds a copy not yet waited on
+    std::vector<size_t> copy_free;          // reusable slots
     // profiling
     bool prof_on = false;
     std::vector<ProfRec> prof;

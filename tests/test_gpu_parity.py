@@ -576,6 +576,15 @@ def test_overlapped_copies_match_stream_ordered_copies(toy):
     assert not LC.torch_to_u64(d).any()
     with pytest.raises(LC.LancelotError):
         g.copy_wait(10 ** 9)
+    with pytest.raises(LC.LancelotError):  # a ticket is consumed by its wait
+        g.copy_wait(t2)
+    # slots are reused: many copies do not grow the event pool past the copies in flight
+    tickets = set()
+    for _ in range(50):
+        tk = g.copy_async(hb, d)
+        g.copy_wait(tk)
+        tickets.add(tk)
+    assert len(tickets) <= 2
 
 
 @pytest.mark.parametrize("log_n", [13, pytest.param(16, marks=pytest.mark.slow)])
