@@ -43,6 +43,24 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (all_reduce MAX); the timing rule takes the slowest rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = f"cuda:{torch.cuda.current_device()}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas: every rank processes units_per_rank per step, the
+    job lasts as long as its slowest rank."""
+    return world * units_per_rank * steps / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -579,13 +597,9 @@ def main():
         prof = g.profile_stop()
         barrier()
         ck = clocks.stop()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world)
         ms_per_step = ms / args.steps
-        value = world * w.n_pairs * args.steps / (ms / 1e3)
+        value = whole_job_rate(w.n_pairs, world, args.steps, ms / 1e3)
 
         # end-to-end through the C ABI: every step copies its inputs in from pinned host memory and
         # its results out.  Serial form: copy in, compute, copy out.  Pipelined form (reported as
@@ -640,20 +654,15 @@ def main():
                 barrier()
                 t0 = time.perf_counter()
                 fn()
-                el = time.perf_counter() - t0
-                if world > 1:
-                    t = torch.tensor([el], device=f"cuda:{local}")
-                    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                    el = float(t.item())
-                return el
+                return max_over_ranks(time.perf_counter() - t0, world)
 
             serial_step()
             el = timed(lambda: [serial_step() for _ in range(args.steps)])
-            e2e_serial = {"value": world * w.n_pairs * args.steps / el, "unit": UNIT,
+            e2e_serial = {"value": whole_job_rate(w.n_pairs, world, args.steps, el), "unit": UNIT,
                           "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes}
             pipelined(2)
             el = timed(lambda: pipelined(args.steps))
-            e2e = {"value": world * w.n_pairs * args.steps / el, "unit": UNIT,
+            e2e = {"value": whole_job_rate(w.n_pairs, world, args.steps, el), "unit": UNIT,
                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                    "form": "double-buffered: next step's H2D and previous step's D2H overlap this step's compute",
                    "serial": e2e_serial}
