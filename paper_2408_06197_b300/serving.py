@@ -60,6 +60,7 @@ class Round:
     t_kgc: float = 0.0
     t_done: float = 0.0
     kgc_seconds: float = 0.0
+    device_kgc: Optional[tuple] = None  # (read-out values, kept indices) on the device, until read back
 
     @property
     def pairs(self) -> int:
@@ -134,7 +135,7 @@ class Server:
         vals = key.readout(r.job.out_dist, c.L - 1, sc)
         w, sel = key.krum(vals, r.n, r.f, r.n_select, r.average)
         r.job.masks = c.encrypt_const_seeded(ten.pk, w, c.scale, self.device_kgc_seed, r.rid << 20)
-        r._device_kgc = (vals, sel)
+        r.device_kgc = (vals, sel)
         if not self.keep:
             r.job.out_dist = None
         r.kgc_seconds = time.perf_counter() - t
@@ -181,15 +182,15 @@ class Server:
             now = self.now()
             for r in agg:
                 r.state, r.t_done = DONE, now
-                if getattr(r, "_device_kgc", None) is not None:  # selection record from the device
-                    vals, sel = r._device_kgc
+                if r.device_kgc is not None:  # selection record from the device
+                    vals, sel = r.device_kgc
                     r.selected = [int(x) for x in sel.cpu().tolist()]
                     v = vals.cpu().numpy()
                     d = np.zeros((r.n, r.n))
                     iu = np.triu_indices(r.n, 1)
                     d[iu] = v
                     r.distances = d + d.T
-                    r._device_kgc = None
+                    r.device_kgc = None
                 self.active.remove(r)
                 self.done.append(r)
                 self.used -= self.footprint(r)
