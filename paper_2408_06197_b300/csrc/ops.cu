@@ -1,6 +1,8 @@
 // Evaluation kernels of the Lancelot server path (elementwise RNS arithmetic, tensor and
 // lazy accumulation, base conversion, key inner product, rescale, automorphism).
 #include <cuda_runtime.h>
+#include <mutex>
+#include <set>
 #include <algorithm>
 #include "ops.cuh"
 
@@ -134,13 +136,22 @@ __global__ void __launch_bounds__(kT) k_sq_acc_pairs(const u64* __restrict__ cts
 // Batched distances tensor phase with client-block tiling.  Clients are grouped in blocks of
 // `cb` (all clients when n <= 11, else 8); a CTA owns one pair of client blocks (I <= J), one
 // 32-coefficient tile and one limb.  Chunk tiles of all its clients stream through a
-// kStages-deep shared-memory ring filled with cp.async (kStages-1 chunks in flight); each warp
-// owns a set of pairs and one lane per coefficient, and accumulates (a-b)^2 for every chunk.
+// shared-memory ring of kRing stages of kCPS chunks, filled with cp.async (kRing - 1 stages in
+// flight, one block barrier per stage); each warp owns a set of pairs and one lane per
+// coefficient, and accumulates (a-b)^2 for every chunk.
 // Each client tile is read from HBM about n/cb times instead of n-1 times.  Pairs outside
 // [p0, p0+np) are skipped (waves).
 constexpr int kTX = 32;
-constexpr int kStages = 4;
+#ifndef LC_TENSOR_RING
+#define LC_TENSOR_RING 3
+#endif
+#ifndef LC_TENSOR_CPS
+#define LC_TENSOR_CPS 4
+#endif
 constexpr int kMaxSlots = 16;                  // client slots staged per chunk (2 blocks of 8, or 11)
+constexpr int kRing = LC_TENSOR_RING;  // ring stages (kRing - 1 groups in flight)
+constexpr int kCPS = LC_TENSOR_CPS;    // chunks per stage (one barrier per stage)
+constexpr size_t kTensorSmem = (size_t)kRing * kCPS * kMaxSlots * 2 * kTX * 8;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -204,7 +215,10 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
     constexpr int NT = WARPS * 32;
     constexpr int UPT = (kMaxSlots * 2 * (kTX / 2) + NT - 1) / NT;  // 16-byte copy units per thread
     static_assert(WARPS * PPT >= 64, "pair slots must cover a block pair (8 x 8, or 55 pairs of 11 clients)");
-    __shared__ __align__(16) u64 sh[kStages][kMaxSlots][2][kTX];
+    // ring of kRing stages of kCPS chunks each, in dynamic shared memory
+    extern __shared__ __align__(16) u64 dyn_sh[];
+    auto sh = reinterpret_cast<u64(*)[kMaxSlots][2][kTX]>(dyn_sh);
+    constexpr int RS = kRing, CPS = kCPS;
     const int nb = (n + cb - 1) / cb;
     int bp = blockIdx.x, I = 0;
     while (bp >= nb - I) {
@@ -274,11 +288,15 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
         gsrc[h] = cts + ((size_t)(ucopy[h] ? c : 0) * chunks * 2 + upp[h]) * P + (size_t)limb * N + x0 + uxx[h];
     }
     const size_t chunk_stride = 2 * P;
+    const int groups = (chunks + CPS - 1) / CPS;
 #pragma unroll
-    for (int st = 0; st < kStages - 1; st++) {
+    for (int st = 0; st < RS - 1; st++) {
 #pragma unroll
-        for (int h = 0; h < UPT; h++)
-            if (ucopy[h] && st < chunks) cp_async16(&sh[st][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)st * chunk_stride);
+        for (int c = 0; c < CPS; c++)
+#pragma unroll
+            for (int h = 0; h < UPT; h++)
+                if (ucopy[h] && st * CPS + c < chunks)
+                    cp_async16(&sh[st * CPS + c][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)(st * CPS + c) * chunk_stride);
         cp_async_commit();
     }
     Acc3 t00[SPLIT ? PPT : 1], t01[SPLIT ? PPT : 1], t11[SPLIT ? PPT : 1];
@@ -299,18 +317,26 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
         ob[t] = (pk[t] & 15) * 2 * kTX + x;
     }
     const u64* shf = &sh[0][0][0][0];
-    for (int k = 0; k < chunks; k++) {
-        cp_async_wait<kStages - 2>();
+    // one barrier per group of CPS chunks: the copies of group g + RS - 1 overlap groups g..
+    for (int gi = 0; gi < groups; gi++) {
+        cp_async_wait<RS - 2>();
         __syncthreads();
         {
-            const int nk = k + kStages - 1;
+            const int ng = gi + RS - 1;
 #pragma unroll
-            for (int h = 0; h < UPT; h++)
-                if (ucopy[h] && nk < chunks)
-                    cp_async16(&sh[nk % kStages][ucs[h]][upp[h]][uxx[h]], gsrc[h] + (size_t)nk * chunk_stride);
+            for (int c = 0; c < CPS; c++)
+#pragma unroll
+                for (int h = 0; h < UPT; h++)
+                    if (ucopy[h] && ng * CPS + c < chunks)
+                        cp_async16(&sh[(ng % RS) * CPS + c][ucs[h]][upp[h]][uxx[h]],
+                                   gsrc[h] + (size_t)(ng * CPS + c) * chunk_stride);
             cp_async_commit();
         }
-        const u64* st = shf + (k % kStages) * STAGE;
+#pragma unroll
+        for (int c = 0; c < CPS; c++) {
+        const int k = gi * CPS + c;
+        if (k >= chunks) break;
+        const u64* st = shf + ((gi % RS) * CPS + c) * STAGE;
 #pragma unroll
         for (int t = 0; t < PPT; t++) {
             if (pk[t] < 0) continue;
@@ -336,6 +362,7 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
                     fold(s11[t], m);
                 }
             }
+        }
         }
     }
     cp_async_wait<0>();
@@ -1321,6 +1348,17 @@ void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     g_lc_launches += 1;
 }
 
+// the tensor kernels' ring lives in dynamic shared memory (above the 48 KB static limit); the
+// attribute is set once per kernel instantiation
+template <typename K>
+static void tensor_smem_attr(K kernel) {
+    static std::mutex mu;
+    static std::set<const void*> done;  // kernels whose attribute is set
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert(reinterpret_cast<const void*>(kernel)).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTensorSmem);
+}
+
 // first limb of the range [split0, nl) whose primes are all below 2^40 (20-bit split products)
 static int split_start(lc_ctx* c, int nl) {
     int s0 = nl;
@@ -1336,24 +1374,28 @@ void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     if (chunks > (1 << 20)) split0 = nl;
     if (split0 > 0) {
         dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), split0);
-        k_sq_acc_tiled<8, 8, false><<<grid, 256, 0, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, cb, p0, np, c->mc,
-                                                                  out);
+        tensor_smem_attr(k_sq_acc_tiled<8, 8, false>);
+        k_sq_acc_tiled<8, 8, false><<<grid, 256, kTensorSmem, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, cb, p0, np,
+                                                                            c->mc, out);
         g_lc_launches += 1;
     }
     if (split0 < nl) {  // warps per block: LC_TUNE_TENSOR_WARPS (pair slots per thread = 64 / warps, rounded up)
         dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), nl - split0);
         switch (c->tune[LC_TUNE_TENSOR_WARPS]) {
             case 8:
-                k_sq_acc_tiled<8, 8, true><<<grid, 256, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
-                                                                         np, c->mc, out);
+                tensor_smem_attr(k_sq_acc_tiled<8, 8, true>);
+                k_sq_acc_tiled<8, 8, true><<<grid, 256, kTensorSmem, c->stream>>>(cts, n, chunks, nl, split0, c->log_n,
+                                                                                   cb, p0, np, c->mc, out);
                 break;
             case 12:
-                k_sq_acc_tiled<12, 6, true><<<grid, 384, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
-                                                                          np, c->mc, out);
+                tensor_smem_attr(k_sq_acc_tiled<12, 6, true>);
+                k_sq_acc_tiled<12, 6, true><<<grid, 384, kTensorSmem, c->stream>>>(cts, n, chunks, nl, split0,
+                                                                                    c->log_n, cb, p0, np, c->mc, out);
                 break;
             default:
-                k_sq_acc_tiled<16, 4, true><<<grid, 512, 0, c->stream>>>(cts, n, chunks, nl, split0, c->log_n, cb, p0,
-                                                                          np, c->mc, out);
+                tensor_smem_attr(k_sq_acc_tiled<16, 4, true>);
+                k_sq_acc_tiled<16, 4, true><<<grid, 512, kTensorSmem, c->stream>>>(cts, n, chunks, nl, split0,
+                                                                                    c->log_n, cb, p0, np, c->mc, out);
                 break;
         }
         g_lc_launches += 1;
