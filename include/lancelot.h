@@ -142,12 +142,15 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 2 or 1
  *   LC_TUNE_TENSOR_WARPS       batched distance tensor (primes below 2^40): warps per block,
  *                              16 (4 pair slots per thread), 8 (8 slots) or 12 (6 slots)
+ *   LC_TUNE_NTT_ROW_TMA        forward row pass: 0 = one block per tile, 1 = persistent blocks
+ *                              streaming tiles through shared memory with bulk copies (TMA)
  * The paper_2408_06197_b300.autotune module times the options on the caller's workload. */
 #define LC_TUNE_NTT_ROW_MINB 1
 #define LC_TUNE_NTT_COL_MINB 2
 #define LC_TUNE_GROUP_SPLIT_ITEMS 3
 #define LC_TUNE_GROUP_WIDE_ITEMS 4
 #define LC_TUNE_TENSOR_WARPS 5
+#define LC_TUNE_NTT_ROW_TMA 6
 int lc_set_tuning(lc_ctx* ctx, uint32_t knob, int32_t value);
 int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
 

@@ -624,6 +624,12 @@ int lc_ctx_create(const lc_params* prm, int device, void* stream, const lc_alloc
         delete c;
         return LC_ECUDA;
     }
+    c->dev_err = static_cast<unsigned*>(lc_dev_alloc(c, 256));
+    if (!c->dev_err || cudaMemset(c->dev_err, 0, 4) != cudaSuccess) {
+        cudaGetLastError();
+        lc_ctx_destroy(c);
+        return LC_ENOMEM;
+    }
     int st = build_tables(c);
     if (st != LC_OK) {
         lc_ctx_destroy(c);
@@ -638,6 +644,7 @@ void lc_ctx_destroy(lc_ctx* c) {
     cudaStreamSynchronize(c->stream);
     lc_dev_free(c, c->tw_fwd);
     lc_dev_free(c, c->tw_inv);
+    lc_dev_free(c, c->dev_err);
     lc_dev_free(c, c->mc);
     lc_dev_free(c, c->modup);
     lc_dev_free(c, c->moddown);
@@ -668,6 +675,12 @@ int lc_set_stream(lc_ctx* c, void* stream) {
 int lc_sync(lc_ctx* c) {
     if (!c) return LC_EINVAL;
     LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned err = 0;
+    LC_CUDA(c, cudaMemcpy(&err, c->dev_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        LC_CUDA(c, cudaMemset(c->dev_err, 0, 4));
+        return fail(c, LC_ETIMEOUT, "a bounded wait on the device gave up (code " + std::to_string(err) + ")");
+    }
     return check_launch(c, "deferred");
 }
 
@@ -1445,6 +1458,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
         case LC_TUNE_GROUP_SPLIT_ITEMS:
         case LC_TUNE_GROUP_WIDE_ITEMS: ok = value == 1 || value == 2; break;
         case LC_TUNE_TENSOR_WARPS: ok = value == 8 || value == 12 || value == 16; break;
+        case LC_TUNE_NTT_ROW_TMA: ok = value == 0 || value == 1; break;
         default: break;
     }
     if (!ok) return fail(c, LC_EINVAL, "lc_set_tuning: knob " + std::to_string(knob) + " has no option " +
@@ -1454,7 +1468,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
 }
 
 int lc_get_tuning(const lc_ctx* c, uint32_t knob, int32_t* value) {
-    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_TENSOR_WARPS) return LC_EINVAL;
+    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_NTT_ROW_TMA) return LC_EINVAL;
     *value = c->tune[knob];
     return LC_OK;
 }

@@ -100,11 +100,13 @@ struct lc_ctx {
     uint64_t n_keyswitch = 0, n_modup = 0;
     uint32_t max_batch = 0;  // 0 = limited only by the scratch budget
     // tile-shape choices (LC_TUNE_*, set by lc_set_tuning; results never depend on them)
-    int tune[8] = {0, 5, 1, 1, 2, 16, 0, 0};
+    int tune[8] = {0, 5, 1, 1, 2, 16, 0, 0};  // [6] LC_TUNE_NTT_ROW_TMA
     bool debug = false;      // LC_DEBUG set: check every launch, remember the first failure
     std::string debug_err;
     bool capturing = false;  // inside lc_graph_begin / lc_graph_end
     uint64_t capture_launches0 = 0;
+    // device error word: kernels with bounded waits OR in LC_ERR_* codes; lc_sync reports them
+    unsigned* dev_err = nullptr;
     // FP64 encoder (created on first use): slot positions 5^j mod 2N, FFT twiddles, work buffer
     unsigned* enc_pos = nullptr;
     double2* enc_w256 = nullptr;
@@ -123,8 +125,10 @@ struct lc_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
 
-    NttTables tables() const { return NttTables{tw_fwd, tw_inv, mc}; }
-    NttTune ntt_tune() const { return NttTune{tune[LC_TUNE_NTT_ROW_MINB], tune[LC_TUNE_NTT_COL_MINB]}; }
+    NttTables tables() const { return NttTables{tw_fwd, tw_inv, mc, dev_err}; }
+    NttTune ntt_tune() const {
+        return NttTune{tune[LC_TUNE_NTT_ROW_MINB], tune[LC_TUNE_NTT_COL_MINB], tune[LC_TUNE_NTT_ROW_TMA]};
+    }
     int digits(int level) const { return (level + 1 + alpha - 1) / alpha; }
     int qp_mod(int level, int t) const { return t <= level ? t : nq + (t - level - 1); }
 };

@@ -8,8 +8,12 @@
 // two radix-16 halves are separated by one swizzled shared-memory exchange, and a second
 // exchange restores a coalesced store (forward) or load (inverse).
 #include <cuda_runtime.h>
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include "ntt.cuh"
 #include "context.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -207,15 +211,18 @@ __global__ void __launch_bounds__(1 << C, MINB) ntt_inv_col(u64* base, size_t ba
 
 // ------------------------------------------------------------------------------ row pass
 // forward: bits 7 .. 0 inside 256-word blocks; output fully reduced to [0, q)
-template <bool LZ>
-__device__ __forceinline__ void fwd_row_body(u64* a, u64* s, const ModConst& mc, const ulonglong2* tw, int log_n,
-                                             int g_blk) {
+// in: the CTA's 8 blocks (global memory, or a shared-memory copy that `s` may alias: then
+// SYNC_IN makes every thread finish reading before the first exchange); a: the output blocks
+template <bool LZ, bool SYNC_IN = false>
+__device__ __forceinline__ void fwd_row_body(const u64* in, u64* a, u64* s, const ModConst& mc, const ulonglong2* tw,
+                                             int log_n, int g_blk) {
     const int tid = threadIdx.x;
     const int lo = tid & 15, blk = tid >> 4;
     const int g0 = g_blk + (blk << 8);
     u64 x[16];
 #pragma unroll
-    for (int u = 0; u < 16; u++) x[u] = a[(blk << 8) + lo + 16 * u];
+    for (int u = 0; u < 16; u++) x[u] = in[(blk << 8) + lo + 16 * u];
+    if (SYNC_IN) __syncthreads();
 #pragma unroll
     for (int st = 3; st >= 0; st--) {
         const int b = 4 + st;
@@ -262,9 +269,68 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_fwd_row(u64* base, size
     const ModConst mc = tb.mc[mi];
     const ulonglong2* tw = tb.fwd + ((size_t)mi << log_n);
     if (mc.q < kLazyLimit)
-        fwd_row_body<true>(a, s, mc, tw, log_n, blockIdx.x * E);
+        fwd_row_body<true>(a, a, s, mc, tw, log_n, blockIdx.x * E);
     else
-        fwd_row_body<false>(a, s, mc, tw, log_n, blockIdx.x * E);
+        fwd_row_body<false>(a, a, s, mc, tw, log_n, blockIdx.x * E);
+}
+
+// Persistent form of the forward row pass: each block walks tiles (limb, 8 blocks of 256 words)
+// with stride gridDim.x; one thread streams the NEXT tile into the other half of a double
+// buffer with a bulk copy (TMA) while the block transforms the current one, so the global-load
+// latency of a tile overlaps the previous tile's butterflies.  The current tile's buffer also
+// serves as the exchange buffer.  A tile that does not arrive within the poll limit makes the
+// whole block stop (block-wide vote) and report LC_ERR_TIMEOUT.
+template <int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) ntt_fwd_row_tma(u64* base, size_t batch_stride, RowMap map,
+                                                                  int log_n, NttTables tb, int total_tiles) {
+    constexpr int E = 8 * 256;
+    constexpr unsigned BYTES = E * 8;
+    __shared__ __align__(128) u64 buf[2][E];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tiles_per_limb = (1 << log_n) / E;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int mi;
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < total_tiles) {
+        const int b = tile / tiles_per_limb;
+        const u64* src = limb_ptr(base, batch_stride, map, b, log_n, mi) + (size_t)(tile - b * tiles_per_limb) * E;
+        mbar_arrive_expect_tx(&bar[0], BYTES);
+        bulk_load(buf[0], src, BYTES, &bar[0]);
+    }
+    for (int i = 0; tile < total_tiles; i++, tile += gridDim.x) {
+        const int nxt = tile + gridDim.x;
+        const bool more = nxt < total_tiles;
+        if (tid == 0 && more) {  // the other buffer was released by the barrier ending iteration i-1
+            fence_proxy_async();
+            const int b = nxt / tiles_per_limb;
+            const u64* src = limb_ptr(base, batch_stride, map, b, log_n, mi) + (size_t)(nxt - b * tiles_per_limb) * E;
+            mbar_arrive_expect_tx(&bar[(i + 1) & 1], BYTES);
+            bulk_load(buf[(i + 1) & 1], src, BYTES, &bar[(i + 1) & 1]);
+        }
+        const int b = tile / tiles_per_limb;
+        u64* a = limb_ptr(base, batch_stride, map, b, log_n, mi) + (size_t)(tile - b * tiles_per_limb) * E;
+        if (!__syncthreads_and(mbar_wait(&bar[i & 1], (i >> 1) & 1))) {
+            if (tid == 0) {
+                atomicOr(tb.err, LC_ERR_TIMEOUT);
+                if (more) mbar_wait(&bar[(i + 1) & 1], ((i + 1) >> 1) & 1);  // let the copy in flight land
+            }
+            return;
+        }
+        const ModConst mc = tb.mc[mi];
+        const ulonglong2* tw = tb.fwd + ((size_t)mi << log_n);
+        const int g_blk = (tile - b * tiles_per_limb) * E;
+        if (mc.q < kLazyLimit)
+            fwd_row_body<true, true>(buf[i & 1], a, buf[i & 1], mc, tw, log_n, g_blk);
+        else
+            fwd_row_body<false, true>(buf[i & 1], a, buf[i & 1], mc, tw, log_n, g_blk);
+        __syncthreads();  // this buffer is free for the copy issued two tiles later
+    }
 }
 
 // inverse: bits 0 .. 7 inside 256-word blocks (global stages 0 .. 7), input in [0, 2q)
@@ -352,6 +418,27 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size
         default: KERNEL<5><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;          \
     }
 
+// persistent grid of a row-pass kernel: resident blocks per SM x SMs (queried once per kernel)
+template <typename K>
+static int persistent_grid(K kernel, int total) {
+    static std::mutex mu;
+    static std::map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(reinterpret_cast<const void*>(kernel));
+    int cap;
+    if (it != cache.end()) {
+        cap = it->second;
+    } else {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kRowThreads, 0);
+        cap = std::max(1, sms * std::max(1, per));
+        cache[reinterpret_cast<const void*>(kernel)] = cap;
+    }
+    return std::min(total, cap);
+}
+
 void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n, const NttTables& tb,
                  cudaStream_t s, NttTune tune) {
     const int limbs = batch * map.n;
@@ -359,7 +446,28 @@ void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, i
     const int C = log_n - 8;
     dim3 gc(16, limbs), gr((1 << log_n) / 2048, limbs);
     LC_COL_DISPATCH(ntt_fwd_col, tune.col_minb, C, gc, s)
-    LC_ROW_DISPATCH(ntt_fwd_row, tune.row_minb, gr, s)
+    if (tune.row_tma) {
+        const int total = limbs * ((1 << log_n) / 2048);
+        switch (tune.row_minb) {
+            case 4: {
+                const int g = persistent_grid(ntt_fwd_row_tma<4>, total);
+                ntt_fwd_row_tma<4><<<g, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb, total);
+                break;
+            }
+            case 6: {
+                const int g = persistent_grid(ntt_fwd_row_tma<6>, total);
+                ntt_fwd_row_tma<6><<<g, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb, total);
+                break;
+            }
+            default: {
+                const int g = persistent_grid(ntt_fwd_row_tma<5>, total);
+                ntt_fwd_row_tma<5><<<g, kRowThreads, 0, s>>>(base, batch_stride, map, log_n, tb, total);
+                break;
+            }
+        }
+    } else {
+        LC_ROW_DISPATCH(ntt_fwd_row, tune.row_minb, gr, s)
+    }
     g_lc_launches += 2;
 }
 

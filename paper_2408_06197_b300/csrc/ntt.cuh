@@ -30,12 +30,14 @@ struct NttTables {
     const ulonglong2* fwd;     // [n_mod][N] {psi^{br(k)}, shoup}
     const ulonglong2* inv;     // [n_mod][N] {psi^{-br(k)}, shoup}; index 0 holds psi^{-br(1)} * N^-1
     const ModConst* mc;        // [n_mod]
+    unsigned* err;             // the context's device error word (bounded waits report here)
 };
 
 // launch-shape choices (register caps) picked by the tuner; results do not depend on them
 struct NttTune {
     int row_minb = 5;  // row pass: minimum resident blocks of 128 threads (4, 5 or 6)
     int col_minb = 1;  // column pass: 1 (no cap), 6 or 8
+    int row_tma = 0;   // forward row pass: 1 = persistent blocks streaming tiles with bulk copies
 };
 
 void ntt_forward(u64* base, size_t batch_stride, int batch, const RowMap& map, int log_n,

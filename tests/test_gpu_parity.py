@@ -611,3 +611,26 @@ def test_other_ring_degrees_bit_exact(log_n):
                         groups=sched)
     Do = o.distances(ocs, orlk, sched, ork, qp_sum=True)
     assert np.array_equal(LC.torch_to_u64(g.to_coeff(Dg, prm.L - 1)), o.to_coeff(Do))
+
+
+@pytest.mark.parametrize("n_polys", [1, 7, 53])
+def test_tma_row_pass_matches_per_tile_row_pass(prod, n_polys):
+    """Forward NTT with the persistent bulk-copy row pass (each block walks several tiles at 53
+    polynomials x 15 limbs x 16 tiles, with a ragged last wave) equals the one-block-per-tile pass
+    bit for bit, round-trips, and leaves the context's error word clear."""
+    LC, g = prod.LC, prod.g
+    rng = np.random.default_rng(n_polys)
+    a = np.stack([np.stack([rng.integers(0, q, size=prod.N, dtype=np.uint64) for q in prod.prm.q])
+                  for _ in range(n_polys)])
+    ga = LC.u64_to_torch(a)
+    before = g.get_tuning(LC.LC_TUNE_NTT_ROW_TMA)
+    try:
+        g.set_tuning(LC.LC_TUNE_NTT_ROW_TMA, 0)
+        ref = LC.torch_to_u64(g.to_eval(ga, prod.L))
+        g.set_tuning(LC.LC_TUNE_NTT_ROW_TMA, 1)
+        ev = g.to_eval(ga, prod.L)
+        assert np.array_equal(LC.torch_to_u64(ev), ref)
+        assert np.array_equal(LC.torch_to_u64(g.to_coeff(ev, prod.L)), a)
+        g.sync()
+    finally:
+        g.set_tuning(LC.LC_TUNE_NTT_ROW_TMA, before)
