@@ -70,6 +70,136 @@ def peaks():
         return 6400.0, "fallback"
 
 
+# Integer-pipe roofline.  The transforms are bound by 64-bit modular arithmetic emulated on the
+# 32-bit integer pipes, not by DRAM.  Their ceiling is measured the way the copy bandwidth and the
+# GEMM rate are: the library's register-resident probe runs the very butterfly of the transforms
+# (lazy Shoup Cooley-Tukey, twiddles in registers, no memory traffic) on every SM, live in the same
+# run at the same clock.  The IMAD probe checks the unit count behind it: 148 SMs x 64 32-bit
+# multiply-adds per clock (profiles/alu_probes.md).
+def run_batched(args):
+    """The batched workload at full size: 50 clients x 256 chunks (94 GB of ciphertexts resident),
+    1,225 pair distances + the masked aggregate of 256 chunks per step, autotuned schedule and
+    tiles, eager launches (the library runs the pairs in waves).  Inputs are encrypted on the GPU
+    with device randomness (the clients' batched step), which is outside the timed region."""
+    import torch
+    from paper_2408_06197_b300 import autotune, kgc
+    from paper_2408_06197_b300 import lancelot as LC
+
+    w = S.BATCHED
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    with torch.cuda.stream(stream):
+        g = LC.Context.production(device=0, stream=stream)
+        N = g.N
+        s = S.secret_key(w.seed, w.config, N)
+        pk = g.pk_gen(s, *S.pk_rand(w.seed, w.config, g.q, N))
+        evk = g.evk()
+        qp = g.q + g.p
+        evk.add(s, None, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, None))
+        rots = set()
+        for nm in SCHEDULES:
+            rots |= set(LC.rotations_of_schedule(SCHEDULES[nm]))
+        for r in sorted(rots):
+            evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
+        cts = g.empty(w.n_clients, w.chunks, 2, g.nq, N)
+        flat = cts.view(w.n_clients * w.chunks, 2, g.nq, N)
+        sq = np.zeros((w.n_clients, w.n_clients))
+        Ws = []
+        for i in range(w.n_clients):
+            Wi = S.client_updates(w, [i])[0]
+            Ws.append(Wi)
+            z = torch.tensor(S.split_chunks(Wi, g.slots), device="cuda:0")
+            g.encode_encrypt_seeded(pk, z, g.scale, w.seed, i * w.chunks, out=flat[i * w.chunks:(i + 1) * w.chunks])
+        for i in range(w.n_clients):
+            for j in range(i + 1, w.n_clients):
+                sq[i, j] = sq[j, i] = float(np.sum((Ws[i] - Ws[j]) ** 2))
+        del Ws
+        sel = kgc.krum_select(sq, w.f, w.n_select)
+        wts = torch.tensor(kgc.mask_weights(w.n_clients, sel, average=True), dtype=torch.float64, device="cuda:0")
+        masks = g.encrypt_const_seeded(pk, wts, g.scale, w.seed, 1 << 40)
+        out_d = g.empty(w.n_pairs, 2, g.L, N)
+        out_a = g.empty(w.chunks, 2, g.L, N)
+        t0 = time.perf_counter()
+        # tune on a 10-client slice of the same ciphertexts (the tiles and schedule do not depend
+        # on the client count; a full-size trial would take seconds each)
+        sub = cts[:10].contiguous()
+        tun = autotune.tune(g, evk, sub, 10, w.chunks, g.scale, schedules=dict(SCHEDULES))
+        del sub
+        tune_s = time.perf_counter() - t0
+        mode = autotune.schedule_mode(tun["schedule"])
+
+        def step():
+            g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=mode, groups=tun["groups"], out=out_d)
+            g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, out=out_a)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        ms = sum(step_ms) / args.steps
+        # accuracy of the last step's read-outs against the FP64 distances (untimed)
+        _, sc = g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=mode, groups=tun["groups"], out=out_d)
+        got = g.decrypt_const(s, out_d, g.L - 1, sc)
+        ref = np.array([sq[i, j] for i in range(w.n_clients) for j in range(i + 1, w.n_clients)])
+        rel = float(np.max(np.abs(got - ref) / ref))
+        g.sync()
+    line = {"metric": "encrypted client-pair distances/s (N=2^15, d=2^22, n=50)", "value": w.n_pairs / (ms / 1e3),
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (GPU encode + encryption with device randomness)",
+            "config": {"workload": "batched_N32768_n50_d2^22_256chunks_1225pairs+masked_aggregate",
+                       "n_clients": w.n_clients, "d": w.d, "chunks": w.chunks, "pairs": w.n_pairs,
+                       "rotation_schedule": tun["schedule"], "tuning": tun["knobs"], "tune_seconds": tune_s,
+                       "launch": "eager (pairs in waves inside the library)",
+                       "l2": "inputs larger than L2 (94 GB client ciphertexts resident)"},
+            "aggregate_chunks_per_s": w.chunks / (ms / 1e3), "clocks": ck, "max_rel_err_vs_fp64": rel,
+            "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))}}
+    print(json.dumps(line), flush=True)
+
+
+def run_probes(args):
+    """One JSON line: each probe at 4, 8 and 16 resident blocks of 256 threads per SM."""
+    import torch
+    from paper_2408_06197_b300 import lancelot as LC
+    g = LC.Context.toy(device=0)
+    out = {}
+    for kind, name in ((LC.LC_PROBE_IMAD, "imad"), (LC.LC_PROBE_IMAD_WIDE, "imad_wide"),
+                       (LC.LC_PROBE_NTT_BFLY, "ntt_butterfly")):
+        iters = args.probe_iters if kind != LC.LC_PROBE_NTT_BFLY else max(1, args.probe_iters // 2)
+        for bps in (4, 8, 16):
+            r = g.alu_probe(kind, iters, bps)
+            out[f"{name}_x{bps}"] = {"ms": r["ms"], "T_ops_per_s": r["ops_per_s"] / 1e12}
+    g.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"probes": out, "unit": "T operations/s (butterflies for ntt_butterfly)"}), flush=True)
+
+
+def alu_roofline(g, ntt_bytes: float, ntt_ms: float, sm_mhz):
+    """NTT butterflies/s against the live register-resident probe of the same butterfly."""
+    probes = {}
+    for kind, name, iters in ((0, "imad", 4096), (1, "imad_wide", 4096), (2, "ntt_butterfly", 2048)):
+        r = g.alu_probe(kind, iters, 8)
+        probes[name] = {"T_ops_per_s": r["ops_per_s"] / 1e12, "ms": r["ms"]}
+    limbs = ntt_bytes / (16.0 * g.N)
+    bfly = limbs * (g.N // 2) * g.log_n
+    achieved = bfly / (ntt_ms / 1e3) / 1e12 if ntt_ms > 0 else 0.0
+    peak = probes["ntt_butterfly"]["T_ops_per_s"]
+    mhz = sm_mhz or 2032.0
+    return {"achieved": achieved, "peak": peak, "unit": "T butterflies/s", "frac": achieved / peak,
+            "peak_source": "register-resident butterfly probe of the same code, measured live (lc_alu_probe)",
+            "butterflies": bfly, "imad_nominal_T_per_s": 148 * 64 * mhz * 1e6 / 1e12, "sm_mhz": mhz,
+            "probes": probes}
+
+
 # ----------------------------------------------------------------------------- clocks sampler
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -232,8 +362,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- kernel micro case
 def run_micro(args):
     """Small isolated case for profiler captures (about 4 GB on the device, inputs larger than
-    L2): batched distances of 10 clients x 8 chunks (45 pairs, rotation schedule --schedule) and
-    their masked aggregate (8 chunks), 960 limbs transformed forward and
+    L2): batched distances of 10 clients x C chunks (C = --micro-chunks, default 8; 45 pairs,
+    rotation schedule --schedule) and their masked aggregate (C chunks), 960 limbs transformed forward and
     back, 16 degree-2 triples relinearised and rescaled at level 14, and 16 ciphertexts rotated
     at level 13.  Prints per-class timings."""
     import torch
@@ -251,7 +381,7 @@ def run_micro(args):
     ct3 = torch.randint(0, 1 << 40, (B, 3, g.nq, N), device="cuda", generator=gen)
     cts = torch.randint(0, 1 << 40, (B, 2, g.L, N), device="cuda", generator=gen)
     xl = torch.randint(0, 1 << 40, (64, g.nq, N), device="cuda", generator=gen)
-    # batched distances over 10 clients x 8 chunks of random residues (45 pairs, 600 MB input),
+    # batched distances over 10 clients x C chunks of random residues (45 pairs, 75 MB per chunk),
     # rotate-and-sum in one-ModDown groups of the chosen schedule
     sname = "g3qp" if args.schedule == "auto" else args.schedule
     sched = SCHEDULES[sname]
@@ -260,9 +390,10 @@ def run_micro(args):
         if r != 1:
             evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r))
     rng = np.random.default_rng(5)
-    dc = np.empty((10, 8, 2, g.nq, N), dtype=np.uint64)
+    C = args.micro_chunks
+    dc = np.empty((10, C, 2, g.nq, N), dtype=np.uint64)
     for i, q in enumerate(g.q):
-        dc[:, :, :, i] = rng.integers(0, q, size=(10, 8, 2, N), dtype=np.uint64)
+        dc[:, :, :, i] = rng.integers(0, q, size=(10, C, 2, N), dtype=np.uint64)
     dcts = LC.u64_to_torch(dc)
     dm = np.empty((10, 2, g.nq, N), dtype=np.uint64)
     for i, q in enumerate(g.q):
@@ -270,17 +401,17 @@ def run_micro(args):
     dmasks = LC.u64_to_torch(dm)
     del dc, dm
     dout = g.empty(45, 2, g.L, N)
-    aout = g.empty(8, 2, g.L, N)
+    aout = g.empty(C, 2, g.L, N)
     nvtx = torch.cuda.nvtx
     for it in range(args.warmup + args.steps):
         if it == args.warmup:
             g.profile_start()
         # NVTX ranges name the phases for profiler filters (ncu --nvtx --nvtx-include "ntt/")
         nvtx.range_push("distances")
-        g.distances(evk, dcts, 10, 8, g.scale, mode=LC.LC_MODE_BATCHED | qpf, groups=sched, out=dout)
+        g.distances(evk, dcts, 10, C, g.scale, mode=LC.LC_MODE_BATCHED | qpf, groups=sched, out=dout)
         nvtx.range_pop()
         nvtx.range_push("aggregate")
-        g.masked_aggregate(evk, dcts, 10, 8, g.scale, dmasks, g.scale, out=aout)
+        g.masked_aggregate(evk, dcts, 10, C, g.scale, dmasks, g.scale, out=aout)
         nvtx.range_pop()
         nvtx.range_push("ntt")  # 960 limbs forward then inverse, in place
         g.to_eval(xl, g.L, inplace=True)
@@ -492,6 +623,7 @@ def main():
     ap.add_argument("--no-client", action="store_true", help="skip the client-side encode+encrypt measurement")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels eagerly instead of replaying a CUDA graph")
     ap.add_argument("--micro", action="store_true", help="small isolated kernel case for profiler captures")
+    ap.add_argument("--micro-chunks", type=int, default=8, help="chunks per client in the --micro distances")
     ap.add_argument("--serving", action="store_true", help="Poisson-arrival serving loop; one line per rate")
     ap.add_argument("--rates", default="1,2,5", help="serving arrival rates (rounds/s), comma separated")
     ap.add_argument("--rounds", type=int, default=100, help="serving rounds per rate")
@@ -499,6 +631,12 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
     ap.add_argument("--host-kgc", action="store_true",
                     help="serving: KGC step on the host (default: on the device, no host round trip)")
+    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
+                    help="batched = n=50 clients, d=2^22 (256 ciphertexts each, 94 GB resident), 1,225 pairs; "
+                         "one JSON line beside the headline workload")
+    ap.add_argument("--probes", action="store_true",
+                    help="integer-pipe probes only (register-resident IMAD, wide IMAD, NTT butterfly)")
+    ap.add_argument("--probe-iters", type=int, default=4096)
     ap.add_argument("--sweep", action="store_true", help="packing-size sweep; one line per N")
     ap.add_argument("--sweep-log-n", default="13,14,15,16")
     args = ap.parse_args()
@@ -512,6 +650,12 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.probes:
+        run_probes(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
     if args.serving:
         # rounds of 0.1-75 GiB come and go: let the caching allocator grow segments instead of
@@ -719,17 +863,28 @@ def main():
         # 2 N 8 per limb, so limbs per call = bytes / (16 N) / calls
         limbs_per_call = d["bytes"] / (16.0 * g.N) / d["launches"]
         traffic = NTT_DRAM_BYTES_PER_LIMB * limbs_per_call
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": peak_kind, "traffic": traffic,
-            "traffic_source": "ncu dram__bytes of the 960-limb transform case, per limb x limbs per call"
-            if traffic else None,
-            "launches": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(1, d["launches"]),
-            "share_of_step": d["ms"] / (ms if not use_graph else sum(v["ms"] for v in prof.values()) or 1.0),
-            "measured_in": "timed region with per-launch CUDA events" + (" (eager replay of the graph's steps)"
-                                                                         if use_graph else ""),
-            "classes": {k: {"ms_per_step": v["ms"] / args.steps, "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9)
-                            if v["ms"] > 0 else 0.0, "launches_per_step": v["launches"] / args.steps}
-                        for k, v in prof.items()}}
+    hbm_view = {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind}
+    alu = None
+    if dom == "ntt":
+        with torch.cuda.stream(stream):
+            alu = alu_roofline(g, d["bytes"], d["ms"], ck.get("sm_mhz"))
+    if alu is not None:  # the transforms are bound by integer issue, not by DRAM
+        roof = {"bound": "alu", "kernel": dom, "achieved": alu["achieved"], "peak": alu["peak"],
+                "unit": alu["unit"], "frac": alu["frac"], "peak_source": alu["peak_source"], "hbm": hbm_view,
+                "alu": alu}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, **hbm_view}
+    roof.update({
+        "traffic": traffic,
+        "traffic_source": ("ncu dram__bytes of the 960-limb transform case, per limb x limbs per call"
+                           if traffic else None),
+        "launches": d["launches"], "avg_launch_us": d["ms"] * 1e3 / max(1, d["launches"]),
+        "share_of_step": d["ms"] / (ms if not use_graph else sum(v["ms"] for v in prof.values()) or 1.0),
+        "measured_in": "timed region with per-launch CUDA events" + (" (eager replay of the graph's steps)"
+                                                                     if use_graph else ""),
+        "classes": {k: {"ms_per_step": v["ms"] / args.steps, "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9)
+                        if v["ms"] > 0 else 0.0, "launches_per_step": v["launches"] / args.steps}
+                    for k, v in prof.items()}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",

@@ -154,6 +154,20 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
 int lc_set_tuning(lc_ctx* ctx, uint32_t knob, int32_t value);
 int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
 
+/* Integer-pipe probes (measurement only; no counterpart in the paper).  Runs one register-
+ * resident kernel of `kind` on the context's device and stream: blocks_per_sm x SM-count blocks
+ * of 256 threads, each thread executing iters x 64 operations (LC_PROBE_NTT_BFLY: iters x 32
+ * butterflies), and returns its device time in *ms (CUDA events) and the operations executed in
+ * *ops.  Kinds: LC_PROBE_IMAD, 32-bit multiply-adds; LC_PROBE_IMAD_WIDE, 32 x 32 -> 64-bit
+ * multiply-adds; LC_PROBE_NTT_BFLY, the lazy Shoup Cooley-Tukey butterfly of the transforms for
+ * primes below 2^46 (the same code, twiddles in registers, no memory traffic).  The kernels read
+ * no buffer and write none (one library-owned word at most); the call synchronises the stream.
+ * LC_EINVAL for an unknown kind, iters == 0 or blocks_per_sm outside [1, 32]. */
+#define LC_PROBE_IMAD 0
+#define LC_PROBE_IMAD_WIDE 1
+#define LC_PROBE_NTT_BFLY 2
+int lc_alu_probe(lc_ctx* ctx, uint32_t kind, uint32_t iters, uint32_t blocks_per_sm, double* ms, double* ops);
+
 /* CUDA-graph capture of a sequence of calls on the context's stream (no counterpart in the
  * paper; replaces per-call kernel launches with one graph launch).  Between lc_graph_begin and
  * lc_graph_end only device-pointer evaluation calls may be made; their scratch must already be

@@ -14,6 +14,7 @@
 #include "context.cuh"
 #include "host_math.hpp"
 #include "ops.cuh"
+#include "probe.cuh"
 
 using lc::hinv;
 using lc::hmul;
@@ -395,6 +396,40 @@ static void ks_moddown(lc_ctx* c, u64* v, int B, int level, const KsBufs& k, con
          op_moddown_combine(c, v, k.conv, B, level, add0, add0_stride, add1, add1_stride, w, w_stride));
 }
 
+// ModDown of v (overwritten) fused with the rescale that follows it: out[b] (level limbs) =
+// rescale(add + MD(v)), bit-identical to ks_moddown then do_rescale with one forward NTT per limb
+// instead of two (op_mdrs_prep / op_mdrs_combine).  Uses k.coef (free after the inner product)
+// for the last limb of (add0, add1) in the coefficient domain.
+static void ks_moddown_rescale(lc_ctx* c, u64* v, int B, int level, const KsBufs& k, const u64* add0,
+                               size_t add0_stride, const u64* add1, size_t add1_stride, u64* out, size_t out_stride) {
+    const size_t N = c->N;
+    const int nl = level + 1, rows = nl + c->np;
+    RowMap mi{};
+    mi.n = 2 * (c->np + 1);
+    for (int p = 0; p < 2; p++) {
+        for (int m = 0; m < c->np; m++) {
+            mi.row[p * (c->np + 1) + m] = (uint16_t)(p * rows + nl + m);
+            mi.mod[p * (c->np + 1) + m] = (uint8_t)(c->nq + m);
+        }
+        mi.row[p * (c->np + 1) + c->np] = (uint16_t)(p * rows + level);
+        mi.mod[p * (c->np + 1) + c->np] = (uint8_t)level;
+    }
+    ntt_inv_p(c, v, (size_t)2 * rows * N, B, mi);
+    u64* al = k.coef;  // [B][2][N]
+    cudaMemcpy2DAsync(al, 2 * N * 8, add0 + (size_t)level * N, add0_stride * 8, N * 8, B, cudaMemcpyDeviceToDevice,
+                      c->stream);
+    cudaMemcpy2DAsync(al + N, 2 * N * 8, add1 + (size_t)level * N, add1_stride * 8, N * 8, B,
+                      cudaMemcpyDeviceToDevice, c->stream);
+    ntt_inv_p(c, al, N, 2 * B, rows_seq(1, level));
+    PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * (c->np + nl), (uint64_t)B,
+         op_moddown_bconv(c, v, B, level, k.conv));
+    PROF(c, PROF_RESCALE, (double)N * 8.0 * 2.0 * B * (2.0 * level + 3.0), (uint64_t)B,
+         op_mdrs_prep(c, v, al, k.conv, B, level));
+    ntt_fwd_p(c, k.conv, (size_t)nl * N, 2 * B, rows_seq(level));
+    PROF(c, PROF_MODDOWN, (double)N * 8.0 * 2.0 * B * level * 4.0, (uint64_t)B,
+         op_mdrs_combine(c, v, k.conv, B, level, add0, add0_stride, add1, add1_stride, out, out_stride));
+}
+
 // inner product with one key + ModDown; W[b] = (add0 + MD(v0), add1 + MD(v1))
 static void ks_apply(lc_ctx* c, const u64* d, size_t d_stride, int B, int level, const u64* key, const KsBufs& k,
                      const u64* add0, const u64* add1, size_t add_stride, u64* w, size_t w_stride) {
@@ -415,6 +450,18 @@ static int do_relin(lc_ctx* c, const lc_evk* evk, const u64* ct3, int B, int lev
     KsBufs kb = ks_layout(c, tmp, B, level);
     ks_modup(c, ct3 + 2 * P, 3 * P, B, level, kb);
     ks_apply(c, ct3 + 2 * P, 3 * P, B, level, k->data, kb, ct3, ct3 + P, 3 * P, out, 2 * P);
+    return LC_OK;
+}
+
+// relinearise B triples ct3 [B][3][nl][N] and rescale: out [B][2][level][N] (tmp = ks scratch)
+static int do_relin_rescale(lc_ctx* c, const lc_evk* evk, const u64* ct3, int B, int level, u64* out, u64* tmp) {
+    const SwKey* k = find_key(evk, -1);
+    if (!k) return fail(c, LC_EKEY, "relinearisation key missing");
+    const size_t P = (size_t)(level + 1) * c->N;
+    KsBufs kb = ks_layout(c, tmp, B, level);
+    ks_modup(c, ct3 + 2 * P, 3 * P, B, level, kb);
+    ks_inner(c, ct3 + 2 * P, 3 * P, B, level, k->data, kb, kb.v);
+    ks_moddown_rescale(c, kb.v, B, level, kb, ct3, 3 * P, ct3 + P, 3 * P, out, (size_t)2 * level * c->N);
     return LC_OK;
 }
 
@@ -1473,6 +1520,40 @@ int lc_get_tuning(const lc_ctx* c, uint32_t knob, int32_t* value) {
     return LC_OK;
 }
 
+int lc_alu_probe(lc_ctx* c, uint32_t kind, uint32_t iters, uint32_t blocks_per_sm, double* ms, double* ops) {
+    clear_prior_error();
+    if (!c || !ms || !ops || kind > LC_PROBE_NTT_BFLY || iters == 0 || blocks_per_sm < 1 || blocks_per_sm > 32)
+        return fail(c, LC_EINVAL, "lc_alu_probe: bad argument");
+    int sms = 0;
+    LC_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int blocks = sms * (int)blocks_per_sm;
+    auto* sink = static_cast<unsigned long long*>(lc_dev_alloc(c, sizeof(unsigned long long)));
+    if (!sink) return fail(c, LC_ENOMEM, "lc_alu_probe: allocation failed");
+    cudaEvent_t e0, e1;
+    LC_CUDA(c, cudaEventCreate(&e0));
+    LC_CUDA(c, cudaEventCreate(&e1));
+    auto launch = [&] {
+        if (kind == LC_PROBE_IMAD) probe_imad(blocks, iters, sink, c->stream);
+        else if (kind == LC_PROBE_IMAD_WIDE) probe_imad_wide(blocks, iters, sink, c->stream);
+        else probe_ntt_bfly(blocks, iters, sink, c->stream);
+    };
+    launch();  // warm: module loaded, clocks up
+    cudaEventRecord(e0, c->stream);
+    launch();
+    cudaEventRecord(e1, c->stream);
+    g_lc_launches += 2;
+    cudaError_t st = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (st == cudaSuccess) st = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lc_dev_free(c, sink);
+    LC_CUDA(c, st);
+    *ms = t;
+    *ops = (double)blocks * kProbeThreads * iters * (kind == LC_PROBE_NTT_BFLY ? 32.0 : 64.0);
+    return check_launch(c, "lc_alu_probe");
+}
+
 int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                  uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale) {
     clear_prior_error();
@@ -1537,12 +1618,17 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         }
         int st = check_launch(c, "lc_distances (tensor accumulate)");
         if (st) return st;
-        st = do_relin(c, evk, acc3, b, L, ct2, tmp);
-        if (!st) st = check_launch(c, "lc_distances (relinearisation)");
-        if (st) return st;
         u64* y = dout + (size_t)p0 * 2 * Pout;
-        do_rescale(c, ct2, b, 2, L, y, tmp);
-        st = check_launch(c, "lc_distances (rescale)");
+        if (mode == LC_MODE_PER_OP) {  // one operation per launch sequence: relinearise, then rescale
+            st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+            if (!st) st = check_launch(c, "lc_distances (relinearisation)");
+            if (st) return st;
+            do_rescale(c, ct2, b, 2, L, y, tmp);
+        } else {
+            st = do_relin_rescale(c, evk, acc3, b, L, y, tmp);
+            if (st) return st;
+        }
+        st = check_launch(c, "lc_distances (relinearisation + rescale)");
         if (st) return st;
         st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp, qp);
         if (!st) st = check_launch(c, "lc_distances (rotate-and-sum)");
@@ -1579,7 +1665,7 @@ bool job_ok(lc_ctx* c, const lc_job& j, bool agg) {
 
 // relinearisation + rescale + (optional) rotate-and-sum of `b` items whose degree-2 sums are in
 // acc3, with per-item key pointer arrays already on the device; results in y [b][2][L][N]
-static int items_tail(lc_ctx* c, u64* acc3, u64* ct2, u64* y, u64* tmp, int b, const u64* const* relin_keys,
+static int items_tail(lc_ctx* c, u64* acc3, u64* y, u64* tmp, int b, const u64* const* relin_keys,
                       const std::vector<const u64* const*>& group_keys, const std::vector<int>& group_t,
                       const std::vector<std::vector<uint64_t>>& group_gal, bool rotate, bool qp) {
     const int L = c->nq - 1;
@@ -1591,9 +1677,8 @@ static int items_tail(lc_ctx* c, u64* acc3, u64* ct2, u64* y, u64* tmp, int b, c
         PROF(c, PROF_INNER, (double)N * 8.0 * b * (c->digits(L) + 2.0) * (L + 1 + c->np), (uint64_t)b,
              op_inner_items(c, kb.ext, acc3 + 2 * Pin, 3 * Pin, b, L, relin_keys, 1, kb.v, 0));
         c->n_keyswitch += (uint64_t)b;
-        ks_moddown(c, kb.v, b, L, kb, acc3, 3 * Pin, acc3 + Pin, 3 * Pin, ct2, 2 * Pin);
+        ks_moddown_rescale(c, kb.v, b, L, kb, acc3, 3 * Pin, acc3 + Pin, 3 * Pin, y, (size_t)2 * L * N);
     }
-    do_rescale(c, ct2, b, 2, L, y, tmp);
     if (!rotate) return check_launch(c, "batch (relinearise + rescale)");
     const int level = L - 1, nl = L, rows = nl + c->np;
     const size_t P = (size_t)nl * N;
@@ -1728,7 +1813,7 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
              op_sq_acc_items(c, reinterpret_cast<const PairItem*>(desc + o_items), b, c->nq, acc3));
         std::vector<const u64* const*> gkd(sched.size());
         for (size_t gi = 0; gi < sched.size(); gi++) gkd[gi] = reinterpret_cast<const u64* const*>(desc + o_gk[gi]);
-        int st = items_tail(c, acc3, ct2, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), gkd, gt, gal,
+        int st = items_tail(c, acc3, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), gkd, gt, gal,
                             true, qp);
         if (st) return st;
         op_copy_items(c, y, 2 * Pout, reinterpret_cast<u64* const*>(desc + o_dst), b);
@@ -1783,7 +1868,7 @@ int lc_batch_aggregate(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs) {
         LC_CUDA(c, cudaMemcpyAsync(desc, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice, c->stream));
         PROF(c, PROF_TENSOR, 0.0, (uint64_t)b,
              op_mask_acc_items(c, reinterpret_cast<const AggItem*>(desc + o_items), b, c->nq, acc3));
-        int st = items_tail(c, acc3, ct2, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), {}, {}, {},
+        int st = items_tail(c, acc3, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), {}, {}, {},
                             false, false);
         if (st) return st;
         op_copy_items(c, y, 2 * Pout, reinterpret_cast<u64* const*>(desc + o_dst), b);
@@ -1835,9 +1920,15 @@ int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint3
         const int b = std::min(Bw, (int)chunks - k0);
         PROF(c, PROF_TENSOR, ((double)n * b * 2.0 + 2.0 * n + 3.0 * b) * Pin * 8.0, (uint64_t)b,
              op_mask_acc(c, din, (int)n, (int)chunks, c->nq, dm, k0, b, acc3));
-        int st = do_relin(c, evk, acc3, b, L, ct2, tmp);
-        if (st) return st;
-        do_rescale(c, ct2, b, 2, L, dout + (size_t)k0 * 2 * Pout, tmp);
+        int st;
+        if (mode == LC_MODE_PER_OP) {
+            st = do_relin(c, evk, acc3, b, L, ct2, tmp);
+            if (st) return st;
+            do_rescale(c, ct2, b, 2, L, dout + (size_t)k0 * 2 * Pout, tmp);
+        } else {
+            st = do_relin_rescale(c, evk, acc3, b, L, dout + (size_t)k0 * 2 * Pout, tmp);
+            if (st) return st;
+        }
     }
     if (out_host) LC_CUDA(c, cudaMemcpyAsync(out, dout, out_words * 8, cudaMemcpyDeviceToHost, c->stream));
     if (out_scale) *out_scale = scale * mask_scale / (double)c->mod[L];

@@ -14,6 +14,7 @@
 #include "ntt.cuh"
 #include "context.cuh"
 #include "tma.cuh"
+#include "probe.cuh"
 
 namespace {
 
@@ -417,6 +418,41 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size
         case 6: KERNEL<6><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;           \
         default: KERNEL<5><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;          \
     }
+
+// Register-resident copy of the forward butterfly network: radix-16 blocks of the lazy
+// Cooley-Tukey butterfly (the 40-bit-prime path of the transforms above) with twiddles held in
+// registers, so that the butterfly arithmetic runs without memory traffic or exchanges.  The
+// values wrap modulo 2^64 instead of staying reduced; the instruction stream is the same.
+__global__ void __launch_bounds__(kProbeThreads) ntt_bfly_probe(u64 q, u64 w, u64 w_sh, uint32_t iters,
+                                                                unsigned long long* sink) {
+    u64 x[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = (u64)threadIdx.x * 16 + u + blockIdx.x;
+    ulonglong2 tw[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) tw[k] = make_ulonglong2(w + 2 * k, w_sh - 2 * k);
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int st = 3; st >= 0; st--) {
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                if (u >> st & 1) continue;
+                ct_bfly<true>(x[u], x[u | (1 << st)], tw[st], q, 2 * q);
+            }
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int u = 0; u < 16; u++) acc ^= x[u];
+    if (acc == 0x9e3779b97f4a7c15ull) atomicAdd(sink, 1ull);
+}
+
+void probe_ntt_bfly(int blocks, uint32_t iters, unsigned long long* sink, cudaStream_t s) {
+    // the largest 40-bit prime q = 1 mod 2^16, and a Shoup pair for one of its residues
+    const u64 q = 1099510054913ull, w = 0x5f3759df12ull % q;
+    const u64 w_sh = (u64)(((unsigned __int128)w << 64) / q);
+    ntt_bfly_probe<<<blocks, kProbeThreads, 0, s>>>(q, w, w_sh, iters, sink);
+}
 
 // persistent grid of a row-pass kernel: resident blocks per SM x SMs (queried once per kernel)
 template <typename K>

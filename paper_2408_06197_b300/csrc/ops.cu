@@ -174,10 +174,13 @@ __device__ __forceinline__ void mac_split(Acc3& s, unsigned h, unsigned l, unsig
     s.b += (u64)l * h2;
     s.c += (u64)l * l2;
 }
-// the same with explicit PTX wide multiply-adds (measured faster in the distance tensor kernel,
-// slower in the others)
+// the same as explicit 32-bit multiply-adds with a carry chain into the two halves of each
+// 64-bit partial sum (measured faster than 64-bit wide multiply-adds in the distance tensor
+// kernel, slower in the others)
 __device__ __forceinline__ void mad_wide(u64& acc, unsigned a, unsigned b) {
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+    unsigned lo = (unsigned)acc, hi = (unsigned)(acc >> 32);
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;" : "+r"(lo), "+r"(hi) : "r"(a), "r"(b));
+    acc = ((u64)hi << 32) | lo;
 }
 __device__ __forceinline__ void mac_split_w(Acc3& s, unsigned h, unsigned l, unsigned h2, unsigned l2) {
     mad_wide(s.a, h, h2);
@@ -1166,6 +1169,68 @@ __global__ void k_moddown_combine(const u64* __restrict__ v, const u64* __restri
     }
 }
 
+// ---------------------------------------------------------------------------- ModDown + rescale
+// A relinearisation followed by a rescale, fused so that each limb i < l of the result takes one
+// forward NTT instead of two.  With x = add + (v - NTT(conv)) P^-1 the ModDown output and
+// r = NTT([x_l]_{q_i}) the rescale's correction, NTT linearity gives exactly
+//   (x_i - r_i) q_l^-1 = (add_i + v_i P^-1 - NTT(z_i)) q_l^-1,   z_i = conv_i P^-1 + [x_l]_{q_i},
+// and the last limb x_l itself is formed in the coefficient domain from iNTT(add_l), iNTT(v_l)
+// and conv_l.  Preparation: one thread per coefficient of one polynomial (bk = item * 2 + poly);
+// v_l, the special-prime rows and al (= add_l) are in the coefficient domain; z overwrites conv.
+__global__ void k_mdrs_prep(const u64* __restrict__ v, const u64* __restrict__ al, u64* __restrict__ conv, int B2,
+                            int nl, int rows, int log_n, const ModDownTab* __restrict__ md,
+                            const RescaleTab* __restrict__ rs, const ModConst* __restrict__ mc) {
+    const size_t N = (size_t)1 << log_n;
+    const size_t total = (size_t)B2 * N;
+    const int L = nl - 1;
+    const u64 ql = mc[L].q;
+    const u64 pl = __ldg(&md->pinv[L]), pl_sh = __ldg(&md->pinv_sh[L]);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t x = idx & (N - 1), bk = idx >> log_n;
+        u64* cb = conv + bk * nl * N + x;
+        const u64 vl = v[(bk * rows + L) * N + x];
+        const u64 xl = add_mod(mul_shoup(sub_mod(vl, cb[(size_t)L << log_n], ql), pl, pl_sh, ql), al[idx], ql);
+        const bool neg = xl > (ql >> 1);
+        for (int i = 0; i < L; i++) {
+            const ModConst m = mc[i];
+            u64 r = reduce64(xl, m);
+            if (neg) r = add_mod(r, __ldg(&rs->negq[i]), m.q);
+            const u64 cv = cb[(size_t)i << log_n];
+            cb[(size_t)i << log_n] = add_mod(mul_shoup(cv, __ldg(&md->pinv[i]), __ldg(&md->pinv_sh[i]), m.q), r, m.q);
+        }
+    }
+}
+
+// out[b][k][i] = (add_k,i + v_k,i P^-1 - z_k,i) q_l^-1 for i < l (evaluation domain), 2
+// coefficients per thread; grid-stride over B*2*l*N/2
+__global__ void k_mdrs_combine(const u64* __restrict__ v, const u64* __restrict__ z, int B, int nl, int rows,
+                               int log_n, const ModDownTab* __restrict__ md, const RescaleTab* __restrict__ rs,
+                               const ModConst* __restrict__ mc, const u64* add0, size_t add0_stride,
+                               const u64* add1, size_t add1_stride, u64* out, size_t out_stride) {
+    const size_t N = (size_t)1 << log_n;
+    const int L = nl - 1;
+    const size_t total = (size_t)B * 2 * L * N / 2;
+    for (size_t h = (size_t)blockIdx.x * blockDim.x + threadIdx.x; h < total; h += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = h * 2;
+        const size_t x = idx & (N - 1);
+        const size_t r = idx >> log_n;  // (b*2 + k)*L + i
+        const int i = (int)(r % L);
+        const size_t bk = r / L;
+        const int k = (int)(bk & 1);
+        const size_t b = bk >> 1;
+        const u64 q = mc[i].q;
+        const u64 pinv = __ldg(&md->pinv[i]), pinvsh = __ldg(&md->pinv_sh[i]);
+        const u64 qinv = __ldg(&rs->qinv[i]), qinvsh = __ldg(&rs->qinv_sh[i]);
+        const ulonglong2 vv = ld2(v + (bk * rows + i) * N + x);
+        const ulonglong2 zz = ld2(z + (bk * nl + i) * N + x);
+        const u64* add = k == 0 ? add0 + b * add0_stride : add1 + b * add1_stride;
+        const ulonglong2 aa = ld2(add + ((size_t)i << log_n) + x);
+        const u64 o0 = mul_shoup(sub_mod(add_mod(aa.x, mul_shoup(vv.x, pinv, pinvsh, q), q), zz.x, q), qinv, qinvsh, q);
+        const u64 o1 = mul_shoup(sub_mod(add_mod(aa.y, mul_shoup(vv.y, pinv, pinvsh, q), q), zz.y, q), qinv, qinvsh, q);
+        st2(out + b * out_stride + ((size_t)(k * L + i) << log_n) + x, o0, o1);
+    }
+}
+
 // ---------------------------------------------------------------------------- rescale
 __global__ void k_rescale_prep(const u64* __restrict__ lastc, int Bdeg, int level, int log_n,
                                const RescaleTab* __restrict__ tab, const ModConst* __restrict__ mc,
@@ -1589,6 +1654,24 @@ void op_moddown_combine(lc_ctx* c, const u64* v, const u64* conv, int B, int lev
     const size_t total = (size_t)B * 2 * nl * c->N / 2;
     k_moddown_combine<<<grid_for(total), kT, 0, c->stream>>>(v, conv, B, nl, rows, c->log_n, c->moddown, c->mc, add0,
                                                              add0_stride, add1, add1_stride, w, w_stride);
+    g_lc_launches += 1;
+}
+
+void op_mdrs_prep(lc_ctx* c, const u64* v, const u64* al, u64* conv, int B, int level) {
+    const int nl = level + 1, rows = nl + c->np;
+    const size_t total = (size_t)B * 2 * c->N;
+    k_mdrs_prep<<<grid_for(total), kT, 0, c->stream>>>(v, al, conv, B * 2, nl, rows, c->log_n, c->moddown,
+                                                       c->rescale + level, c->mc);
+    g_lc_launches += 1;
+}
+
+void op_mdrs_combine(lc_ctx* c, const u64* v, const u64* z, int B, int level, const u64* add0, size_t add0_stride,
+                     const u64* add1, size_t add1_stride, u64* out, size_t out_stride) {
+    const int nl = level + 1, rows = nl + c->np;
+    const size_t total = (size_t)B * 2 * level * c->N / 2;
+    k_mdrs_combine<<<grid_for(total), kT, 0, c->stream>>>(v, z, B, nl, rows, c->log_n, c->moddown, c->rescale + level,
+                                                          c->mc, add0, add0_stride, add1, add1_stride, out,
+                                                          out_stride);
     g_lc_launches += 1;
 }
 

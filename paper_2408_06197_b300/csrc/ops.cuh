@@ -18,6 +18,11 @@ void op_mask_acc(lc_ctx* c, const u64* cts, int n, int chunks, int nl, const u64
 //  d: [B] input polys (evaluation domain, nl rows), stride d_stride words
 //  scratch layout is owned by the caller (see capi.cu)
 void op_modup(lc_ctx* c, const u64* coef, size_t coef_stride, int B, int level, u64* ext);
+// fused ModDown + rescale (relinearisation followed by a rescale): preparation in the
+// coefficient domain (z overwrites conv rows i < level) and the evaluation-domain combination
+void op_mdrs_prep(lc_ctx* c, const u64* v, const u64* al, u64* conv, int B, int level);
+void op_mdrs_combine(lc_ctx* c, const u64* v, const u64* z, int B, int level, const u64* add0, size_t add0_stride,
+                     const u64* add1, size_t add1_stride, u64* out, size_t out_stride);
 void op_inner(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level, const u64* key, u64* v);
 // inner products of one hoisted group's T keys (T <= 7), reading the extended digits once:
 // v + t * v_key_stride receives [B][2][rows][N] for key t

@@ -34,6 +34,7 @@ LC_TUNE_GROUP_SPLIT_ITEMS = 3
 LC_TUNE_GROUP_WIDE_ITEMS = 4
 LC_TUNE_TENSOR_WARPS = 5
 LC_TUNE_NTT_ROW_TMA = 6
+LC_PROBE_IMAD, LC_PROBE_IMAD_WIDE, LC_PROBE_NTT_BFLY = 0, 1, 2
 TUNING_OPTIONS = {
     LC_TUNE_NTT_ROW_MINB: (5, 4, 6),
     LC_TUNE_NTT_COL_MINB: (1, 6, 8),
@@ -135,6 +136,7 @@ def lib() -> ctypes.CDLL:
             "lc_copy_async": [vp, vp, vp, ctypes.c_size_t, ctypes.c_int, vp],
             "lc_copy_wait": [vp, ctypes.c_uint64],
             "lc_get_tuning": [vp, u32, vp],
+            "lc_alu_probe": [vp, u32, u32, u32, vp, vp],
             "lc_graph_begin": [vp],
             "lc_graph_end": [vp, vp],
             "lc_graph_launch": [vp, vp],
@@ -362,6 +364,13 @@ class Context:
 
     def tuning(self) -> Dict[str, int]:
         return {TUNING_NAMES[k]: self.get_tuning(k) for k in TUNING_OPTIONS}
+
+    def alu_probe(self, kind: int, iters: int = 4096, blocks_per_sm: int = 8) -> Dict[str, float]:
+        """Register-resident integer-pipe probe (LC_PROBE_*): {"ms", "ops", "ops_per_s"}."""
+        ms, ops = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().lc_alu_probe(self.h, int(kind), int(iters), int(blocks_per_sm), ctypes.byref(ms),
+                                       ctypes.byref(ops)), "lc_alu_probe")
+        return {"ms": ms.value, "ops": ops.value, "ops_per_s": ops.value / (ms.value * 1e-3)}
 
     def sync(self):
         self._check(lib().lc_sync(self.h), "lc_sync")

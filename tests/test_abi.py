@@ -60,6 +60,9 @@ def test_tuning_entry_points_reject_bad_arguments_without_gpu(lib):
     v = ctypes.c_int32()
     assert lib.lc_set_tuning(None, 1, 5) == -1
     assert lib.lc_get_tuning(None, 1, ctypes.byref(v)) == -1
+    lib.lc_alu_probe.argtypes = [ctypes.c_void_p] + [ctypes.c_uint32] * 3 + [ctypes.c_void_p] * 2
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    assert lib.lc_alu_probe(None, 0, 64, 2, ctypes.byref(ms), ctypes.byref(ops)) == -1
 
 
 def test_autotune_candidate_schedules_cover_every_rotation_bit():

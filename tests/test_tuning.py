@@ -68,3 +68,20 @@ def test_autotune_picks_a_loaded_schedule_and_valid_knobs(env):
     for knob, options in LC.TUNING_OPTIONS.items():
         g.set_tuning(knob, options[0])
 
+
+
+def test_alu_probes_count_their_operations_and_reject_bad_arguments(env):
+    """The integer-pipe probes report blocks x 256 threads x iters x 64 operations (32 butterflies
+    per iteration for the butterfly probe), a positive device time, and rates below the issue
+    ceiling of the GPU (148 SMs x 128 thread instructions per clock at most 2.1 GHz)."""
+    LC, g = env.LC, env.g
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ceiling = sms * 128 * 2.1e9
+    for kind, per in ((LC.LC_PROBE_IMAD, 64), (LC.LC_PROBE_IMAD_WIDE, 64), (LC.LC_PROBE_NTT_BFLY, 32)):
+        r = g.alu_probe(kind, iters=64, blocks_per_sm=2)
+        assert r["ops"] == sms * 2 * 256 * 64 * per
+        assert r["ms"] > 0 and r["ops_per_s"] < ceiling
+    for bad in ((3, 64, 2), (0, 0, 2), (0, 64, 0), (0, 64, 33)):
+        with pytest.raises(LC.LancelotError):
+            g.alu_probe(*bad)
+    g.sync()
