@@ -135,8 +135,8 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  * the GPU).  Every option computes identical results; only speed differs.  Unknown knobs or
  * options fail with LC_EINVAL and leave the setting unchanged.  Options (default first):
  *   LC_TUNE_NTT_ROW_MINB       row pass of the NTT: minimum resident 128-thread blocks, i.e. a
- *                              register cap: 5, 4, 6
- *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 1 (no cap), 6, 8
+ *                              register cap: 4, 5, 6
+ *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 8, 1 (no cap), 6
  *   LC_TUNE_GROUP_SPLIT_ITEMS  one-ModDown group kernel, rows with primes below 2^40: items per
  *                              thread, 1 or 2
  *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 2 or 1
@@ -167,6 +167,15 @@ int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
 #define LC_PROBE_IMAD_WIDE 1
 #define LC_PROBE_NTT_BFLY 2
 int lc_alu_probe(lc_ctx* ctx, uint32_t kind, uint32_t iters, uint32_t blocks_per_sm, double* ms, double* ops);
+
+/* Self-test of the bounded device waits (no counterpart in the paper).  Kernels that stream tiles
+ * with bulk copies wait on shared-memory barriers for at most a fixed number of polls; a wait that
+ * runs out sets the context's device error word, which the next lc_sync reports as LC_ETIMEOUT
+ * (and clears).  This call runs one block that copies 64 bytes through such a barrier and checks
+ * them, then, if never_arrive != 0, waits at most max_polls polls on a barrier at which nothing
+ * ever arrives.  Synchronous.  Returns LC_OK when the copy arrived intact and no wait ran out,
+ * LC_ETIMEOUT when a wait ran out (the context stays usable), LC_EINVAL for max_polls == 0. */
+int lc_wait_selftest(lc_ctx* ctx, int never_arrive, uint32_t max_polls);
 
 /* CUDA-graph capture of a sequence of calls on the context's stream (no counterpart in the
  * paper; replaces per-call kernel launches with one graph launch).  Between lc_graph_begin and

@@ -1554,6 +1554,28 @@ int lc_alu_probe(lc_ctx* c, uint32_t kind, uint32_t iters, uint32_t blocks_per_s
     return check_launch(c, "lc_alu_probe");
 }
 
+int lc_wait_selftest(lc_ctx* c, int never_arrive, uint32_t max_polls) {
+    clear_prior_error();
+    if (!c || max_polls == 0) return fail(c, LC_EINVAL, "lc_wait_selftest: bad argument");
+    auto* buf = static_cast<unsigned long long*>(lc_dev_alloc(c, 128));
+    if (!buf) return fail(c, LC_ENOMEM, "lc_wait_selftest: allocation failed");
+    unsigned long long pattern[8], back[8] = {};
+    for (int i = 0; i < 8; i++) pattern[i] = 0x9e3779b97f4a7c15ull * (unsigned long long)(i + 1);
+    cudaError_t e = cudaMemcpyAsync(buf, pattern, sizeof(pattern), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf + 8, 0, 64, c->stream);
+    if (e == cudaSuccess) {
+        wait_selftest(buf, buf + 8, never_arrive, max_polls, c->dev_err, c->stream);
+        g_lc_launches += 1;
+        e = cudaMemcpyAsync(back, buf + 8, sizeof(back), cudaMemcpyDeviceToHost, c->stream);
+    }
+    const int st = e == cudaSuccess ? lc_sync(c) : fail(c, LC_ECUDA, cudaGetErrorString(e));
+    lc_dev_free(c, buf);
+    if (st) return st;
+    if (std::memcmp(back, pattern, sizeof(back)) != 0)
+        return fail(c, LC_ECUDA, "lc_wait_selftest: the bulk copy delivered wrong bytes");
+    return LC_OK;
+}
+
 int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                  uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale) {
     clear_prior_error();

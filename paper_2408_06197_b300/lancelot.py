@@ -36,8 +36,8 @@ LC_TUNE_TENSOR_WARPS = 5
 LC_TUNE_NTT_ROW_TMA = 6
 LC_PROBE_IMAD, LC_PROBE_IMAD_WIDE, LC_PROBE_NTT_BFLY = 0, 1, 2
 TUNING_OPTIONS = {
-    LC_TUNE_NTT_ROW_MINB: (5, 4, 6),
-    LC_TUNE_NTT_COL_MINB: (1, 6, 8),
+    LC_TUNE_NTT_ROW_MINB: (4, 5, 6),
+    LC_TUNE_NTT_COL_MINB: (8, 1, 6),
     LC_TUNE_GROUP_SPLIT_ITEMS: (1, 2),
     LC_TUNE_GROUP_WIDE_ITEMS: (2, 1),
     LC_TUNE_TENSOR_WARPS: (16, 8, 12),
@@ -137,6 +137,7 @@ def lib() -> ctypes.CDLL:
             "lc_copy_wait": [vp, ctypes.c_uint64],
             "lc_get_tuning": [vp, u32, vp],
             "lc_alu_probe": [vp, u32, u32, u32, vp, vp],
+            "lc_wait_selftest": [vp, ctypes.c_int, u32],
             "lc_graph_begin": [vp],
             "lc_graph_end": [vp, vp],
             "lc_graph_launch": [vp, vp],
@@ -371,6 +372,10 @@ class Context:
         self._check(lib().lc_alu_probe(self.h, int(kind), int(iters), int(blocks_per_sm), ctypes.byref(ms),
                                        ctypes.byref(ops)), "lc_alu_probe")
         return {"ms": ms.value, "ops": ops.value, "ops_per_s": ops.value / (ms.value * 1e-3)}
+
+    def wait_selftest(self, never_arrive: bool = False, max_polls: int = 1 << 16) -> int:
+        """Bounded-wait self-test: LC_OK, or -6 (LC_ETIMEOUT) when a wait ran out (no exception)."""
+        return int(lib().lc_wait_selftest(self.h, int(bool(never_arrive)), int(max_polls)))
 
     def sync(self):
         self._check(lib().lc_sync(self.h), "lc_sync")

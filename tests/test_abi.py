@@ -63,6 +63,8 @@ def test_tuning_entry_points_reject_bad_arguments_without_gpu(lib):
     lib.lc_alu_probe.argtypes = [ctypes.c_void_p] + [ctypes.c_uint32] * 3 + [ctypes.c_void_p] * 2
     ms, ops = ctypes.c_double(), ctypes.c_double()
     assert lib.lc_alu_probe(None, 0, 64, 2, ctypes.byref(ms), ctypes.byref(ops)) == -1
+    lib.lc_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]
+    assert lib.lc_wait_selftest(None, 0, 16) == -1
 
 
 def test_autotune_candidate_schedules_cover_every_rotation_bit():

@@ -85,3 +85,18 @@ def test_alu_probes_count_their_operations_and_reject_bad_arguments(env):
         with pytest.raises(LC.LancelotError):
             g.alu_probe(*bad)
     g.sync()
+
+
+def test_bounded_wait_runs_out_and_is_reported(env):
+    """The bounded shared-memory-barrier wait of the bulk-copy kernels: a wait that completes
+    returns LC_OK with the copied bytes intact; a wait on a barrier at which nothing arrives runs
+    out after its poll limit and the next sync reports LC_ETIMEOUT (-6); the context stays usable
+    and the error word is cleared."""
+    LC, g = env.LC, env.g
+    assert g.wait_selftest(never_arrive=False) == 0
+    assert g.wait_selftest(never_arrive=True, max_polls=1 << 12) == -6
+    assert g.wait_selftest(never_arrive=False) == 0
+    a = np.stack([np.random.default_rng(3).integers(0, q, size=env.N, dtype=np.uint64) for q in env.prm.q])
+    ev = g.to_eval(LC.u64_to_torch(a), env.L)
+    assert np.array_equal(LC.torch_to_u64(g.to_coeff(ev, env.L)), a)
+    g.sync()
