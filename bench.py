@@ -746,35 +746,53 @@ def main():
         value = whole_job_rate(w.n_pairs, world, args.steps, ms / 1e3)
 
         # end-to-end through the C ABI: every step copies its inputs in from pinned host memory and
-        # its results out.  Serial form: copy in, compute, copy out.  Pipelined form (reported as
-        # e2e): double-buffered device inputs/outputs, the next step's inputs copied in and the
-        # previous step's results copied out on the context's copy streams while this step
+        # its results out, in the wire form (lc_pack / lc_unpack: residues of 40-bit primes in 5
+        # bytes, 78 instead of 120 bytes per coefficient at level 14), unpacked and packed on the
+        # device inside the step.  Serial form: copy in, compute, copy out.  Pipelined form
+        # (reported as e2e): double-buffered device buffers, the next step's inputs copied in and
+        # the previous step's results copied out on the context's copy streams while this step
         # computes (lc_copy_async / lc_copy_wait).
         e2e = e2e_serial = None
         if not args.no_e2e:
-            h_cts = LC.pinned_empty(tuple(cts.shape))
-            h_masks = LC.pinned_empty(tuple(masks.shape))
-            h_out_d = LC.pinned_empty(tuple(out_d.shape))
-            h_out_a = LC.pinned_empty(tuple(out_a.shape))
-            h_cts[...] = LC.torch_to_u64(cts)
-            h_masks[...] = LC.torch_to_u64(masks)
-            bufs = [(torch.empty_like(cts), torch.empty_like(masks), torch.empty_like(out_d), torch.empty_like(out_a))
-                    for _ in range(2)]
+            L = g.L
+            nct, nmk = w.n_clients * w.chunks, w.n_clients
+            wb_in, wb_out = g.wire_bytes(2, L), g.wire_bytes(2, L - 1)
+            h_cts = LC.pinned_empty((nct, wb_in), np.uint8)
+            h_masks = LC.pinned_empty((nmk, wb_in), np.uint8)
+            h_out_d = LC.pinned_empty((w.n_pairs, wb_out), np.uint8)
+            h_out_a = LC.pinned_empty((w.chunks, wb_out), np.uint8)
+            wc, wm = g.pack(cts.view(nct, 2, g.nq, g.N), 2, L), g.pack(masks, 2, L)
+            g.sync()
+            h_cts[...] = wc.cpu().numpy()
+            h_masks[...] = wm.cpu().numpy()
+            del wc, wm
+            torch.cuda.synchronize()
+
+            def wire_set():
+                u8 = dict(dtype=torch.uint8, device=cts.device)
+                return (torch.empty((nct, wb_in), **u8), torch.empty((nmk, wb_in), **u8),
+                        torch.empty((w.n_pairs, wb_out), **u8), torch.empty((w.chunks, wb_out), **u8))
+            bufs = [wire_set() for _ in range(2)]
+            d_cts, d_masks = torch.empty_like(cts), torch.empty_like(masks)
             h2d_bytes = int(h_cts.nbytes + h_masks.nbytes)
             d2h_bytes = int(h_out_d.nbytes + h_out_a.nbytes)
 
             def compute(b):
-                d_cts, d_masks, o_d, o_a = b
-                g.distances(evk, d_cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=o_d)
-                g.masked_aggregate(evk, d_cts, w.n_clients, w.chunks, g.scale, d_masks, g.scale, mode=mode, out=o_a)
+                w_cts, w_masks, w_d, w_a = b
+                g.unpack(w_cts, nct, 2, L, out=d_cts)
+                g.unpack(w_masks, nmk, 2, L, out=d_masks)
+                g.distances(evk, d_cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d)
+                g.masked_aggregate(evk, d_cts, w.n_clients, w.chunks, g.scale, d_masks, g.scale, mode=mode, out=out_a)
+                g.pack(out_d, 2, L - 1, out=w_d)
+                g.pack(out_a, 2, L - 1, out=w_a)
 
             def serial_step():
-                d_cts, d_masks, o_d, o_a = bufs[0]
-                g.h2d(d_cts, h_cts)
-                g.h2d(d_masks, h_masks)
+                w_cts, w_masks, w_d, w_a = bufs[0]
+                g.h2d(w_cts, h_cts)
+                g.h2d(w_masks, h_masks)
                 compute(bufs[0])
-                g.d2h(h_out_d, o_d)
-                g.d2h(h_out_a, o_a)
+                g.d2h(h_out_d, w_d)
+                g.d2h(h_out_a, w_a)
                 g.sync()
 
             def pipelined(steps):
@@ -808,9 +826,33 @@ def main():
             el = timed(lambda: pipelined(args.steps))
             e2e = {"value": whole_job_rate(w.n_pairs, world, args.steps, el), "unit": UNIT,
                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
-                   "form": "double-buffered: next step's H2D and previous step's D2H overlap this step's compute",
+                   "form": "wire form (lc_pack/lc_unpack on the device); double-buffered: next step's H2D and "
+                           "previous step's D2H overlap this step's compute",
                    "serial": e2e_serial}
-            del bufs
+            del bufs, d_cts, d_masks
+
+    # the two halves of a step timed alone (device time, CUDA events): distances and the masked
+    # aggregate (chunks/s beside the pair metric)
+    parts = None
+    if args.mode == "batched":
+        with torch.cuda.stream(stream):
+            def tm(fn, reps=3):
+                fn()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / reps
+            dms = tm(lambda: g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched,
+                                         out=out_d))
+            ams = tm(lambda: g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, mode=mode,
+                                                out=out_a))
+        parts = {"distances_ms": dms, "pairs_per_s": w.n_pairs / (dms / 1e3), "aggregate_ms": ams,
+                 "aggregate_chunks_per_s": w.chunks / (ams / 1e3), "launch": "eager"}
 
     # the clients' step on the device: GPU encode + encryption with device randomness of all
     # n x chunks update chunks (beside the server metric; not part of a step)
@@ -897,7 +939,7 @@ def main():
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (4.8 GB client ciphertexts resident)"},
             "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e, "plain_form": plain,
-            "client_step": client,
+            "client_step": client, "step_parts": parts,
             "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                  "definition": "one round = 45 pair distances + masked aggregate of 64 chunks, "
                                                "device time per step (rank 0)"}}

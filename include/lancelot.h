@@ -168,6 +168,20 @@ int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
 #define LC_PROBE_NTT_BFLY 2
 int lc_alu_probe(lc_ctx* ctx, uint32_t kind, uint32_t iters, uint32_t blocks_per_sm, double* ms, double* ops);
 
+/* Wire form of ciphertext arrays (no counterpart in the paper; a transfer format).  A record of
+ * deg polynomials at `level` stores, polynomial after polynomial and limb after limb, the N
+ * residues of limb i (canonical, below q_i) in w_i = ceil(bits(q_i - 1) / 8) little-endian bytes
+ * each (4 <= w_i <= 8): a production ciphertext at level 14 takes 78 bytes per coefficient
+ * instead of 120.  lc_wire_bytes gives the bytes of one record.  lc_pack / lc_unpack convert
+ * `count` records between the word layout [count][deg][level+1][N] and the wire form, both on
+ * the device (16-byte aligned device buffers; host buffers are LC_EINVAL -- copy with
+ * lc_copy_async first).  Asynchronous on the context's stream.  lc_unpack checks every residue:
+ * one that is not below its prime makes the next lc_sync return LC_EINVAL (the words written
+ * for it are unspecified). */
+int lc_wire_bytes(lc_ctx* ctx, uint32_t deg, uint32_t level, uint64_t* bytes);
+int lc_pack(lc_ctx* ctx, const uint64_t* in, uint32_t count, uint32_t deg, uint32_t level, uint8_t* out);
+int lc_unpack(lc_ctx* ctx, const uint8_t* in, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out);
+
 /* Self-test of the bounded device waits (no counterpart in the paper).  Kernels that stream tiles
  * with bulk copies wait on shared-memory barriers for at most a fixed number of polls; a wait that
  * runs out sets the context's device error word, which the next lc_sync reports as LC_ETIMEOUT

@@ -15,6 +15,8 @@
 #include "host_math.hpp"
 #include "ops.cuh"
 #include "probe.cuh"
+#include "tma.cuh"
+#include "wire.cuh"
 
 using lc::hinv;
 using lc::hmul;
@@ -726,7 +728,9 @@ int lc_sync(lc_ctx* c) {
     LC_CUDA(c, cudaMemcpy(&err, c->dev_err, 4, cudaMemcpyDeviceToHost));
     if (err) {
         LC_CUDA(c, cudaMemset(c->dev_err, 0, 4));
-        return fail(c, LC_ETIMEOUT, "a bounded wait on the device gave up (code " + std::to_string(err) + ")");
+        if (err & LC_ERR_TIMEOUT)
+            return fail(c, LC_ETIMEOUT, "a bounded wait on the device gave up (code " + std::to_string(err) + ")");
+        return fail(c, LC_EINVAL, "a wire-form residue was not below its prime (lc_unpack)");
     }
     return check_launch(c, "deferred");
 }
@@ -1527,11 +1531,18 @@ int lc_alu_probe(lc_ctx* c, uint32_t kind, uint32_t iters, uint32_t blocks_per_s
     int sms = 0;
     LC_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int blocks = sms * (int)blocks_per_sm;
-    auto* sink = static_cast<unsigned long long*>(lc_dev_alloc(c, sizeof(unsigned long long)));
-    if (!sink) return fail(c, LC_ENOMEM, "lc_alu_probe: allocation failed");
     cudaEvent_t e0, e1;
     LC_CUDA(c, cudaEventCreate(&e0));
-    LC_CUDA(c, cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, LC_ECUDA, "lc_alu_probe: event creation failed");
+    }
+    auto* sink = static_cast<unsigned long long*>(lc_dev_alloc(c, sizeof(unsigned long long)));
+    if (!sink) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(c, LC_ENOMEM, "lc_alu_probe: allocation failed");
+    }
     auto launch = [&] {
         if (kind == LC_PROBE_IMAD) probe_imad(blocks, iters, sink, c->stream);
         else if (kind == LC_PROBE_IMAD_WIDE) probe_imad_wide(blocks, iters, sink, c->stream);
@@ -1552,6 +1563,53 @@ int lc_alu_probe(lc_ctx* c, uint32_t kind, uint32_t iters, uint32_t blocks_per_s
     *ms = t;
     *ops = (double)blocks * kProbeThreads * iters * (kind == LC_PROBE_NTT_BFLY ? 32.0 : 64.0);
     return check_launch(c, "lc_alu_probe");
+}
+
+static bool wire_map(lc_ctx* c, uint32_t deg, uint32_t level, WireMap& m) {
+    if (deg < 1 || deg > 3 || (int)level >= c->nq || level + 1 > LC_WIRE_MAX_LIMBS || c->log_n < 4) return false;
+    m = WireMap{};
+    m.log_n = c->log_n;
+    m.nl = (int)level + 1;
+    size_t off = 0;
+    for (int i = 0; i < m.nl; i++) {
+        int bits = 0;
+        for (u64 v = c->mod[i] - 1; v; v >>= 1) bits++;
+        m.w[i] = std::min(8, std::max(4, (bits + 7) / 8));
+        m.off[i] = off;
+        m.q[i] = c->mod[i];
+        off += (size_t)c->N * m.w[i];
+    }
+    m.poly_bytes = off;
+    return true;
+}
+
+int lc_wire_bytes(lc_ctx* c, uint32_t deg, uint32_t level, uint64_t* bytes) {
+    WireMap m;
+    if (!c || !bytes || !wire_map(c, deg, level, m)) return fail(c, LC_EINVAL, "lc_wire_bytes: bad argument");
+    *bytes = (uint64_t)m.poly_bytes * deg;
+    return LC_OK;
+}
+
+int lc_pack(lc_ctx* c, const uint64_t* in, uint32_t count, uint32_t deg, uint32_t level, uint8_t* out) {
+    clear_prior_error();
+    WireMap m;
+    if (!c || !in || !out || !wire_map(c, deg, level, m) || is_host_ptr(in) || is_host_ptr(out) ||
+        (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16)
+        return fail(c, LC_EINVAL, "lc_pack: bad argument (device buffers, 16-byte aligned)");
+    wire_pack(in, out, (size_t)count * deg, m, c->stream);
+    g_lc_launches += count ? 1 : 0;
+    return check_launch(c, "lc_pack");
+}
+
+int lc_unpack(lc_ctx* c, const uint8_t* in, uint32_t count, uint32_t deg, uint32_t level, uint64_t* out) {
+    clear_prior_error();
+    WireMap m;
+    if (!c || !in || !out || !wire_map(c, deg, level, m) || is_host_ptr(in) || is_host_ptr(out) ||
+        (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16)
+        return fail(c, LC_EINVAL, "lc_unpack: bad argument (device buffers, 16-byte aligned)");
+    wire_unpack(in, out, (size_t)count * deg, m, c->dev_err, c->stream);
+    g_lc_launches += count ? 1 : 0;
+    return check_launch(c, "lc_unpack");
 }
 
 int lc_wait_selftest(lc_ctx* c, int never_arrive, uint32_t max_polls) {

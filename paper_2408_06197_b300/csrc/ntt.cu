@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <utility>
 #include "ntt.cuh"
 #include "context.cuh"
 #include "tma.cuh"
@@ -454,23 +455,26 @@ void probe_ntt_bfly(int blocks, uint32_t iters, unsigned long long* sink, cudaSt
     ntt_bfly_probe<<<blocks, kProbeThreads, 0, s>>>(q, w, w_sh, iters, sink);
 }
 
-// persistent grid of a row-pass kernel: resident blocks per SM x SMs (queried once per kernel)
+// persistent grid of a row-pass kernel: resident blocks per SM x SMs (queried once per kernel
+// and device)
 template <typename K>
 static int persistent_grid(K kernel, int total) {
     static std::mutex mu;
-    static std::map<const void*, int> cache;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(reinterpret_cast<const void*>(kernel));
+    auto it = cache.find(key);
     int cap;
     if (it != cache.end()) {
         cap = it->second;
     } else {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
+        int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kRowThreads, 0);
         cap = std::max(1, sms * std::max(1, per));
-        cache[reinterpret_cast<const void*>(kernel)] = cap;
+        cache[key] = cap;
     }
     return std::min(total, cap);
 }

@@ -7,7 +7,9 @@
 #pragma once
 #include <cstdint>
 
+// bits of the context's device error word (reported by lc_sync)
 #define LC_ERR_TIMEOUT 1u   // a bounded wait on a shared-memory barrier gave up
+#define LC_ERR_RANGE 2u     // a wire-form residue was not below its prime
 constexpr unsigned kMbarPolls = 1u << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -138,6 +138,9 @@ def lib() -> ctypes.CDLL:
             "lc_get_tuning": [vp, u32, vp],
             "lc_alu_probe": [vp, u32, u32, u32, vp, vp],
             "lc_wait_selftest": [vp, ctypes.c_int, u32],
+            "lc_wire_bytes": [vp, u32, u32, vp],
+            "lc_pack": [vp, vp, u32, u32, u32, vp],
+            "lc_unpack": [vp, vp, u32, u32, u32, vp],
             "lc_graph_begin": [vp],
             "lc_graph_end": [vp, vp],
             "lc_graph_launch": [vp, vp],
@@ -373,6 +376,38 @@ class Context:
                                        ctypes.byref(ops)), "lc_alu_probe")
         return {"ms": ms.value, "ops": ops.value, "ops_per_s": ops.value / (ms.value * 1e-3)}
 
+    # ------------------------------------------------------------------ wire form
+    def wire_bytes(self, deg: int, level: int) -> int:
+        """Bytes of one wire-form record of `deg` polynomials at `level` (lc_wire_bytes)."""
+        v = ctypes.c_uint64()
+        self._check(lib().lc_wire_bytes(self.h, int(deg), int(level), ctypes.byref(v)), "lc_wire_bytes")
+        return int(v.value)
+
+    def pack(self, data: torch.Tensor, deg: int, level: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Word layout [count][deg][level+1][N] -> wire form (uint8 CUDA tensor [count][bytes])."""
+        count = _whole(data, deg * (level + 1) * self.N, "pack")
+        _need(data, count * deg * (level + 1) * self.N, "pack")
+        rb = self.wire_bytes(deg, level)
+        if out is None:
+            out = torch.empty((count, rb), dtype=torch.uint8, device=data.device)
+        if out.dtype != torch.uint8 or not out.is_cuda or not out.is_contiguous() or out.numel() < count * rb:
+            raise LancelotError("pack: out must be a contiguous uint8 CUDA tensor of count x wire_bytes")
+        self._check(lib().lc_pack(self.h, _t_ptr(data), count, int(deg), int(level), _t_ptr(out)), "lc_pack")
+        return out
+
+    def unpack(self, wire: torch.Tensor, count: int, deg: int, level: int,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Wire form -> word layout [count][deg][level+1][N]; a residue not below its prime makes
+        the next sync raise (LC_EINVAL)."""
+        rb = self.wire_bytes(deg, level)
+        if wire.dtype != torch.uint8 or not wire.is_cuda or not wire.is_contiguous() or wire.numel() < count * rb:
+            raise LancelotError("unpack: wire must be a contiguous uint8 CUDA tensor of count x wire_bytes")
+        if out is None:
+            out = self.empty(count, deg, level + 1, self.N)
+        _need(out, count * deg * (level + 1) * self.N, "unpack: out")
+        self._check(lib().lc_unpack(self.h, _t_ptr(wire), int(count), int(deg), int(level), _t_ptr(out)), "lc_unpack")
+        return out
+
     def wait_selftest(self, never_arrive: bool = False, max_polls: int = 1 << 16) -> int:
         """Bounded-wait self-test: LC_OK, or -6 (LC_ETIMEOUT) when a wait ran out (no exception)."""
         return int(lib().lc_wait_selftest(self.h, int(bool(never_arrive)), int(max_polls)))
@@ -417,11 +452,17 @@ class Context:
         """Overlapped copy between a device tensor and a pinned host array (either direction),
         ordered after the work enqueued so far; returns a ticket for copy_wait."""
         t = ctypes.c_uint64()
+
+        def dev_ok(x, nbytes):
+            return (x.is_cuda and x.is_contiguous() and x.dtype in (torch.int64, torch.uint64, torch.uint8)
+                    and x.numel() * x.element_size() >= nbytes)
         if isinstance(dst, torch.Tensor) and isinstance(src, np.ndarray):
-            _need(dst, src.size, "copy_async: dst")
+            if not dev_ok(dst, src.nbytes):
+                raise LancelotError("copy_async: dst must be a contiguous 64-bit or byte CUDA tensor of src's size")
             args = (_t_ptr(dst), _np_ptr(src), src.nbytes, LC_H2D)
         elif isinstance(dst, np.ndarray) and isinstance(src, torch.Tensor):
-            _need(src, dst.size, "copy_async: src")
+            if not dev_ok(src, dst.nbytes):
+                raise LancelotError("copy_async: src must be a contiguous 64-bit or byte CUDA tensor of dst's size")
             args = (_np_ptr(dst), _t_ptr(src), dst.nbytes, LC_D2H)
         else:
             raise LancelotError("copy_async: one side must be a device tensor and the other a host array")

@@ -65,6 +65,9 @@ def test_tuning_entry_points_reject_bad_arguments_without_gpu(lib):
     assert lib.lc_alu_probe(None, 0, 64, 2, ctypes.byref(ms), ctypes.byref(ops)) == -1
     lib.lc_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32]
     assert lib.lc_wait_selftest(None, 0, 16) == -1
+    lib.lc_wire_bytes.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
+    nb = ctypes.c_uint64()
+    assert lib.lc_wire_bytes(None, 2, 0, ctypes.byref(nb)) == -1
 
 
 def test_autotune_candidate_schedules_cover_every_rotation_bit():
