@@ -320,52 +320,66 @@ __global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(cons
         ob[t] = (pk[t] & 15) * 2 * kTX + x;
     }
     const u64* shf = &sh[0][0][0][0];
-    // one barrier per group of CPS chunks: the copies of group g + RS - 1 overlap groups g..
-    for (int gi = 0; gi < groups; gi++) {
-        cp_async_wait<RS - 2>();
-        __syncthreads();
-        {
-            const int ng = gi + RS - 1;
+    const u64* pa[PPT];
+    const u64* pb[PPT];
 #pragma unroll
-            for (int c = 0; c < CPS; c++)
+    for (int t = 0; t < PPT; t++) {
+        pa[t] = shf + oa[t];
+        pb[t] = shf + ob[t];
+    }
+    // one barrier per group of CPS chunks: the copies of group g + RS - 1 overlap groups g..;
+    // the ring slot is a compile-time index (the loop over slots is unrolled), so every
+    // shared-memory load is [pair base + constant]
+    for (int g0 = 0; g0 < groups; g0 += RS) {
 #pragma unroll
-                for (int h = 0; h < UPT; h++)
-                    if (ucopy[h] && ng * CPS + c < chunks)
-                        cp_async16(&sh[(ng % RS) * CPS + c][ucs[h]][upp[h]][uxx[h]],
-                                   gsrc[h] + (size_t)(ng * CPS + c) * chunk_stride);
-            cp_async_commit();
-        }
+        for (int rs = 0; rs < RS; rs++) {
+            const int gi = g0 + rs;
+            if (gi >= groups) break;
+            cp_async_wait<RS - 2>();
+            __syncthreads();
+            {
+                const int ng = gi + RS - 1;
 #pragma unroll
-        for (int c = 0; c < CPS; c++) {
-        const int k = gi * CPS + c;
-        if (k >= chunks) break;
-        const u64* st = shf + ((gi % RS) * CPS + c) * STAGE;
+                for (int c = 0; c < CPS; c++)
 #pragma unroll
-        for (int t = 0; t < PPT; t++) {
-            if (pk[t] < 0) continue;
-            const u64 a0 = st[oa[t]], a1 = st[oa[t] + kTX];
-            const u64 b0 = st[ob[t]], b1 = st[ob[t] + kTX];
-            if (SPLIT) {
-                // a + q - b in [1, 2q): congruent to the difference, halves below 2^21, so every
-                // partial product stays below 2^42 and < 2^20 chunks cannot overflow
-                const u64 d0 = a0 + m.q - b0, d1 = a1 + m.q - b1;
-                const unsigned h0 = (unsigned)(d0 >> 20), l0 = (unsigned)d0 & 0xFFFFFu;
-                const unsigned h1 = (unsigned)(d1 >> 20), l1 = (unsigned)d1 & 0xFFFFFu;
-                sq_split_w(t00[t], h0, l0);
-                mac_split_w(t01[t], h0, l0, h1, l1);
-                sq_split_w(t11[t], h1, l1);
-            } else {
-                const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
-                mac128(s00[t], d0, d0);
-                mac128(s01[t], d0, d1);
-                mac128(s11[t], d1, d1);
-                if ((k & 7) == 7) {
-                    fold(s00[t], m);
-                    fold(s01[t], m);
-                    fold(s11[t], m);
+                    for (int h = 0; h < UPT; h++)
+                        if (ucopy[h] && ng * CPS + c < chunks)
+                            cp_async16(&sh[((rs + RS - 1) % RS) * CPS + c][ucs[h]][upp[h]][uxx[h]],
+                                       gsrc[h] + (size_t)(ng * CPS + c) * chunk_stride);
+                cp_async_commit();
+            }
+#pragma unroll
+            for (int c = 0; c < CPS; c++) {
+                const int k = gi * CPS + c;
+                if (k >= chunks) break;
+                const int so = (rs * CPS + c) * STAGE;
+#pragma unroll
+                for (int t = 0; t < PPT; t++) {
+                    if (pk[t] < 0) continue;
+                    const u64 a0 = pa[t][so], a1 = pa[t][so + kTX];
+                    const u64 b0 = pb[t][so], b1 = pb[t][so + kTX];
+                    if (SPLIT) {
+                        // a + q - b in [1, 2q): congruent to the difference, halves below 2^21, so
+                        // every partial product stays below 2^42 and < 2^20 chunks cannot overflow
+                        const u64 d0 = a0 + m.q - b0, d1 = a1 + m.q - b1;
+                        const unsigned h0 = (unsigned)(d0 >> 20), l0 = (unsigned)d0 & 0xFFFFFu;
+                        const unsigned h1 = (unsigned)(d1 >> 20), l1 = (unsigned)d1 & 0xFFFFFu;
+                        sq_split_w(t00[t], h0, l0);
+                        mac_split_w(t01[t], h0, l0, h1, l1);
+                        sq_split_w(t11[t], h1, l1);
+                    } else {
+                        const u64 d0 = sub_mod(a0, b0, m.q), d1 = sub_mod(a1, b1, m.q);
+                        mac128(s00[t], d0, d0);
+                        mac128(s01[t], d0, d1);
+                        mac128(s11[t], d1, d1);
+                        if ((k & 7) == 7) {
+                            fold(s00[t], m);
+                            fold(s01[t], m);
+                            fold(s11[t], m);
+                        }
+                    }
                 }
             }
-        }
         }
     }
     cp_async_wait<0>();
