@@ -261,9 +261,10 @@ __device__ __forceinline__ void fwd_row_body(const u64* in, u64* a, u64* s, cons
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kRowThreads, MINB) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+template <int LOGN, int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) ntt_fwd_row(u64* base, size_t batch_stride, RowMap map,
                                                               NttTables tb) {
+    constexpr int log_n = LOGN;
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
     int mi;
@@ -378,9 +379,10 @@ __device__ __forceinline__ void inv_row_body(u64* a, u64* s, const ModConst& mc,
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = x[u];
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size_t batch_stride, RowMap map, int log_n,
+template <int LOGN, int MINB>
+__global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size_t batch_stride, RowMap map,
                                                               NttTables tb) {
+    constexpr int log_n = LOGN;
     constexpr int E = 8 * 256;
     __shared__ u64 s[E];
     int mi;
@@ -412,12 +414,21 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size
         case 8: LC_COL_C(KERNEL, 8, C_, GRID, S_) break;        \
         default: LC_COL_C(KERNEL, 1, C_, GRID, S_) break;       \
     }
-// row pass: MINB 4, 5 or 6
-#define LC_ROW_DISPATCH(KERNEL, MINB_, GRID, S_)                                                              \
-    switch (MINB_) {                                                                                          \
-        case 4: KERNEL<4><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;           \
-        case 6: KERNEL<6><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;           \
-        default: KERNEL<5><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, log_n, tb); break;          \
+// row pass: log_n in [12, 16] (a compile-time ring degree), MINB 4, 5 or 6
+#define LC_ROW_N(KERNEL, MB, LOGN_, GRID, S_)                                                      \
+    switch (LOGN_) {                                                                               \
+        case 12: KERNEL<12, MB><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, tb); break; \
+        case 13: KERNEL<13, MB><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, tb); break; \
+        case 14: KERNEL<14, MB><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, tb); break; \
+        case 15: KERNEL<15, MB><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, tb); break; \
+        case 16: KERNEL<16, MB><<<GRID, kRowThreads, 0, S_>>>(base, batch_stride, map, tb); break; \
+        default: break;                                                                            \
+    }
+#define LC_ROW_DISPATCH(KERNEL, MINB_, GRID, S_)                   \
+    switch (MINB_) {                                               \
+        case 4: LC_ROW_N(KERNEL, 4, log_n, GRID, S_) break;        \
+        case 6: LC_ROW_N(KERNEL, 6, log_n, GRID, S_) break;        \
+        default: LC_ROW_N(KERNEL, 5, log_n, GRID, S_) break;       \
     }
 
 // Register-resident copy of the forward butterfly network: radix-16 blocks of the lazy
