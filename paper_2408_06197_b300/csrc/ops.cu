@@ -211,7 +211,7 @@ __device__ __forceinline__ u64 acc3_reduce(const Acc3& s, int bshift, const ModC
 // WARPS warps, PPT pair slots per thread; SPLIT: the limbs' primes are below 2^40 (20-bit split
 // arithmetic), else 128-bit multiply-accumulate with a fold every 8 chunks.  Limb = limb0 + z.
 template <int WARPS, int PPT, bool SPLIT>
-__global__ void __launch_bounds__(WARPS * 32, SPLIT ? 1 : 2) k_sq_acc_tiled(const u64* __restrict__ cts, int n, int chunks,
+__global__ void __launch_bounds__(WARPS * 32, (SPLIT || WARPS > 8) ? 1 : 2) k_sq_acc_tiled(const u64* __restrict__ cts, int n, int chunks,
                                                                 int nl, int limb0, int log_n, int cb, int p0, int np,
                                                                 const ModConst* __restrict__ mc,
                                                                 u64* __restrict__ out) {
@@ -1453,9 +1453,9 @@ void op_sq_acc_tiled(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     if (chunks > (1 << 20)) split0 = nl;
     if (split0 > 0) {
         dim3 grid(nb * (nb + 1) / 2, (unsigned)(c->N / kTX), split0);
-        tensor_smem_attr(k_sq_acc_tiled<8, 8, false>);
-        k_sq_acc_tiled<8, 8, false><<<grid, 256, kTensorSmem, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, cb, p0, np,
-                                                                            c->mc, out);
+        tensor_smem_attr(k_sq_acc_tiled<16, 4, false>);
+        k_sq_acc_tiled<16, 4, false><<<grid, 512, kTensorSmem, c->stream>>>(cts, n, chunks, nl, 0, c->log_n, cb, p0,
+                                                                             np, c->mc, out);
         g_lc_launches += 1;
     }
     if (split0 < nl) {  // warps per block: LC_TUNE_TENSOR_WARPS (pair slots per thread = 64 / warps, rounded up)
