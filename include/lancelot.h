@@ -136,7 +136,7 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  * options fail with LC_EINVAL and leave the setting unchanged.  Options (default first):
  *   LC_TUNE_NTT_ROW_MINB       row pass of the NTT: minimum resident 128-thread blocks, i.e. a
  *                              register cap: 4, 5, 6
- *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 8, 1 (no cap), 6
+ *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 8, 1 (no cap), 6, 7
  *   LC_TUNE_GROUP_SPLIT_ITEMS  one-ModDown group kernel, rows with primes below 2^40: items per
  *                              thread, 1 or 2
  *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 2 or 1

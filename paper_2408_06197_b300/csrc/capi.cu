@@ -1505,7 +1505,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
     bool ok = false;
     switch (knob) {
         case LC_TUNE_NTT_ROW_MINB: ok = value == 4 || value == 5 || value == 6; break;
-        case LC_TUNE_NTT_COL_MINB: ok = value == 1 || value == 6 || value == 8; break;
+        case LC_TUNE_NTT_COL_MINB: ok = value == 1 || value == 6 || value == 7 || value == 8; break;
         case LC_TUNE_GROUP_SPLIT_ITEMS:
         case LC_TUNE_GROUP_WIDE_ITEMS: ok = value == 1 || value == 2; break;
         case LC_TUNE_TENSOR_WARPS: ok = value == 8 || value == 12 || value == 16; break;

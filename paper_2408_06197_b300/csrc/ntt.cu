@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size
 }  // namespace
 
 // column pass: C = log_n - 8 in [4, 8]; MINB (minimum resident blocks, i.e. a register cap) is
-// a tuning choice: 1, 6 or 8
+// a tuning choice: 1, 6, 7 or 8
 #define LC_COL_C(KERNEL, MB, C_, GRID, S_)                                                          \
     switch (C_) {                                                                                   \
         case 4: KERNEL<4, MB><<<GRID, 1 << 4, 0, S_>>>(base, batch_stride, map, tb); break;         \
@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(kRowThreads, MINB) ntt_inv_row(u64* base, size
 #define LC_COL_DISPATCH(KERNEL, MINB_, C_, GRID, S_)            \
     switch (MINB_) {                                            \
         case 6: LC_COL_C(KERNEL, 6, C_, GRID, S_) break;        \
+        case 7: LC_COL_C(KERNEL, 7, C_, GRID, S_) break;        \
         case 8: LC_COL_C(KERNEL, 8, C_, GRID, S_) break;        \
         default: LC_COL_C(KERNEL, 1, C_, GRID, S_) break;       \
     }

@@ -36,7 +36,7 @@ struct NttTables {
 // launch-shape choices (register caps) picked by the tuner; results do not depend on them
 struct NttTune {
     int row_minb = 4;  // row pass: minimum resident blocks of 128 threads (4, 5 or 6)
-    int col_minb = 8;  // column pass: 1 (no cap), 6 or 8
+    int col_minb = 8;  // column pass: 1 (no cap), 6, 7 or 8
     int row_tma = 0;   // forward row pass: 1 = persistent blocks streaming tiles with bulk copies
 };
 
