@@ -166,6 +166,109 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """The uneven batch at full size: 8 jobs (seed 2), each with its own key set (relinearisation +
+    the 31 rotation keys of the [3,3,3,3,2] schedule), n in {5,10,20,40}, d in {2^16..2^22}
+    (147 GB of ciphertexts resident), distances + masked aggregates of all jobs per step in
+    shared launches (lc_batch_distances / lc_batch_aggregate: ragged pair and chunk lists packed
+    into waves).  Beside it, the same jobs one after another through lc_distances /
+    lc_masked_aggregate.  Inputs are encrypted on the GPU with device randomness (untimed)."""
+    import torch
+    from paper_2408_06197_b300 import kgc
+    from paper_2408_06197_b300 import lancelot as LC
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(0)
+    sched = SCHEDULES["g3qp"]
+    jobs_w = S.uneven_jobs()
+    with torch.cuda.stream(stream):
+        g = LC.Context.production(device=0, stream=stream)
+        N, qp = g.N, g.q + g.p
+        jobs, evks, keys_s = [], [], []
+        for j, w in enumerate(jobs_w):
+            s = S.secret_key(w.seed, w.config, N, job=j)
+            pk = g.pk_gen(s, *S.pk_rand(w.seed, w.config, g.q, N, job=j))
+            evk = g.evk()
+            evk.add(s, None, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, None, job=j))
+            for r in LC.rotations_of_schedule(sched):
+                evk.add(s, r, *S.swk_rand(w.seed, w.config, qp, g.dnum, N, r, job=j))
+            cts = g.empty(w.n_clients, w.chunks, 2, g.nq, N)
+            flat = cts.view(w.n_clients * w.chunks, 2, g.nq, N)
+            W = np.stack([S.client_updates(w, [i])[0] for i in range(w.n_clients)])
+            for i in range(w.n_clients):
+                z = torch.tensor(S.split_chunks(W[i], g.slots), device="cuda:0")
+                g.encode_encrypt_seeded(pk, z, g.scale, w.seed * 1000 + j, i * w.chunks,
+                                        out=flat[i * w.chunks:(i + 1) * w.chunks])
+            gram = W @ W.T
+            sq = np.diag(gram)[:, None] + np.diag(gram)[None, :] - 2 * gram
+            del W
+            wts = kgc.mask_weights(w.n_clients, kgc.krum_select(sq, w.f, w.n_select), average=True)
+            masks = g.encrypt_const_seeded(pk, torch.tensor(wts, dtype=torch.float64, device="cuda:0"), g.scale,
+                                           w.seed * 1000 + j, 1 << 40)
+            jobs.append(LC.Job(evk, cts, w.n_clients, w.chunks, masks))
+            evks.append(evk)
+            keys_s.append(s)
+        torch.cuda.synchronize()
+        qpf = LC.LC_HOIST_QP_SUM
+        n_pairs = sum(w.n_pairs for w in jobs_w)
+        pair_chunks = sum(w.n_pairs * w.chunks for w in jobs_w)
+
+        def batched():
+            LC.batch_distances(g, jobs, qpf, sched)
+            LC.batch_aggregate(g, jobs)
+
+        def alone():
+            for jb in jobs:
+                g.distances(jb.evk, jb.cts, jb.n, jb.chunks, g.scale, mode=LC.LC_MODE_BATCHED | qpf, groups=sched,
+                            out=jb.out_dist)
+                g.masked_aggregate(jb.evk, jb.cts, jb.n, jb.chunks, g.scale, jb.masks, g.scale, out=jb.out_agg)
+
+        def timed(fn, steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            ev[0].record(stream)
+            for k in range(steps):
+                fn()
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize()
+            return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+
+        for _ in range(args.warmup):
+            batched()
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        step_ms = timed(batched, args.steps)
+        ck = clocks.stop()
+        alone()
+        alone_ms = timed(alone, max(1, args.steps))
+        # accuracy of the batched read-outs against the FP64 distances of one small job (untimed)
+        batched()
+        j0 = min(range(len(jobs_w)), key=lambda k: jobs_w[k].n_clients * jobs_w[k].chunks)
+        w0 = jobs_w[j0]
+        W0 = np.stack([S.client_updates(w0, [i])[0] for i in range(w0.n_clients)])
+        ref = np.array([np.sum((W0[a] - W0[b]) ** 2) for a in range(w0.n_clients) for b in range(a + 1, w0.n_clients)])
+        got = g.decrypt_const(keys_s[j0], jobs[j0].out_dist, g.L - 1, g.scale * g.scale / g.q[g.L])
+        rel = float(np.max(np.abs(got - ref) / ref))
+        g.sync()
+    ms = sum(step_ms) / len(step_ms)
+    ams = sum(alone_ms) / len(alone_ms)
+    line = {"metric": "encrypted client-pair distances/s (uneven batch of 8 jobs, N=2^15)",
+            "value": n_pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic (GPU encode + encryption with device randomness)",
+            "config": {"workload": "uneven_8jobs_seed2_n{5,10,20,40}_d{2^16..2^22}",
+                       "jobs": [{"n": w.n_clients, "d": w.d, "chunks": w.chunks, "pairs": w.n_pairs} for w in jobs_w],
+                       "pairs": n_pairs, "pair_chunks": pair_chunks, "rotation_schedule": "g3qp",
+                       "launch": "lc_batch_distances + lc_batch_aggregate (shared waves)",
+                       "l2": "inputs larger than L2 (147 GB client ciphertexts resident)"},
+            "pair_chunks_per_s": pair_chunks / (ms / 1e3), "clocks": ck,
+            "jobs_one_after_another": {"ms_per_step": ams, "pairs_per_s": n_pairs / (ams / 1e3),
+                                       "batched_over_alone": ams / ms},
+            "max_rel_err_vs_fp64": rel, "accuracy_job": j0,
+            "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))}}
+    print(json.dumps(line), flush=True)
+
+
 def run_probes(args):
     """One JSON line: each probe at 4, 8 and 16 resident blocks of 256 threads per SM."""
     import torch
@@ -631,9 +734,10 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving HBM admission budget")
     ap.add_argument("--host-kgc", action="store_true",
                     help="serving: KGC step on the host (default: on the device, no host round trip)")
-    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "batched", "uneven"], default="plain",
                     help="batched = n=50 clients, d=2^22 (256 ciphertexts each, 94 GB resident), 1,225 pairs; "
-                         "one JSON line beside the headline workload")
+                         "uneven = 8 jobs with their own keys, n in {5..40}, d in {2^16..2^22} (147 GB "
+                         "resident), in shared launches; one JSON line beside the headline workload")
     ap.add_argument("--probes", action="store_true",
                     help="integer-pipe probes only (register-resident IMAD, wide IMAD, NTT butterfly)")
     ap.add_argument("--probe-iters", type=int, default=4096)
@@ -656,6 +760,10 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "uneven":
+        os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
+        run_uneven(args)
         return
     if args.serving:
         # rounds of 0.1-75 GiB come and go: let the caching allocator grow segments instead of

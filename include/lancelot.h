@@ -393,15 +393,19 @@ typedef struct {
     uint64_t* out_agg;     /* [chunks][2][n_q-1][N], for lc_batch_aggregate */
 } lc_job;
 
-/* Encrypted distances of several rounds at once (Algorithm 1 "Server Executes" per job): all
- * (job, pair) items -- different client counts, model sizes and key sets -- run together in
- * batched waves; each job's results are bit-identical to lc_distances on that job alone with
- * the same schedule.  flags: 0 or LC_HOIST_QP_SUM; groups as in lc_rotate_sum (sizes <= 3).
- * Synchronises the stream between waves (descriptors are rewritten). */
+/* Encrypted distances of several rounds at once (Algorithm 1 "Server Executes" per job): the
+ * (job, pair) items of small jobs -- different client counts, model sizes and key sets -- run
+ * together in batched waves (per-item key tables); a job with at least half a wave of pairs runs
+ * on its own through the lc_distances path (keys shared by the launch) after them.  Each job's
+ * results are bit-identical to lc_distances on that job alone with the same schedule.  flags: 0
+ * or LC_HOIST_QP_SUM; groups as in lc_rotate_sum (sizes <= 3).  Synchronises the stream between
+ * shared waves (descriptors are rewritten). */
 int lc_batch_distances(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t n_groups,
                        const uint32_t* groups);
-/* Masked aggregates of several rounds at once (Algorithm 1 "ServerUpdate" per job); each job's
- * results are bit-identical to lc_masked_aggregate on that job alone. */
+/* Masked aggregates of several rounds at once (Algorithm 1 "ServerUpdate" per job): chunks of
+ * small jobs share waves, a job with at least half a wave of chunks runs through the
+ * lc_masked_aggregate path; each job's results are bit-identical to lc_masked_aggregate on that
+ * job alone. */
 int lc_batch_aggregate(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs);
 
 #ifdef __cplusplus

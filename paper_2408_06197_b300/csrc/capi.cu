@@ -1819,9 +1819,18 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
     int maxg = 1;
     for (uint32_t g : sched) maxg = std::max(maxg, (int)g);
     if (maxg > 3) return fail(c, LC_EINVAL, "batched groups are limited to size 3");
-    // every item: (job, pair)
+    const size_t rot_words = std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp),
+                                              ks_words(c, 1, L - 1) + ((((size_t)1 << maxg) - 1) * 2 * (L + c->np) +
+                                                                       (((size_t)1 << maxg) - 1) * 2 * L) * N);
+    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
+                            rot_words + 64;
+    const int Bcap = max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
+    // every item: (job, pair) of the jobs that share waves; a job with at least half a wave of
+    // pairs runs alone through the single-job path (keys shared by the whole launch, no
+    // per-item key tables), after the shared waves
     struct It { int job, i, j, p; };
     std::vector<It> items;
+    std::vector<uint32_t> alone;
     for (uint32_t jb = 0; jb < n_jobs; jb++) {
         const lc_job& J = jobs[jb];
         if (!job_ok(c, J, false)) return fail(c, LC_EINVAL, "lc_batch_distances: job " + std::to_string(jb) + " invalid");
@@ -1834,17 +1843,25 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
                                                 " missing");
             stride <<= g;
         }
+        if ((uint64_t)J.n * (J.n - 1) / 2 >= (uint64_t)std::max(1, Bcap / 2)) {
+            alone.push_back(jb);
+            continue;
+        }
         int p = 0;
         for (uint32_t i = 0; i < J.n; i++)
             for (uint32_t j = i + 1; j < J.n; j++) items.push_back(It{(int)jb, (int)i, (int)j, p++});
     }
-    if (items.empty()) return LC_OK;
-    const size_t rot_words = std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp),
-                                              ks_words(c, 1, L - 1) + ((((size_t)1 << maxg) - 1) * 2 * (L + c->np) +
-                                                                       (((size_t)1 << maxg) - 1) * 2 * L) * N);
-    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
-                            rot_words + 64;
-    const int Bw = std::min<int>(max_batch_for(c, per_item, (size_t)8 << 30 >> 3), (int)items.size());
+    auto run_alone = [&]() {
+        for (uint32_t jb : alone) {
+            const lc_job& J = jobs[jb];
+            const int st = lc_distances(c, J.evk, J.cts, J.n, J.chunks, 1.0, LC_MODE_BATCHED | (qp ? LC_HOIST_QP_SUM : 0),
+                                        (uint32_t)sched.size(), sched.data(), J.out_dist, nullptr);
+            if (st) return st;
+        }
+        return (int)LC_OK;
+    };
+    if (items.empty()) return run_alone();
+    const int Bw = std::min<int>(Bcap, (int)items.size());
     const size_t desc_words = (size_t)Bw * 64 + 4096;
     u64* t = lc_scratch(c, (per_item * Bw + desc_words) * 8);
     if (!t) return fail(c, LC_ENOMEM, "scratch");
@@ -1856,7 +1873,6 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
     for (size_t w0 = 0; w0 < items.size(); w0 += Bw) {
         const int b = (int)std::min<size_t>(Bw, items.size() - w0);
         WaveBlob blob;
-        std::vector<PairItem> pi(b);
         std::vector<const u64*> rk(b);
         std::vector<u64*> dst(b);
         std::vector<std::vector<const u64*>> gk(sched.size(), std::vector<const u64*>());
@@ -1865,8 +1881,6 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
         for (int k = 0; k < b; k++) {
             const It& it = items[w0 + k];
             const lc_job& J = jobs[it.job];
-            const size_t cs = (size_t)J.chunks * 2 * Pin;
-            pi[k] = PairItem{J.cts + (size_t)it.i * cs, J.cts + (size_t)it.j * cs, (int)J.chunks, k};
             rk[k] = find_key(J.evk, -1)->data;
             dst[k] = J.out_dist + (size_t)it.p * 2 * Pout;
             long stride = 1;
@@ -1882,15 +1896,26 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
                 stride <<= sched[gi];
             }
         }
-        const size_t o_items = blob.put(pi.data(), pi.size());
         const size_t o_rk = blob.put(rk.data(), rk.size());
         const size_t o_dst = blob.put(dst.data(), dst.size());
         std::vector<size_t> o_gk(sched.size());
         for (size_t gi = 0; gi < sched.size(); gi++) o_gk[gi] = blob.put(gk[gi].data(), gk[gi].size());
         if (blob.bytes.size() > desc_words * 8) return fail(c, LC_EINVAL, "descriptor area too small");
         LC_CUDA(c, cudaMemcpyAsync(desc, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice, c->stream));
-        PROF(c, PROF_TENSOR, 0.0, (uint64_t)b,
-             op_sq_acc_items(c, reinterpret_cast<const PairItem*>(desc + o_items), b, c->nq, acc3));
+        // tensor phase: the wave's items are runs of consecutive pairs of one job each; every run
+        // takes the client-block-tiled kernel of that job (each client tile read about n/8 times
+        // instead of once per pair it belongs to)
+        for (int k0 = 0; k0 < b;) {
+            const It& first = items[w0 + k0];
+            int k1 = k0 + 1;
+            while (k1 < b && items[w0 + k1].job == first.job && items[w0 + k1].p == first.p + (k1 - k0)) k1++;
+            const lc_job& J = jobs[first.job];
+            const double touched = std::min<double>(J.n, 2.0 * (k1 - k0));
+            PROF(c, PROF_TENSOR, (touched * J.chunks * 2.0 + 3.0 * (k1 - k0)) * Pin * 8.0, (uint64_t)(k1 - k0),
+                 op_sq_acc_tiled(c, J.cts, (int)J.n, (int)J.chunks, c->nq, first.p, k1 - k0,
+                                 acc3 + (size_t)k0 * 3 * Pin));
+            k0 = k1;
+        }
         std::vector<const u64* const*> gkd(sched.size());
         for (size_t gi = 0; gi < sched.size(); gi++) gkd[gi] = reinterpret_cast<const u64* const*>(desc + o_gk[gi]);
         int st = items_tail(c, acc3, y, tmp, b, reinterpret_cast<const u64* const*>(desc + o_rk), gkd, gt, gal,
@@ -1900,6 +1925,8 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
         // the next wave rewrites the descriptors: wait until this wave has consumed them
         LC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    const int st = run_alone();
+    if (st) return st;
     return check_launch(c, "lc_batch_distances");
 }
 
@@ -1909,17 +1936,34 @@ int lc_batch_aggregate(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs) {
     const int L = c->nq - 1;
     const size_t N = c->N;
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) + 64;
+    const int Bcap = max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
+    // chunks of the jobs that share waves; a job with at least half a wave of chunks runs alone
+    // through the single-job path after the shared waves
     struct It { int job, k; };
     std::vector<It> items;
+    std::vector<uint32_t> alone;
     for (uint32_t jb = 0; jb < n_jobs; jb++) {
         const lc_job& J = jobs[jb];
         if (!job_ok(c, J, true)) return fail(c, LC_EINVAL, "lc_batch_aggregate: job " + std::to_string(jb) + " invalid");
         if (!find_key(J.evk, -1)) return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": relinearisation key missing");
+        if (J.chunks >= (uint32_t)std::max(1, Bcap / 2)) {
+            alone.push_back(jb);
+            continue;
+        }
         for (uint32_t k = 0; k < J.chunks; k++) items.push_back(It{(int)jb, (int)k});
     }
-    if (items.empty()) return LC_OK;
-    const size_t per_item = 3 * Pin + 2 * Pin + 2 * Pout + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) + 64;
-    const int Bw = std::min<int>(max_batch_for(c, per_item, (size_t)8 << 30 >> 3), (int)items.size());
+    auto run_alone = [&]() {
+        for (uint32_t jb : alone) {
+            const lc_job& J = jobs[jb];
+            const int st = lc_masked_aggregate(c, J.evk, J.cts, J.n, J.chunks, 1.0, J.masks, 1.0, LC_MODE_BATCHED,
+                                               J.out_agg, nullptr);
+            if (st) return st;
+        }
+        return (int)LC_OK;
+    };
+    if (items.empty()) return run_alone();
+    const int Bw = std::min<int>(Bcap, (int)items.size());
     const size_t desc_words = (size_t)Bw * 16 + 1024;
     u64* t = lc_scratch(c, (per_item * Bw + desc_words) * 8);
     if (!t) return fail(c, LC_ENOMEM, "scratch");
@@ -1954,6 +1998,8 @@ int lc_batch_aggregate(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs) {
         op_copy_items(c, y, 2 * Pout, reinterpret_cast<u64* const*>(desc + o_dst), b);
         LC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    const int st = run_alone();
+    if (st) return st;
     return check_launch(c, "lc_batch_aggregate");
 }
 

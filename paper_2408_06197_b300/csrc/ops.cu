@@ -193,11 +193,6 @@ __device__ __forceinline__ void sq_split_w(Acc3& s, unsigned h, unsigned l) {  /
     mad_wide(s.b, h, l);
     mad_wide(s.c, l, l);
 }
-__device__ __forceinline__ void sq_split(Acc3& s, unsigned h, unsigned l) {  // b holds sum h l (doubled at the end)
-    s.a += (u64)h * h;
-    s.b += (u64)h * l;
-    s.c += (u64)l * l;
-}
 // a 2^40 + b 2^20 * bmul + c mod q
 __device__ __forceinline__ u64 acc3_reduce(const Acc3& s, int bshift, const ModConst& m) {
     u128v v{s.c, 0};
@@ -667,49 +662,6 @@ __global__ void k_pack_key(const u64* __restrict__ in, u64* __restrict__ out, in
 }
 
 // ---------------------------------------------------------------------------- multi-job items
-// tensor accumulate of one pair per item (ragged chunk counts).  grid: x = item, y = tile, z = limb
-template <bool SPLIT>
-__global__ void __launch_bounds__(kT) k_sq_acc_items(const PairItem* __restrict__ items, int nl, int limb0, int log_n,
-                                                     const ModConst* __restrict__ mc, u64* __restrict__ out) {
-    const PairItem it = items[blockIdx.x];
-    const int limb = limb0 + blockIdx.z;
-    const size_t N = (size_t)1 << log_n;
-    const size_t x = (size_t)blockIdx.y * kT + threadIdx.x;
-    const ModConst m = mc[limb];
-    const size_t P = (size_t)nl * N;
-    const u64* ai = it.a + (size_t)limb * N + x;
-    const u64* aj = it.b + (size_t)limb * N + x;
-    u128v s00{0, 0}, s01{0, 0}, s11{0, 0};
-    Acc3 t00{0, 0, 0}, t01{0, 0, 0}, t11{0, 0, 0};
-    for (int k = 0; k < it.chunks; k++) {
-        const u64 a0 = __ldg(ai), a1 = __ldg(ai + P), b0 = __ldg(aj), b1 = __ldg(aj + P);
-        ai += 2 * P;
-        aj += 2 * P;
-        const u64 x0 = sub_mod(a0, b0, m.q), x1 = sub_mod(a1, b1, m.q);
-        if (SPLIT) {
-            const unsigned h0 = (unsigned)(x0 >> 20), l0 = (unsigned)x0 & 0xFFFFFu;
-            const unsigned h1 = (unsigned)(x1 >> 20), l1 = (unsigned)x1 & 0xFFFFFu;
-            sq_split(t00, h0, l0);
-            mac_split(t01, h0, l0, h1, l1);
-            sq_split(t11, h1, l1);
-        } else {
-            mac128(s00, x0, x0);
-            mac128(s01, x0, x1);
-            mac128(s11, x1, x1);
-            if ((k & 7) == 7) {
-                fold(s00, m);
-                fold(s01, m);
-                fold(s11, m);
-            }
-        }
-    }
-    u64* o = out + (size_t)it.slot * 3 * P + (size_t)limb * N + x;
-    const u64 d1 = SPLIT ? acc3_reduce(t01, 20, m) : reduce128(s01, m);
-    o[0] = SPLIT ? acc3_reduce(t00, 21, m) : reduce128(s00, m);
-    o[P] = add_mod(d1, d1, m.q);
-    o[2 * P] = SPLIT ? acc3_reduce(t11, 21, m) : reduce128(s11, m);
-}
-
 // masked accumulate of one chunk of one job per item.  grid: x = item, y = tile, z = limb
 template <bool SPLIT>
 __global__ void __launch_bounds__(kT) k_mask_acc_items(const AggItem* __restrict__ items, int nl, int limb0,
@@ -1810,21 +1762,6 @@ void op_const_plain(lc_ctx* c, const double* w, int count, double scale, int64_t
     if (count <= 0) return;
     k_const_plain<<<grid_for((size_t)count * c->N), kT, 0, c->stream>>>(w, count, c->log_n, scale, m);
     g_lc_launches += 1;
-}
-
-void op_sq_acc_items(lc_ctx* c, const PairItem* items_dev, int count, int nl, u64* out) {
-    if (count <= 0) return;
-    const int s0 = split_start(c, nl);  // an item's chunks (< 2^20) fit the 64-bit partial sums
-    if (s0 > 0) {
-        dim3 grid(count, (unsigned)(c->N / kT), s0);
-        k_sq_acc_items<false><<<grid, kT, 0, c->stream>>>(items_dev, nl, 0, c->log_n, c->mc, out);
-        g_lc_launches += 1;
-    }
-    if (s0 < nl) {
-        dim3 grid(count, (unsigned)(c->N / kT), nl - s0);
-        k_sq_acc_items<true><<<grid, kT, 0, c->stream>>>(items_dev, nl, s0, c->log_n, c->mc, out);
-        g_lc_launches += 1;
-    }
 }
 
 void op_mask_acc_items(lc_ctx* c, const AggItem* items_dev, int count, int nl, u64* out) {

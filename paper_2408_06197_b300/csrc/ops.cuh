@@ -68,13 +68,6 @@ void op_dec_combine(lc_ctx* c, const u64* ct, const u64* s, int deg, int nl, u64
 void op_square_rows(lc_ctx* c, const u64* s, u64* out, const int* mods_host, int nrows);
 
 // ------------------------------------------------------------------ multi-job (ragged) batches
-// one pair of one job: client chunk arrays a, b ([chunks][2][nl][N]), result slot `slot`
-struct PairItem {
-    const u64* a;
-    const u64* b;
-    int chunks;
-    int slot;
-};
 // one chunk k of one job: the job's ciphertexts ([n][chunks][2][nl][N]) and masks ([n][2][nl][N])
 struct AggItem {
     const u64* cts;
@@ -84,7 +77,6 @@ struct AggItem {
     int k;
     int slot;
 };
-void op_sq_acc_items(lc_ctx* c, const PairItem* items_dev, int count, int nl, u64* out);
 void op_mask_acc_items(lc_ctx* c, const AggItem* items_dev, int count, int nl, u64* out);
 // inner products with per-item keys: keys_dev[b * T + t] is item b's key for slot t
 void op_inner_items(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, int B, int level,

@@ -389,7 +389,8 @@ def test_uneven_batch_matches_each_job_alone(toy):
     keys_b = KeySet(toy.prm, 7, S.CFG_UNEVEN, O.rotations_of_schedule(toy.sched) + [3])
     _, evk_b = keys_b.gpu_keys(g)
     pk_b = g.pk_gen(keys_b.s, keys_b.pk_a, keys_b.pk_e)
-    specs = [(3, 1, toy.gevk, toy.gpk, 0), (5, 3, evk_b, pk_b, 1), (2, 2, toy.gevk, toy.gpk, 2), (4, 2, evk_b, pk_b, 3)]
+    specs = [(3, 1, toy.gevk, toy.gpk, 0), (5, 3, evk_b, pk_b, 1), (2, 2, toy.gevk, toy.gpk, 2), (4, 2, evk_b, pk_b, 3),
+             (2, 1, evk_b, pk_b, 4), (2, 3, toy.gevk, toy.gpk, 5), (2, 1, toy.gevk, toy.gpk, 6), (2, 2, evk_b, pk_b, 7)]
     jobs = []
     for n, chunks, evk, pk, jid in specs:
         w = S.Workload(f"u{jid}", S.CFG_UNEVEN, 12, n, chunks * toy.prm.slots - 7, 2, (n - 1,), "scale5", 1, 1, job=jid)
@@ -410,16 +411,24 @@ def test_uneven_batch_matches_each_job_alone(toy):
     for j in jobs:
         alone, _ = g.masked_aggregate(j.evk, j.cts, j.n, j.chunks, toy.prm.scale, j.masks, toy.prm.scale)
         assert torch.equal(alone, j.out_agg)
-    g.set_max_batch(3)  # several waves: still identical
-    try:
-        for j in jobs:
-            j.out_dist = None
-        LC.batch_distances(g, jobs)
-        for j in jobs:
-            alone, _ = g.distances(j.evk, j.cts, j.n, j.chunks, toy.prm.scale)
-            assert torch.equal(alone, j.out_dist)
-    finally:
-        g.set_max_batch(0)
+    # smaller waves: jobs with at least half a wave of pairs (chunks) run on their own, the others
+    # share waves -- 4: the five single-pair jobs in two shared waves (and the single-chunk jobs'
+    # aggregates in one), the rest alone; 8: the jobs of at most 3 pairs shared; 3: every job
+    # alone.  Identical in every case.
+    for cap in (4, 8, 3):
+        g.set_max_batch(cap)
+        try:
+            for j in jobs:
+                j.out_dist = j.out_agg = None
+            LC.batch_distances(g, jobs)
+            LC.batch_aggregate(g, jobs)
+            for j in jobs:
+                alone, _ = g.distances(j.evk, j.cts, j.n, j.chunks, toy.prm.scale)
+                assert torch.equal(alone, j.out_dist)
+                alone, _ = g.masked_aggregate(j.evk, j.cts, j.n, j.chunks, toy.prm.scale, j.masks, toy.prm.scale)
+                assert torch.equal(alone, j.out_agg)
+        finally:
+            g.set_max_batch(0)
 
 
 # ------------------------------------------------------------------------------- production sizes
