@@ -12,6 +12,14 @@ generated on the device once (client ciphertexts: 4.8 GB, larger than L2) and st
 Under torchrun each rank runs an independent replica on its own GPU (weak scaling); rank 0 prints
 one JSON line.  The reference arm (--impl reference) times the CPU oracle on the host cores on a
 bounded sample per step (1 pair + 1 aggregate chunk), extrapolated to the same workload.
+
+Other modes, one JSON line each (per rate / ring degree where stated):
+  --workload batched   n = 50 clients, d = 2^22 (94 GB resident), 1,225 pairs + aggregate
+  --workload uneven    8 jobs with their own key sets (147 GB resident) in shared launches
+  --serving            Poisson round arrivals per rate, p50/p99 round latency
+  --sweep              the same round at N = 2^13 .. 2^16
+  --probes             register-resident integer-pipe probes (the ALU roofline's peak)
+  --micro              small isolated kernel case for profiler captures (NVTX ranges)
 """
 from __future__ import annotations
 
