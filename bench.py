@@ -78,12 +78,6 @@ def peaks():
         return 6400.0, "fallback"
 
 
-# Integer-pipe roofline.  The transforms are bound by 64-bit modular arithmetic emulated on the
-# 32-bit integer pipes, not by DRAM.  Their ceiling is measured the way the copy bandwidth and the
-# GEMM rate are: the library's register-resident probe runs the very butterfly of the transforms
-# (lazy Shoup Cooley-Tukey, twiddles in registers, no memory traffic) on every SM, live in the same
-# run at the same clock.  The IMAD probe checks the unit count behind it: 148 SMs x 64 32-bit
-# multiply-adds per clock (profiles/alu_probes.md).
 def run_batched(args):
     """The batched workload at full size: 50 clients x 256 chunks (94 GB of ciphertexts resident),
     1,225 pair distances + the masked aggregate of 256 chunks per step, autotuned schedule and
@@ -294,6 +288,12 @@ def run_probes(args):
     print(json.dumps({"probes": out, "unit": "T operations/s (butterflies for ntt_butterfly)"}), flush=True)
 
 
+# Integer-pipe roofline.  The transforms are bound by 64-bit modular arithmetic emulated on the
+# 32-bit integer pipes, not by DRAM.  Their ceiling is measured the way the copy bandwidth and the
+# GEMM rate are: the library's register-resident probe runs the very butterfly of the transforms
+# (lazy Shoup Cooley-Tukey, twiddles in registers, no memory traffic) on every SM, live in the same
+# run at the same clock.  The IMAD probe checks the unit count behind it: 148 SMs x 64 32-bit
+# multiply-adds per clock x 2.03 GHz = 19.2 T/s nominal, 19.2 T/s measured on a B300.
 def alu_roofline(g, ntt_bytes: float, ntt_ms: float, sm_mhz):
     """NTT butterflies/s against the live register-resident probe of the same butterfly."""
     probes = {}
@@ -357,9 +357,10 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload (GPU)
 SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7, "g3qp": [3, 3, 3, 3, 2]}
 
-# DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture of the
-# 960-limb case of `bench.py --micro` (profiles/ntt_micro_960limbs.md): forward 443.7 + 453.9 MB,
-# inverse 453.5 + 443.8 MB per 960 limbs.  Valid for the current ntt.cu only.
+# DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
+# forward 443.7 + 453.9 MB, inverse 453.5 + 443.8 MB per 960 limbs.  Valid for the current
+# transform kernels only.
 NTT_DRAM_BYTES_PER_LIMB = (443.7e6 + 453.9e6 + 453.5e6 + 443.8e6) / (2 * 960)
 
 
