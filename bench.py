@@ -359,9 +359,9 @@ SCHEDULES = {"log": [1] * 14, "g2qp": [2] * 7, "g3qp": [3, 3, 3, 3, 2]}
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
-# forward 443.7 + 453.9 MB, inverse 453.5 + 443.8 MB per 960 limbs.  Valid for the current
-# transform kernels only.
-NTT_DRAM_BYTES_PER_LIMB = (443.7e6 + 453.9e6 + 453.5e6 + 443.8e6) / (2 * 960)
+# forward 449.1 + 453.4 MB, inverse 452.7 + 443.8 MB per 960 limbs (column cap 8, row cap 4).
+# Valid for the current transform kernels only.
+NTT_DRAM_BYTES_PER_LIMB = (449.1e6 + 453.4e6 + 452.7e6 + 443.8e6) / (2 * 960)
 
 
 def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):
