@@ -1,0 +1,92 @@
+"""Host logic of the autotuner on the CPU: candidate schedules filtered by the loaded rotation
+keys and the key budget, the fastest schedule kept, then each knob set by coordinate descent and
+left on the context.  Device timing is replaced by a deterministic cost model (no GPU); the GPU
+test (tests/test_tuning.py) checks that every option computes the same bits."""
+import pytest
+
+pytest.importorskip("torch")
+
+from paper_2408_06197_b300 import autotune  # noqa: E402
+from paper_2408_06197_b300 import lancelot as LC  # noqa: E402
+
+
+class FakeCtx:
+    log_n, N, nq, np_, dnum, L = 15, 1 << 15, 15, 4, 4, 14
+
+    def __init__(self):
+        self.knobs = {k: opts[0] for k, opts in LC.TUNING_OPTIONS.items()}
+        self.calls = []
+
+    def set_tuning(self, knob, value):
+        assert value in LC.TUNING_OPTIONS[knob]
+        self.knobs[knob] = value
+
+    def get_tuning(self, knob):
+        return self.knobs[knob]
+
+    def tuning(self):
+        return {LC.TUNING_NAMES[k]: v for k, v in self.knobs.items()}
+
+    def empty(self, *shape):
+        return None
+
+    def distances(self, evk, cts, n, chunks, scale, mode=0, groups=None, out=None):
+        self.calls.append((tuple(groups), mode, dict(self.knobs)))
+
+
+class FakeEvk:
+    def __init__(self, rotations):
+        self.rotations = list(rotations)
+
+
+# cost model: schedule base cost, plus one preferred option per knob (the second one listed)
+BASE = {"log": 50.0, "g2qp": 40.0, "g3qp": 30.0}
+
+
+def _cost(ctx, groups):
+    name = {tuple(v): k for k, v in autotune.candidate_schedules(15).items()}[tuple(groups)]
+    ms = BASE[name]
+    for knob, opts in LC.TUNING_OPTIONS.items():
+        ms += 0.0 if ctx.knobs[knob] == opts[1 % len(opts)] else 1.0
+    return ms
+
+
+@pytest.fixture
+def model(monkeypatch):
+    def time_ms(ctx, fn, reps):
+        fn()
+        return _cost(ctx, ctx.calls[-1][0])
+    monkeypatch.setattr(autotune, "_time_ms", time_ms)
+
+
+def _all_rots():
+    rots = set()
+    for s in autotune.candidate_schedules(15).values():
+        rots |= set(LC.rotations_of_schedule(s))
+    return sorted(rots)
+
+
+def test_picks_fastest_schedule_then_each_knob(model):
+    ctx = FakeCtx()
+    res = autotune.tune(ctx, FakeEvk(_all_rots()), None, 10, 64, 1.0)
+    assert res["schedule"] == "g3qp" and res["groups"] == [3, 3, 3, 3, 2]
+    assert res["mode"] == LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM
+    for knob, opts in LC.TUNING_OPTIONS.items():  # coordinate descent found every preferred option
+        assert ctx.knobs[knob] == opts[1 % len(opts)]
+        assert res["knobs"][LC.TUNING_NAMES[knob]] == opts[1 % len(opts)]
+    assert res["ms"] == pytest.approx(30.0)
+    n_opts = sum(len(o) for o in LC.TUNING_OPTIONS.values())
+    assert len(res["trials"]) == 3 + n_opts
+
+
+def test_candidates_need_their_keys_and_fit_the_budget(model):
+    ctx = FakeCtx()
+    log_keys = LC.rotations_of_schedule(autotune.candidate_schedules(15)["log"])
+    res = autotune.tune(ctx, FakeEvk(log_keys), None, 10, 64, 1.0)
+    assert res["schedule"] == "log"  # only the log-step keys are loaded
+    # a budget that holds the 14 + 1 log-step keys but not the 21 + 1 or 31 + 1 of the others
+    budget = autotune.key_bytes(ctx, 15) * 1.01
+    res = autotune.tune(FakeCtx(), FakeEvk(_all_rots()), None, 10, 64, 1.0, key_budget_bytes=budget)
+    assert res["schedule"] == "log"
+    with pytest.raises(LC.LancelotError):
+        autotune.tune(FakeCtx(), FakeEvk([1, 2]), None, 10, 64, 1.0)
