@@ -68,6 +68,10 @@ def test_tuning_entry_points_reject_bad_arguments_without_gpu(lib):
     lib.lc_wire_bytes.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
     nb = ctypes.c_uint64()
     assert lib.lc_wire_bytes(None, 2, 0, ctypes.byref(nb)) == -1
+    lib.lc_pack.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_uint32] * 3 + [ctypes.c_void_p]
+    lib.lc_unpack.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_uint32] * 3 + [ctypes.c_void_p]
+    assert lib.lc_pack(None, None, 1, 2, 0, None) == -1
+    assert lib.lc_unpack(None, None, 1, 2, 0, None) == -1
 
 
 def test_autotune_candidate_schedules_cover_every_rotation_bit():
