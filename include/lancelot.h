@@ -222,6 +222,12 @@ void lc_evk_free(lc_evk* evk);
 int lc_evk_add(lc_ctx* ctx, lc_evk* evk, const int8_t* s, int32_t rotation, const uint64_t* a, const int32_t* e);
 /* Copies a key back in canonical form: host uint64[dnum][2][n_q+n_p][N], coefficient domain. */
 int lc_evk_export(lc_ctx* ctx, const lc_evk* evk, int32_t rotation, uint64_t* out);
+/* Adds a key from that canonical form (no counterpart in the paper; checkpoint / restore of a key
+ * set without the secret): `in` as lc_evk_export writes it, for the key of `rotation` (< 0:
+ * relinearisation).  The key is stored exactly as lc_evk_add would store it, so results are
+ * bit-identical.  LC_EINVAL if a residue is not below its prime, LC_EBUSY if the key exists.
+ * Synchronous. */
+int lc_evk_import(lc_ctx* ctx, lc_evk* evk, int32_t rotation, const uint64_t* in);
 
 /* ---------------------------------------------------------------- client side */
 

@@ -868,6 +868,55 @@ int lc_evk_add(lc_ctx* c, lc_evk* evk, const int8_t* s, int32_t rotation, const 
     return LC_OK;
 }
 
+int lc_evk_import(lc_ctx* c, lc_evk* evk, int32_t rotation, const uint64_t* in) {
+    clear_prior_error();
+    if (!c || !evk || !in) return fail(c, LC_EINVAL, "lc_evk_import: null argument");
+    const int32_t id = rotation < 0 ? -1 : rotation;
+    if (rotation == 0) return fail(c, LC_EINVAL, "rotation 0 has no key");
+    if (evk->keys.count(id)) return fail(c, LC_EBUSY, "key exists");
+    const size_t N = c->N;
+    const int rows = c->nq + c->np;
+    const size_t keywords = (size_t)c->dnum * 2 * rows * N;
+    // canonical residues only (row t of every digit and polynomial below its prime)
+    for (size_t blk = 0; blk < (size_t)c->dnum * 2 * rows; blk++) {
+        const u64 m = c->mod[blk % rows];
+        const uint64_t* row = in + blk * N;
+        for (size_t x = 0; x < N; x++)
+            if (row[x] >= m) return fail(c, LC_EINVAL, "lc_evk_import: residue not below its prime");
+    }
+    u64* key = static_cast<u64*>(lc_dev_alloc(c, keywords * 8));
+    if (!key) return fail(c, LC_ENOMEM, "key allocation");
+    u64* qpkey = nullptr;
+    u64* t = lc_scratch(c, keywords * 8);
+    if (!t) {
+        lc_dev_free(c, key);
+        return fail(c, LC_ENOMEM, "scratch");
+    }
+    const uint64_t g = id < 0 ? 0 : galois_of(c, id);
+    u64* dst = id < 0 ? key : t;
+    LC_CUDA(c, cudaMemcpyAsync(dst, in, keywords * 8, cudaMemcpyHostToDevice, c->stream));
+    ntt_fwd_p(c, dst, (size_t)rows * N, c->dnum * 2, rows_seq(rows));
+    if (id >= 0) {  // the two device layouts of a rotation key, as lc_evk_add stores them
+        const uint64_t ginv = hpow(g, (u64)c->N / 2 - 1, 2 * (u64)c->N);
+        op_permute_rows(c, t, key, c->dnum * 2 * rows, ginv);
+        qpkey = static_cast<u64*>(lc_dev_alloc(c, keywords * 8));
+        if (!qpkey) {
+            lc_dev_free(c, key);
+            return fail(c, LC_ENOMEM, "key allocation");
+        }
+        op_pack_key(c, t, qpkey, keywords);
+    }
+    LC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int st = check_launch(c, "lc_evk_import");
+    if (st != LC_OK) {
+        lc_dev_free(c, key);
+        lc_dev_free(c, qpkey);
+        return st;
+    }
+    evk->keys[id] = SwKey{key, g, qpkey};
+    return LC_OK;
+}
+
 int lc_evk_export(lc_ctx* c, const lc_evk* evk, int32_t rotation, uint64_t* out) {
     clear_prior_error();
     if (!c || !evk || !out) return fail(c, LC_EINVAL, "lc_evk_export: null argument");

@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
             "lc_evk_free": [vp],
             "lc_evk_add": [vp, vp, vp, ctypes.c_int32, vp, vp],
             "lc_evk_export": [vp, vp, ctypes.c_int32, vp],
+            "lc_evk_import": [vp, vp, ctypes.c_int32, vp],
             "lc_encode": [vp, vp, ctypes.c_size_t, ctypes.c_double, vp],
             "lc_decode": [vp, vp, ctypes.c_double, vp],
             "lc_encrypt": [vp, vp, vp, vp, vp, vp, u32, vp],
@@ -822,6 +823,18 @@ class EvalKeys:
         rot = -1 if rotation is None else int(rotation)
         c._check(lib().lc_evk_export(c.h, self.h, rot, _np_ptr(out)), "lc_evk_export")
         return out
+
+    def import_key(self, rotation: Optional[int], key: np.ndarray):
+        """Adds a key from its canonical form (as `export` returns it): a key set restored without
+        the secret."""
+        c = self.ctx
+        k = np.ascontiguousarray(key, np.uint64)
+        if k.shape != (c.dnum, 2, c.nq + c.np_, c.N):
+            raise LancelotError(f"import_key: expected shape {(c.dnum, 2, c.nq + c.np_, c.N)}, got {k.shape}")
+        rot = -1 if rotation is None else int(rotation)
+        c._check(lib().lc_evk_import(c.h, self.h, rot, _np_ptr(k)), "lc_evk_import")
+        if rotation is not None:
+            self.rotations.append(int(rotation))
 
     def close(self):
         if getattr(self, "h", None):

@@ -104,6 +104,31 @@ def test_keys_bit_exact(env):
     assert np.array_equal(env.gevk.export(r), env.o.key_to_coeff(env.ork[r]))
 
 
+def test_key_set_restored_from_export_gives_identical_distances(toy):
+    """Checkpoint / restore of a key set without the secret: every key exported in canonical form
+    and imported into a fresh set exports the same words and gives bit-identical distances with
+    the one-ModDown schedule; a non-canonical residue is rejected."""
+    LC, g = toy.LC, toy.g
+    fresh = g.evk()
+    fresh.import_key(None, toy.gevk.export(None))
+    for r in toy.gevk.rotations:
+        fresh.import_key(r, toy.gevk.export(r))
+    r0 = toy.gevk.rotations[0]
+    assert np.array_equal(fresh.export(r0), toy.gevk.export(r0))
+    X = S.split_chunks(S.client_updates(S.Workload("ck", S.CFG_TOY, 12, 3, toy.prm.slots, 9, (2,), "scale10", 1, 1)),
+                       toy.prm.slots)
+    _, gcs = toy.encrypt_both(X, range(3), range(1))
+    sched = [2] + [1] * (len(toy.sched) - 2)
+    mode = LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM
+    a, _ = g.distances(toy.gevk, gcs, 3, 1, toy.prm.scale, mode=mode, groups=sched)
+    b, _ = g.distances(fresh, gcs, 3, 1, toy.prm.scale, mode=mode, groups=sched)
+    assert torch.equal(a, b)
+    bad = toy.gevk.export(None)
+    bad[0, 1, 0, 5] = toy.prm.q[0]
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):
+        g.evk().import_key(None, bad)
+
+
 def test_encrypt_decrypt_bit_exact(env):
     X = np.random.default_rng(3).normal(0, 0.01, (2, 1, env.prm.slots))
     ocs, gcs = env.encrypt_both(X, [0, 1], [0])
