@@ -29,7 +29,7 @@ import torch
 from . import kgc
 from . import lancelot as LC
 
-WAITING, DIST, AGG, DONE = "waiting", "distances", "aggregate", "done"
+WAITING, DIST, AGG, DONE, CANCELLED = "waiting", "distances", "aggregate", "done", "cancelled"
 
 
 @dataclasses.dataclass
@@ -61,6 +61,7 @@ class Round:
     t_done: float = 0.0
     kgc_seconds: float = 0.0
     device_kgc: Optional[tuple] = None  # (read-out values, kept indices) on the device, until read back
+    cancel_requested: bool = False
 
     @property
     def pairs(self) -> int:
@@ -92,6 +93,7 @@ class Server:
         self.waiting: List[Round] = []
         self.active: List[Round] = []
         self.done: List[Round] = []
+        self.cancelled: List[Round] = []
         self.used = 0.0
         self.stats = {"distance_batches": 0, "rounds_batched": 0, "aggregate_batches": 0, "max_used": 0.0}
         self.t0 = time.perf_counter()
@@ -107,6 +109,33 @@ class Server:
 
     def submit(self, r: Round):
         self.waiting.append(r)
+
+    def cancel(self, rid: int) -> bool:
+        """Cancels round `rid`: a waiting round leaves the queue at once; an admitted round is
+        dropped at its next phase boundary (a batch already on the GPU is not interrupted) and
+        its device buffers and budget are released.  False if the round is unknown or done."""
+        for r in self.waiting:
+            if r.rid == rid:
+                self.waiting.remove(r)
+                r.state = CANCELLED
+                self.cancelled.append(r)
+                return True
+        for r in self.active:
+            if r.rid == rid:
+                r.cancel_requested = True
+                return True
+        return False
+
+    def _drop_cancelled(self):
+        for r in [r for r in self.active if r.cancel_requested]:
+            self.active.remove(r)
+            self.used -= self.footprint(r)
+            r.state = CANCELLED
+            r.cts = None
+            r.device_kgc = None
+            if r.job is not None:
+                r.job.cts = r.job.masks = r.job.out_dist = r.job.out_agg = None
+            self.cancelled.append(r)
 
     # ------------------------------------------------------------------ scheduling
     def _admit(self):
@@ -170,6 +199,7 @@ class Server:
 
     def tick(self) -> bool:
         """One scheduler step; returns False when there was nothing to run."""
+        self._drop_cancelled()
         self._admit()
         dist = [r for r in self.active if r.state == DIST]
         agg = [r for r in self.active if r.state == AGG]

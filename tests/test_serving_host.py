@@ -154,3 +154,24 @@ def test_latency_summary():
     assert s["rounds"] == 4 and s["pairs"] == 40
     assert s["p50_ms"] == pytest.approx(250.0)
     assert s["p99_ms"] == pytest.approx(397.0)
+
+
+def test_cancelled_rounds_leave_and_release_their_budget(fake_lib):
+    srv, one = _server(budget_rounds=1)
+    _tag_jobs(srv)
+    for i in range(4):
+        srv.submit(SV.Round(i, 0, 10, 64, 0.0))
+    assert srv.cancel(2)                       # waiting: leaves the queue at once
+    assert [r.rid for r in srv.waiting] == [0, 1, 3]
+    srv.tick()                                 # round 0: distances + KGC
+    assert srv.cancel(0)                       # admitted: dropped at the next phase boundary
+    srv.tick()
+    assert fake_lib["agg"] == []               # round 0 never aggregated
+    assert fake_lib["dist"][1] == [1]          # its budget went to the next round
+    assert not srv.cancel(0) and not srv.cancel(99)
+    while srv.tick():
+        pass
+    assert [r.rid for r in srv.done] == [1, 3]
+    assert sorted(r.rid for r in srv.cancelled) == [0, 2]
+    assert all(r.state == SV.CANCELLED for r in srv.cancelled)
+    assert srv.used == pytest.approx(0.0)
