@@ -372,7 +372,8 @@ int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count,
  * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits), optionally | LC_HOIST_QP_SUM.
  * groups: hoisting schedule as in
  * lc_rotate_sum (NULL = all ones).  evk must hold the relinearisation key and every
- * rotation key the schedule needs. */
+ * rotation key the schedule needs (else LC_EKEY); a scale that is not finite and positive is
+ * LC_ESCALE. */
 int lc_distances(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks, double scale,
                  uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale);
 
@@ -380,7 +381,8 @@ int lc_distances(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n
  * out[k] = rescale(relin(sum_i ct_i[k] (x) M_i)), M_i the mask ciphertext of client i
  * (its selection weight in every slot, Section "Masked-based Encrypted Sorting").
  * cts: host or device [n][chunks][2][n_q][N]; masks: host or device [n][2][n_q][N];
- * out: host or device [chunks][2][n_q-1][N]; *out_scale = scale * mask_scale / q_L. */
+ * out: host or device [chunks][2][n_q-1][N]; *out_scale = scale * mask_scale / q_L.  Scales
+ * that are not finite and positive are LC_ESCALE. */
 int lc_masked_aggregate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* cts, uint32_t n, uint32_t chunks,
                         double scale, const uint64_t* masks, double mask_scale, uint32_t mode, uint64_t* out,
                         double* out_scale);

@@ -1687,6 +1687,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
                  uint32_t mode, uint32_t n_groups, const uint32_t* groups, uint64_t* out, double* out_scale) {
     clear_prior_error();
     if (!c || !evk || !cts || !out || n < 2 || chunks == 0) return fail(c, LC_EINVAL, "lc_distances: bad argument");
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, LC_ESCALE, "lc_distances: scale must be finite and > 0");
     const int L = c->nq - 1;
     const size_t N = c->N;
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
@@ -2057,6 +2058,8 @@ int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint3
     clear_prior_error();
     if (!c || !evk || !cts || !masks || !out || n == 0 || chunks == 0)
         return fail(c, LC_EINVAL, "lc_masked_aggregate: bad argument");
+    if (!(scale > 0.0) || !std::isfinite(scale) || !(mask_scale > 0.0) || !std::isfinite(mask_scale))
+        return fail(c, LC_ESCALE, "lc_masked_aggregate: scales must be finite and > 0");
     const int L = c->nq - 1;
     const size_t N = c->N;
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;

@@ -395,6 +395,11 @@ def test_edge_cases(toy):
         toy.g.distances(empty, gcs, 4, 1, toy.prm.scale)
     with pytest.raises(LC.LancelotError):
         toy.g.distances(toy.gevk, gcs, 4, 1, toy.prm.scale, groups=[1, 1])  # does not cover all slots
+    for bad in (0.0, -1.0, float("nan"), float("inf")):  # malformed scale
+        with pytest.raises(LC.LancelotError, match="LC_ESCALE"):
+            toy.g.distances(toy.gevk, gcs, 4, 1, bad)
+        with pytest.raises(LC.LancelotError, match="LC_ESCALE"):
+            toy.g.masked_aggregate(toy.gevk, gcs, 4, 1, toy.prm.scale, gcs[:, 0].contiguous(), bad)
 
 
 def _job_inputs(env, keys, w, seed_client0):
