@@ -6,10 +6,13 @@ sizes g trade key memory for fewer ModUp/ModDown rounds).  `tune` times one work
 context's stream with CUDA events and keeps, by coordinate descent, the fastest schedule and then
 the fastest option of each knob in turn, leaving the context set to the winner.  Candidate
 schedules are those whose rotation keys are loaded in `evk` and whose key set fits
-`key_budget_bytes`.
+`key_budget_bytes`.  Results can be kept in a JSON cache file keyed by GPU model and workload
+shape, so that a server tunes once per shape.
 """
 from __future__ import annotations
 
+import json
+import os
 import statistics
 from typing import Dict, List, Optional, Sequence
 
@@ -48,11 +51,24 @@ def _time_ms(ctx: "LC.Context", fn, reps: int) -> float:
     return statistics.median(ev[k].elapsed_time(ev[k + 1]) for k in range(reps))
 
 
+def cache_key(ctx: "LC.Context", n: int, chunks: int, candidates: Sequence[str], device: Optional[str] = None) -> str:
+    """Key of one tuned workload shape: the GPU model, the ring degree, clients, chunks and the
+    candidate schedules considered."""
+    if device is None:
+        device = torch.cuda.get_device_name(getattr(ctx, "device", 0)) if torch.cuda.is_available() else "cpu"
+    return f"{device}|log_n={ctx.log_n}|n={n}|chunks={chunks}|schedules={','.join(sorted(candidates))}"
+
+
 def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunks: int, scale: float,
          reps: int = 3, schedules: Optional[Dict[str, Sequence[int]]] = None,
-         key_budget_bytes: Optional[float] = None, out: Optional[torch.Tensor] = None) -> dict:
+         key_budget_bytes: Optional[float] = None, out: Optional[torch.Tensor] = None,
+         cache_path: Optional[str] = None, device: Optional[str] = None) -> dict:
     """Returns {"schedule", "groups", "mode", "knobs", "ms", "trials"}; the context keeps the
-    chosen knob settings (the schedule is an argument of each distances call)."""
+    chosen knob settings (the schedule is an argument of each distances call).
+
+    cache_path: a JSON file of earlier results keyed by `cache_key`; a hit sets the cached knobs
+    and returns the cached result (with "cached": True) without timing anything, a miss tunes and
+    adds the result to the file."""
     have = set(evk.rotations)
     cands = {}
     for name, sched in (schedules or candidate_schedules(ctx.log_n)).items():
@@ -64,6 +80,17 @@ def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunk
         cands[name] = list(sched)
     if not cands:
         raise LC.LancelotError("autotune: no candidate schedule has all its rotation keys loaded")
+    key = cache_key(ctx, n, chunks, list(cands), device) if cache_path else None
+    if key:
+        cache = _load_cache(cache_path)
+        hit = cache.get(key)
+        if hit and hit.get("schedule") in cands:
+            names = {v: k for k, v in LC.TUNING_NAMES.items()}
+            for name, v in hit["knobs"].items():
+                if name in names and v in LC.TUNING_OPTIONS[names[name]]:
+                    ctx.set_tuning(names[name], v)
+            return dict(hit, groups=cands[hit["schedule"]], mode=schedule_mode(hit["schedule"]),
+                        knobs=ctx.tuning(), cached=True)
     if out is None:
         out = ctx.empty(n * (n - 1) // 2, 2, ctx.L, ctx.N)
     trials = []
@@ -87,5 +114,22 @@ def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunk
         pick = min(times, key=times.get)
         ctx.set_tuning(knob, pick)
         best_ms = min(best_ms, times[pick])
-    return {"schedule": best, "groups": cands[best], "mode": schedule_mode(best), "knobs": ctx.tuning(),
-            "ms": best_ms, "trials": trials}
+    res = {"schedule": best, "groups": cands[best], "mode": schedule_mode(best), "knobs": ctx.tuning(),
+           "ms": best_ms, "trials": trials}
+    if key:
+        cache = _load_cache(cache_path)
+        cache[key] = {"schedule": best, "knobs": res["knobs"], "ms": best_ms, "trials": trials}
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return res
+
+
+def _load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}

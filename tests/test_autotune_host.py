@@ -90,3 +90,21 @@ def test_candidates_need_their_keys_and_fit_the_budget(model):
     assert res["schedule"] == "log"
     with pytest.raises(LC.LancelotError):
         autotune.tune(FakeCtx(), FakeEvk([1, 2]), None, 10, 64, 1.0)
+
+
+def test_cache_file_reuses_a_tuned_shape(model, tmp_path):
+    path = str(tmp_path / "tune.json")
+    ctx = FakeCtx()
+    first = autotune.tune(ctx, FakeEvk(_all_rots()), None, 10, 64, 1.0, cache_path=path, device="B300")
+    assert "cached" not in first
+    n_calls = len(ctx.calls)
+    ctx2 = FakeCtx()
+    again = autotune.tune(ctx2, FakeEvk(_all_rots()), None, 10, 64, 1.0, cache_path=path, device="B300")
+    assert again["cached"] and ctx2.calls == []          # nothing timed
+    assert again["schedule"] == first["schedule"] and again["groups"] == first["groups"]
+    assert ctx2.tuning() == first["knobs"]               # the context got the cached knobs
+    other = autotune.tune(FakeCtx(), FakeEvk(_all_rots()), None, 10, 32, 1.0, cache_path=path, device="B300")
+    assert "cached" not in other                         # another shape is tuned and added
+    import json
+    assert len(json.load(open(path))) == 2
+    assert n_calls > 0
