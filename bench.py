@@ -294,6 +294,9 @@ def run_probes(args):
 # (lazy Shoup Cooley-Tukey, twiddles in registers, no memory traffic) on every SM, live in the same
 # run at the same clock.  The IMAD probe checks the unit count behind it: 148 SMs x 64 32-bit
 # multiply-adds per clock x 2.03 GHz = 19.2 T/s nominal, 19.2 T/s measured on a B300.
+BFLY_INSTR = 21.65  # thread instructions per lazy butterfly of the register-resident probe (ncu)
+
+
 def alu_roofline(g, ntt_bytes: float, ntt_ms: float, sm_mhz):
     """NTT butterflies/s against the live register-resident probe of the same butterfly."""
     probes = {}
@@ -305,9 +308,15 @@ def alu_roofline(g, ntt_bytes: float, ntt_ms: float, sm_mhz):
     achieved = bfly / (ntt_ms / 1e3) / 1e12 if ntt_ms > 0 else 0.0
     peak = probes["ntt_butterfly"]["T_ops_per_s"]
     mhz = sm_mhz or 2032.0
+    # the nominal view beside it: 148 SMs x 4 schedulers x 32 lanes issue one instruction per clock;
+    # the lazy butterfly is BFLY_INSTR thread instructions (ncu count of the probe), so issue
+    # alone would allow this many butterflies per second (the probe sustains ~0.58 of it: the mix
+    # saturates the integer pipes first)
+    issue_bfly = 148 * 4 * 32 * mhz * 1e6 / BFLY_INSTR / 1e12
     return {"achieved": achieved, "peak": peak, "unit": "T butterflies/s", "frac": achieved / peak,
             "peak_source": "register-resident butterfly probe of the same code, measured live (lc_alu_probe)",
             "butterflies": bfly, "imad_nominal_T_per_s": 148 * 64 * mhz * 1e6 / 1e12, "sm_mhz": mhz,
+            "issue_bound_T_butterflies_per_s": issue_bfly, "frac_of_issue_bound": achieved / issue_bfly,
             "probes": probes}
 
 
