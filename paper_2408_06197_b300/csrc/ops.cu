@@ -783,6 +783,7 @@ __global__ void __launch_bounds__(kT) k_modup(const u64* __restrict__ coef, size
     }
     u64* eb = ext + ((size_t)b * beta + j) * rows * N + x;
     const int nd = tab.n_dst;
+#pragma unroll 2
     for (int t = 0; t < nd; t++) {
         u128v a0{0, 0}, a1{0, 0};
 #pragma unroll
@@ -1089,6 +1090,7 @@ __global__ void __launch_bounds__(kT) k_moddown_bconv(const u64* __restrict__ v,
         negm |= (y1[k] > (p >> 1) ? 2u : 0u) << (2 * k);
     }
     u64* cb = conv + (size_t)bk * nl * N + x;
+#pragma unroll 2
     for (int i = 0; i < nl; i++) {
         u128v a0{0, 0}, a1{0, 0};
 #pragma unroll
