@@ -25,7 +25,12 @@
  *  - Scales are tracked by the caller (double); each evaluation call documents the
  *    resulting scale.
  *  - Randomness (secret, errors, uniform "a" polynomials, encryption ephemerals) is supplied
- *    by the caller, so that results are reproducible bit for bit.
+ *    by the caller, so that results are reproducible bit for bit; the seeded calls
+ *    (lc_sample_enc, lc_encrypt_seeded, ...) instead draw it on the device from a seed
+ *    (Philox4x64-10), equally reproducible.
+ *  - Host transfers may use the wire form (lc_pack / lc_unpack: each residue in as many bytes
+ *    as its prime needs).  Device waits are bounded; one that runs out is reported by the next
+ *    lc_sync as LC_ETIMEOUT.
  */
 #ifndef LANCELOT_H
 #define LANCELOT_H
