@@ -343,11 +343,15 @@ int lc_rescale(lc_ctx* ctx, const uint64_t* ct, uint32_t count, uint32_t deg, ui
  * that cannot allocate at that point: a process whose device-memory budget is fully committed
  * at start-up, code running while its allocator must not be entered, or latency-sensitive
  * paths that cannot take the device synchronisation cudaMalloc / cudaFree can cause.
- *  - Calls no cudaMalloc, cudaFree or allocating routine.  Every GPU that loads the library
- *    holds the array until the process exits.
+ *  - Calls no cudaMalloc, cudaFree or allocating routine, and creates no CUDA event (the call
+ *    is left out of lc_profile's per-class timing).  Every GPU that loads the library holds the
+ *    array until the process exits.
+ *  - Launch failures are returned as LC_ECUDA by this call itself (as lc_rescale does), and a
+ *    non-sticky error left by earlier unrelated code is cleared on entry.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *    with that device made current for the look-up); make that first call before any stream
- *    capture.
+ *    capture.  The address is kept for the life of the process: after cudaDeviceReset on that
+ *    device (which also invalidates its contexts) do not call this entry point there again.
  *  - A request needing more than 16 MiB of scratch (count * deg * N * (level+1) words) is
  *    rejected with LC_EINVAL and a message in lc_last_error; split it into smaller calls.
  *  - All calls in the process share the one array and leave their last contents in it (nothing

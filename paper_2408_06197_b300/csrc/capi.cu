@@ -36,6 +36,8 @@ int fail(lc_ctx* c, int code, const std::string& msg) {
         if (e_ != cudaSuccess) return fail((c), LC_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
+}  // namespace
+
 int check_launch(lc_ctx* c, const char* what) {
     if (c && !c->debug_err.empty()) {
         std::string m = c->debug_err;
@@ -51,6 +53,8 @@ int check_launch(lc_ctx* c, const char* what) {
 // An entry point reports only errors of its own launches: clear a non-sticky error left by other
 // code on this thread (a sticky device fault stays and is reported by the launches).
 void clear_prior_error() { cudaGetLastError(); }
+
+namespace {
 
 RowMap rows_seq(int n, int mod0 = 0, int row0 = 0) {
     RowMap m{};

@@ -138,6 +138,11 @@ void* lc_dev_alloc(lc_ctx* c, size_t bytes);
 void lc_dev_free(lc_ctx* c, void* p);
 // scratch arena of at least `bytes` (grows; contents not preserved across growth)
 u64* lc_scratch(lc_ctx* c, size_t bytes);
+// status of the launches an entry point just made: the first launch failure recorded in a debug
+// context, else cudaGetLastError (LC_OK or LC_ECUDA, message in c->err)
+int check_launch(lc_ctx* c, const char* what);
+// clears a non-sticky error left on this thread by code outside the library
+void clear_prior_error();
 // rescale of B ciphertexts using caller-provided scratch `tmp` of rescale_words() words
 size_t rescale_words(lc_ctx* c, int B, int deg, int level);
 void do_rescale(lc_ctx* c, const u64* ct, int B, int deg, int level, u64* out, u64* tmp);

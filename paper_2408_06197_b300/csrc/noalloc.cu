@@ -19,12 +19,16 @@ static __device__ __align__(256) u64 lc_noalloc_scratch[LC_NOALLOC_SCRATCH_WORDS
 
 namespace {
 std::mutex g_mu;
-u64* g_addr[64] = {nullptr};  // device address of the array, per device ordinal
+// Device address of the array, per device ordinal, looked up once.  It stays valid for the
+// life of the device's primary context; after cudaDeviceReset (which also invalidates every
+// lc_ctx on that device) a process must not call lc_rescale_noalloc on that device again.
+u64* g_addr[64] = {nullptr};
 }  // namespace
 
 extern "C" int lc_rescale_noalloc(lc_ctx* c, const uint64_t* ct, uint32_t count, uint32_t deg, uint32_t level,
                                   uint64_t* out) {
     if (!c) return LC_EINVAL;
+    clear_prior_error();
     if (!ct || !out || level < 1 || (int)level >= c->nq || deg < 1 || deg > 3) {
         c->err = "lc_rescale_noalloc: bad argument";
         return LC_EINVAL;
@@ -70,12 +74,11 @@ extern "C" int lc_rescale_noalloc(lc_ctx* c, const uint64_t* ct, uint32_t count,
         scratch = g_addr[c->device];
     }
     // nothing in the scratch must start at zero: the last-limb copy and the reduced residues are
-    // fully written before they are read
+    // fully written before they are read.  Per-class timing (lc_profile) is skipped for this
+    // call: recording it can create CUDA events, and this entry point creates nothing.
+    const bool prof = c->prof_on;
+    c->prof_on = false;
     do_rescale(c, ct, (int)count, (int)deg, (int)level, out, scratch);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        c->err = std::string("lc_rescale_noalloc: ") + cudaGetErrorString(e);
-        return LC_ECUDA;
-    }
-    return LC_OK;
+    c->prof_on = prof;
+    return check_launch(c, "lc_rescale_noalloc");
 }
