@@ -425,6 +425,114 @@ int lc_batch_distances(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs, uint32_
  * job alone. */
 int lc_batch_aggregate(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs);
 
+/* ---------------------------------------------------------------- handles (level / scale tracked) */
+
+/* The calls above take plain arrays whose level and scale the caller tracks.  The calls below
+ * follow the roles of the paper's problem statement (Fig. 1 and Algorithm 1: the KGC generates
+ * keys and decrypts, clients encrypt, the server evaluates with the evaluation keys only) with
+ * handles that carry this metadata, so that a ciphertext at the wrong level or scale is rejected
+ * (LC_ELEVEL / LC_ESCALE) instead of computed on.  They run the same kernels as the array calls
+ * and give the same bits.  Every handle belongs to one context and must be freed before it. */
+
+/* A device-resident array of `count` ciphertexts of one degree (number of polynomials, 1..3),
+ * level and scale: device words [count][deg][level+1][N] in the evaluation domain. */
+typedef struct lc_ct lc_ct;
+/* The KGC's secret key (a host copy of the ternary secret) and the public key (device). */
+typedef struct lc_sk lc_sk;
+typedef struct lc_pk lc_pk;
+
+/* A handle of `count` ciphertexts, all words zero (valid residues).  LC_ELEVEL for level > L,
+ * LC_ESCALE for a scale that is not finite and positive. */
+int lc_ct_create(lc_ctx* ctx, uint32_t count, uint32_t deg, uint32_t level, double scale, lc_ct** out);
+/* Imports ciphertexts given in the canonical interchange form: host uint64
+ * [count][deg][level+1][N], COEFFICIENT domain, every residue below its prime (else LC_EINVAL,
+ * checked on the host before anything is copied).  Synchronous. */
+int lc_ct_import(lc_ctx* ctx, const uint64_t* coeffs, uint32_t count, uint32_t deg, uint32_t level, double scale,
+                 lc_ct** out);
+/* Exports a handle in that form into host coeffs[count][deg][level+1][N], and its level and
+ * scale (either may be NULL).  Synchronous. */
+int lc_ct_export(const lc_ct* ct, uint64_t* coeffs, uint32_t* level, double* scale);
+/* Metadata of a handle (any output may be NULL). */
+int lc_ct_info(const lc_ct* ct, uint32_t* count, uint32_t* deg, uint32_t* level, double* scale);
+/* The handle's device words (evaluation domain), for use with the array calls; NULL for NULL. */
+uint64_t* lc_ct_data(const lc_ct* ct);
+/* A handle on ciphertexts first .. first+count-1 of `ct`, sharing its memory (the memory lives
+ * until the last handle on it is freed).  Views of one handle in order are contiguous, so the
+ * evaluation calls use them without copying; other handle sets are gathered first. */
+int lc_ct_view(const lc_ct* ct, uint32_t first, uint32_t count, lc_ct** out);
+void lc_ct_free(lc_ct* ct);
+
+/* Randomness of key generation, supplied by the caller (host arrays):
+ *   pk_a  [n_q][N]  uniform residues (coefficient domain), pk_e [N] errors;
+ *   swk_a [1 + n_rot][dnum][n_q + n_p][N], swk_e [1 + n_rot][dnum][N]: the relinearisation key's
+ *         first, then one per rotation step in rot_steps order. */
+typedef struct {
+    const uint64_t* pk_a;
+    const int32_t* pk_e;
+    const uint64_t* swk_a;
+    const int32_t* swk_e;
+} lc_keygen_rand;
+/* KeyGen (Section "CKKS Scheme Description"; the KGC of Fig. 1): from the ternary secret s
+ * (host int8[N]) makes the secret-key handle, the public key ([-a s + e]_Q, a) and the
+ * evaluation keys -- the relinearisation key and one rotation key per step in rot_steps[n_rot]
+ * (left rotation by that many slots, 1 <= step < N/2, no repeats) -- exactly as lc_pk_gen and
+ * lc_evk_add make them.  Any of sk, pk, evk may be NULL to skip it (not all three).
+ * Synchronous.  Free with lc_sk_free, lc_pk_free, lc_evk_free. */
+int lc_keygen(lc_ctx* ctx, const int8_t* s, const lc_keygen_rand* rand, const int32_t* rot_steps, uint32_t n_rot,
+              lc_sk** sk, lc_pk** pk, lc_evk** evk);
+void lc_sk_free(lc_sk* sk);
+void lc_pk_free(lc_pk* pk);
+
+/* Encryption randomness (host arrays [count][N]): r ternary, e0 and e1 errors. */
+typedef struct {
+    const int8_t* r;
+    const int32_t* e0;
+    const int32_t* e1;
+} lc_enc_rand;
+/* Enc of `count` integer plaintexts m (host int64[count][N]) at level L with the given scale,
+ * as lc_encrypt; the new handle has degree 2, level L.  Synchronous. */
+int lc_encrypt_plain(lc_ctx* ctx, const lc_pk* pk, const int64_t* m, uint32_t count, double scale,
+                     const lc_enc_rand* rand, lc_ct** out);
+/* Encode + Enc of real values[len] (host), N/2 slots per ciphertext, the last one zero padded:
+ * ceil(len / (N/2)) ciphertexts (rand holds that many rows). */
+int lc_encrypt_values(lc_ctx* ctx, const lc_pk* pk, const double* values, size_t len, double scale,
+                      const lc_enc_rand* rand, lc_ct** out);
+/* Dec + Decode of every ciphertext of a handle with its own level and scale: out[len] (host)
+ * receives the N/2 slot values of ciphertext 0, then of ciphertext 1, ... up to len values. */
+int lc_decrypt_values(lc_ctx* ctx, const lc_sk* sk, const lc_ct* ct, double* out, size_t len);
+
+/* Encrypted pairwise squared distances (Algorithm 1, "Server Executes") on handles:
+ * clients[n], clients[i] holding client i's chunks (count = chunks, the same for every client),
+ * each of degree 2 at level L (else LC_ELEVEL) with one common scale (else LC_ESCALE).
+ * *out = a new handle of n(n-1)/2 ciphertexts (pairs i<j lexicographic) at level L-1 with scale
+ * scale^2 / q_L.  mode, n_groups, groups as in lc_distances. */
+int lc_ct_distances(lc_ctx* ctx, const lc_evk* evk, const lc_ct* const* clients, uint32_t n, uint32_t mode,
+                    uint32_t n_groups, const uint32_t* groups, lc_ct** out);
+/* Masked aggregate (Algorithm 1, "ServerUpdate") on handles: clients as above; masks[n] one
+ * ciphertext each at level L with one common scale.  *out = a new handle of `chunks`
+ * ciphertexts at level L-1, scale = scale * mask scale / q_L. */
+int lc_ct_masked_aggregate(lc_ctx* ctx, const lc_evk* evk, const lc_ct* const* clients, uint32_t n,
+                           const lc_ct* const* masks, uint32_t mode, lc_ct** out);
+
+/* One round of one tenant for lc_batch_run: inputs as in lc_ct_distances / lc_ct_masked_aggregate
+ * (masks may be NULL: no aggregate; want_dist = 0: no distances), outputs set by the call. */
+typedef struct {
+    const lc_evk* evk;
+    const lc_ct* const* clients;
+    uint32_t n;
+    const lc_ct* const* masks;
+    uint32_t want_dist;
+    lc_ct* dist; /* out: n(n-1)/2 distance ciphertexts (NULL if not asked) */
+    lc_ct* agg;  /* out: chunks aggregate ciphertexts (NULL without masks) */
+} lc_ct_job;
+/* Several rounds at once (the uneven multi-job batch): validates every job's handles first
+ * (nothing runs if one is malformed), then runs the distances of all jobs through
+ * lc_batch_distances and the aggregates through lc_batch_aggregate; flags, n_groups, groups as
+ * there.  Each job's results are bit-identical to the same job run alone.  On failure no output
+ * handle is left set. */
+int lc_batch_run(lc_ctx* ctx, lc_ct_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t n_groups,
+                 const uint32_t* groups);
+
 #ifdef __cplusplus
 }
 #endif

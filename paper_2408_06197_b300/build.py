@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblancelot.so")
-SOURCES = ["ntt.cu", "ops.cu", "capi.cu", "noalloc.cu", "probe.cu", "wire.cu"]
+SOURCES = ["ntt.cu", "ops.cu", "capi.cu", "handles.cu", "noalloc.cu", "probe.cu", "wire.cu"]
 HEADERS = ["modarith.cuh", "ntt.cuh", "ops.cuh", "context.cuh", "host_math.hpp", "tma.cuh", "probe.cuh", "wire.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

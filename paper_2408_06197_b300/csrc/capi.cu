@@ -704,6 +704,7 @@ void lc_ctx_destroy(lc_ctx* c) {
     lc_dev_free(c, c->rescale);
     lc_dev_free(c, c->scratch);
     lc_dev_free(c, c->stage);
+    lc_dev_free(c, c->gather);
     lc_dev_free(c, c->enc_pos);
     lc_dev_free(c, c->enc_w256);
     lc_dev_free(c, c->enc_wbig);

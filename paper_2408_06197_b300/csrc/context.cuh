@@ -96,6 +96,9 @@ struct lc_ctx {
     // staging for host buffers
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    // gathered ciphertext handles that are not contiguous (handle calls)
+    void* gather = nullptr;
+    size_t gather_bytes = 0;
     std::string err;
     uint64_t n_keyswitch = 0, n_modup = 0;
     uint32_t max_batch = 0;  // 0 = limited only by the scratch budget

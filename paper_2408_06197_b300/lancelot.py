@@ -92,6 +92,19 @@ class _Allocator(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", vp)]
 
 
+class _KeygenRand(ctypes.Structure):
+    _fields_ = [("pk_a", vp), ("pk_e", vp), ("swk_a", vp), ("swk_e", vp)]
+
+
+class _EncRand(ctypes.Structure):
+    _fields_ = [("r", vp), ("e0", vp), ("e1", vp)]
+
+
+class _CtJob(ctypes.Structure):
+    _fields_ = [("evk", vp), ("clients", vp), ("n", u32), ("masks", vp), ("want_dist", u32), ("dist", vp),
+                ("agg", vp)]
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
@@ -158,11 +171,29 @@ def lib() -> ctypes.CDLL:
             "lc_kgc_free": [vp],
             "lc_kgc_readout": [vp, vp, vp, u32, u32, ctypes.c_double, vp],
             "lc_kgc_krum": [vp, vp, u32, u32, u32, ctypes.c_int, vp, vp],
+            "lc_ct_create": [vp, u32, u32, u32, ctypes.c_double, vp],
+            "lc_ct_import": [vp, vp, u32, u32, u32, ctypes.c_double, vp],
+            "lc_ct_export": [vp, vp, vp, vp],
+            "lc_ct_info": [vp, vp, vp, vp, vp],
+            "lc_ct_view": [vp, u32, u32, vp],
+            "lc_ct_free": [vp],
+            "lc_keygen": [vp, vp, vp, vp, u32, vp, vp, vp],
+            "lc_sk_free": [vp],
+            "lc_pk_free": [vp],
+            "lc_encrypt_plain": [vp, vp, vp, u32, ctypes.c_double, vp, vp],
+            "lc_encrypt_values": [vp, vp, vp, ctypes.c_size_t, ctypes.c_double, vp, vp],
+            "lc_decrypt_values": [vp, vp, vp, vp, ctypes.c_size_t],
+            "lc_ct_distances": [vp, vp, vp, u32, u32, u32, vp, vp],
+            "lc_ct_masked_aggregate": [vp, vp, vp, u32, vp, u32, vp],
+            "lc_batch_run": [vp, vp, u32, u32, u32, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name in ("lc_ctx_destroy", "lc_evk_free", "lc_graph_free") else ctypes.c_int
+            f.restype = None if name in ("lc_ctx_destroy", "lc_evk_free", "lc_graph_free", "lc_ct_free",
+                                         "lc_sk_free", "lc_pk_free") else ctypes.c_int
+        L.lc_ct_data.argtypes = [vp]
+        L.lc_ct_data.restype = vp
         L.lc_last_error.argtypes = [vp]
         L.lc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -491,6 +522,117 @@ class Context:
     def evk(self) -> "EvalKeys":
         return EvalKeys(self)
 
+    # ------------------------------------------------------------------ handles (lc_ct, lc_keygen, ...)
+    def keygen(self, s: np.ndarray, pk_a: np.ndarray, pk_e: np.ndarray, rlk_rand, rot_rand: Dict[int, tuple]):
+        """lc_keygen: (SecretKey, PublicKey, EvalKeys) from the secret and the caller's randomness;
+        rlk_rand = (a, e) of the relinearisation key, rot_rand = {step: (a, e)}."""
+        steps = [int(r) for r in rot_rand]
+        sw_a = np.ascontiguousarray(np.stack([rlk_rand[0]] + [rot_rand[r][0] for r in steps]), np.uint64)
+        sw_e = np.ascontiguousarray(np.stack([rlk_rand[1]] + [rot_rand[r][1] for r in steps]), np.int32)
+        pa, pe = np.ascontiguousarray(pk_a, np.uint64), np.ascontiguousarray(pk_e, np.int32)
+        if sw_a.shape != (1 + len(steps), self.dnum, self.nq + self.np_, self.N) or pa.shape != (self.nq, self.N):
+            raise LancelotError("keygen: randomness of the wrong shape")
+        s8 = np.ascontiguousarray(s, np.int8)
+        if s8.size != self.N:
+            raise LancelotError("keygen: the secret must hold N values")
+        rnd = _KeygenRand(pa.ctypes.data, pe.ctypes.data, sw_a.ctypes.data, sw_e.ctypes.data)
+        rs = (ctypes.c_int32 * max(1, len(steps)))(*steps)
+        hs, hp, he = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(lib().lc_keygen(self.h, _np_ptr(s8), ctypes.byref(rnd), rs, len(steps), ctypes.byref(hs),
+                                    ctypes.byref(hp), ctypes.byref(he)), "lc_keygen")
+        evk = EvalKeys.__new__(EvalKeys)
+        evk.ctx, evk.h, evk.rotations = self, he, steps
+        self._deps.add(evk)
+        _LIVE.add(evk)
+        return SecretKey(self, hs), PublicKey(self, hp), evk
+
+    def ct_create(self, count: int, deg: int, level: int, scale: float) -> "Ciphertext":
+        h = ctypes.c_void_p()
+        self._check(lib().lc_ct_create(self.h, int(count), int(deg), int(level), float(scale), ctypes.byref(h)),
+                    "lc_ct_create")
+        return Ciphertext(self, h)
+
+    def ct_import(self, coeffs: np.ndarray, deg: int, level: int, scale: float) -> "Ciphertext":
+        """Ciphertexts in the canonical interchange form (coefficient domain, [count][deg][level+1][N])."""
+        a = np.ascontiguousarray(coeffs, np.uint64)
+        unit = deg * (level + 1) * self.N
+        if a.size == 0 or a.size % unit:
+            raise LancelotError(f"ct_import: {a.size} words is not a whole number of {unit}-word ciphertexts")
+        count = a.size // unit
+        h = ctypes.c_void_p()
+        self._check(lib().lc_ct_import(self.h, _np_ptr(a), count, int(deg), int(level), float(scale),
+                                       ctypes.byref(h)), "lc_ct_import")
+        return Ciphertext(self, h)
+
+    @staticmethod
+    def _enc_rand(count: int, N: int, r, e0, e1):
+        arrs = (np.ascontiguousarray(r, np.int8), np.ascontiguousarray(e0, np.int32), np.ascontiguousarray(e1, np.int32))
+        if any(x.size != count * N for x in arrs):
+            raise LancelotError(f"encryption randomness must hold {count} x N values each")
+        return arrs, _EncRand(*(x.ctypes.data for x in arrs))
+
+    def encrypt_plain(self, pk: "PublicKey", m: np.ndarray, scale: float, r, e0, e1) -> "Ciphertext":
+        mm = np.ascontiguousarray(m, np.int64).reshape(-1, self.N)
+        keep, rnd = self._enc_rand(mm.shape[0], self.N, r, e0, e1)
+        h = ctypes.c_void_p()
+        self._check(lib().lc_encrypt_plain(self.h, pk.h, _np_ptr(mm), mm.shape[0], float(scale), ctypes.byref(rnd),
+                                           ctypes.byref(h)), "lc_encrypt_plain")
+        return Ciphertext(self, h)
+
+    def encrypt_values(self, pk: "PublicKey", values: np.ndarray, scale: float, r, e0, e1) -> "Ciphertext":
+        v = np.ascontiguousarray(values, np.float64).reshape(-1)
+        count = -(-v.size // self.slots)
+        keep, rnd = self._enc_rand(count, self.N, r, e0, e1)
+        h = ctypes.c_void_p()
+        self._check(lib().lc_encrypt_values(self.h, pk.h, _np_ptr(v), v.size, float(scale), ctypes.byref(rnd),
+                                            ctypes.byref(h)), "lc_encrypt_values")
+        return Ciphertext(self, h)
+
+    def decrypt_values(self, sk: "SecretKey", ct: "Ciphertext", length: Optional[int] = None) -> np.ndarray:
+        n = ct.count * self.slots if length is None else int(length)
+        out = np.zeros(n, dtype=np.float64)
+        self._check(lib().lc_decrypt_values(self.h, sk.h, ct.h, _np_ptr(out), n), "lc_decrypt_values")
+        return out
+
+    @staticmethod
+    def _handles(cts: Sequence["Ciphertext"]):
+        return (ctypes.c_void_p * len(cts))(*[c.h.value if c is not None else None for c in cts])
+
+    def ct_distances(self, evk: "EvalKeys", clients: Sequence["Ciphertext"], mode: int = 1,
+                     groups: Optional[Sequence[int]] = None) -> "Ciphertext":
+        arr = self._handles(clients)
+        g = np.ascontiguousarray(groups if groups is not None else [], np.uint32)
+        h = ctypes.c_void_p()
+        self._check(lib().lc_ct_distances(self.h, evk.h, arr, len(clients), int(mode), g.size,
+                                          _np_ptr(g) if g.size else None, ctypes.byref(h)), "lc_ct_distances")
+        return Ciphertext(self, h)
+
+    def ct_masked_aggregate(self, evk: "EvalKeys", clients: Sequence["Ciphertext"], masks: Sequence["Ciphertext"],
+                            mode: int = 1) -> "Ciphertext":
+        arr, marr = self._handles(clients), self._handles(masks)
+        h = ctypes.c_void_p()
+        self._check(lib().lc_ct_masked_aggregate(self.h, evk.h, arr, len(clients), marr, int(mode), ctypes.byref(h)),
+                    "lc_ct_masked_aggregate")
+        return Ciphertext(self, h)
+
+    def batch_run(self, jobs: Sequence[dict], flags: int = 0, groups: Optional[Sequence[int]] = None):
+        """lc_batch_run over jobs {"evk", "clients", "masks" (optional), "distances" (bool)}:
+        returns [(dist Ciphertext or None, agg Ciphertext or None)] in job order."""
+        keep = []
+        cj = (_CtJob * max(1, len(jobs)))()
+        for k, j in enumerate(jobs):
+            arr = self._handles(j["clients"])
+            marr = self._handles(j["masks"]) if j.get("masks") is not None else None
+            keep.append((arr, marr))
+            cj[k] = _CtJob(j["evk"].h, ctypes.cast(arr, vp), len(j["clients"]),
+                           ctypes.cast(marr, vp) if marr is not None else None, int(bool(j.get("distances", True))),
+                           None, None)
+        g = np.ascontiguousarray(groups if groups is not None else [], np.uint32)
+        self._check(lib().lc_batch_run(self.h, cj, len(jobs), int(flags), g.size, _np_ptr(g) if g.size else None),
+                    "lc_batch_run")
+        return [(Ciphertext(self, ctypes.c_void_p(cj[k].dist)) if cj[k].dist else None,
+                 Ciphertext(self, ctypes.c_void_p(cj[k].agg)) if cj[k].agg else None) for k in range(len(jobs))]
+
     # ------------------------------------------------------------------ encode / encrypt / decrypt
     def encode(self, z: np.ndarray, scale: float) -> np.ndarray:
         z = np.ascontiguousarray(z, dtype=np.float64)
@@ -795,6 +937,87 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class _Handle:
+    """A library handle freed through its (live) context."""
+    _free = None
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        ctx._deps.add(self)
+        _LIVE.add(self)
+
+    def close(self):
+        if getattr(self, "h", None):
+            if getattr(self.ctx, "h", None) and self.h.value:
+                getattr(lib(), self._free)(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SecretKey(_Handle):
+    """lc_sk: the KGC's secret key."""
+    _free = "lc_sk_free"
+
+
+class PublicKey(_Handle):
+    """lc_pk: the public key the clients encrypt with."""
+    _free = "lc_pk_free"
+
+
+class Ciphertext(_Handle):
+    """lc_ct: a device-resident array of ciphertexts that carries its degree, level and scale."""
+    _free = "lc_ct_free"
+
+    def info(self):
+        c, d, l, sc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+        self.ctx._check(lib().lc_ct_info(self.h, ctypes.byref(c), ctypes.byref(d), ctypes.byref(l), ctypes.byref(sc)),
+                        "lc_ct_info")
+        return int(c.value), int(d.value), int(l.value), float(sc.value)
+
+    @property
+    def count(self) -> int:
+        return self.info()[0]
+
+    @property
+    def level(self) -> int:
+        return self.info()[2]
+
+    @property
+    def scale(self) -> float:
+        return self.info()[3]
+
+    def export(self) -> np.ndarray:
+        """[count][deg][level+1][N] in the coefficient domain (canonical interchange form)."""
+        count, deg, level, _ = self.info()
+        out = np.zeros((count, deg, level + 1, self.ctx.N), dtype=np.uint64)
+        self.ctx._check(lib().lc_ct_export(self.h, _np_ptr(out), None, None), "lc_ct_export")
+        return out
+
+    def view(self, first: int, count: int) -> "Ciphertext":
+        h = ctypes.c_void_p()
+        self.ctx._check(lib().lc_ct_view(self.h, int(first), int(count), ctypes.byref(h)), "lc_ct_view")
+        return Ciphertext(self.ctx, h)
+
+    def tensor(self) -> torch.Tensor:
+        """A torch view of the device words [count][deg][level+1][N] (evaluation domain) that
+        keeps this handle alive."""
+        count, deg, level, _ = self.info()
+        n = count * deg * (level + 1) * self.ctx.N
+        ptr = lib().lc_ct_data(self.h)
+
+        class _Arr:  # __cuda_array_interface__ over the handle's memory
+            __cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False), "version": 2,
+                                        "strides": None}
+        t = torch.as_tensor(_Arr(), device=f"cuda:{self.ctx.device}")
+        t._lc_owner = self
+        return t.view(count, deg, level + 1, self.ctx.N)
 
 
 class EvalKeys:

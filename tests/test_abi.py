@@ -84,3 +84,41 @@ def test_autotune_candidate_schedules_cover_every_rotation_bit():
             assert sum(sched) == log_n - 1
             assert len(LC.rotations_of_schedule(sched)) == sum((1 << g) - 1 for g in sched)
     assert autotune.candidate_schedules(15)["g3qp"] == [3, 3, 3, 3, 2]
+
+
+def test_handle_entry_points_reject_null_handles_without_gpu(lib):
+    """The handle layer validates its arguments on the host before any device work: a missing
+    context, handle or output is LC_EINVAL, and freeing a null handle is a no-op."""
+    vp, u32 = ctypes.c_void_p, ctypes.c_uint32
+    lib.lc_ct_info.argtypes = [vp] * 5
+    lib.lc_ct_export.argtypes = [vp] * 4
+    lib.lc_ct_view.argtypes = [vp, u32, u32, vp]
+    lib.lc_ct_create.argtypes = [vp, u32, u32, u32, ctypes.c_double, vp]
+    lib.lc_ct_import.argtypes = [vp, vp, u32, u32, u32, ctypes.c_double, vp]
+    lib.lc_keygen.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp]
+    lib.lc_encrypt_plain.argtypes = [vp, vp, vp, u32, ctypes.c_double, vp, vp]
+    lib.lc_ct_distances.argtypes = [vp, vp, vp, u32, u32, u32, vp, vp]
+    lib.lc_ct_masked_aggregate.argtypes = [vp, vp, vp, u32, vp, u32, vp]
+    lib.lc_batch_run.argtypes = [vp, vp, u32, u32, u32, vp]
+    lib.lc_decrypt_values.argtypes = [vp, vp, vp, vp, ctypes.c_size_t]
+    lib.lc_ct_data.argtypes = [vp]
+    lib.lc_ct_data.restype = vp
+    for f in ("lc_ct_free", "lc_sk_free", "lc_pk_free"):
+        getattr(lib, f).argtypes = [vp]
+        getattr(lib, f).restype = None
+    out = vp()
+    assert lib.lc_ct_info(None, None, None, None, None) == -1
+    assert lib.lc_ct_export(None, None, None, None) == -1
+    assert lib.lc_ct_view(None, 0, 1, ctypes.byref(out)) == -1
+    assert lib.lc_ct_create(None, 1, 2, 0, 1.0, ctypes.byref(out)) == -1
+    assert lib.lc_ct_import(None, None, 1, 2, 0, 1.0, ctypes.byref(out)) == -1
+    assert lib.lc_keygen(None, None, None, None, 0, None, None, None) == -1
+    assert lib.lc_encrypt_plain(None, None, None, 1, 1.0, None, ctypes.byref(out)) == -1
+    assert lib.lc_ct_distances(None, None, None, 2, 1, 0, None, ctypes.byref(out)) == -1
+    assert lib.lc_ct_masked_aggregate(None, None, None, 2, None, 1, ctypes.byref(out)) == -1
+    assert lib.lc_batch_run(None, None, 1, 0, 0, None) == -1
+    assert lib.lc_decrypt_values(None, None, None, None, 0) == -1
+    assert lib.lc_ct_data(None) is None
+    lib.lc_ct_free(None)
+    lib.lc_sk_free(None)
+    lib.lc_pk_free(None)

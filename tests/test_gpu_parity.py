@@ -542,8 +542,8 @@ def test_production_full_size_sampled(prod_g3):
 def test_batched_config_full_size_sampled(prod_g3):
     """The batched configuration at full size (n=50, d=2^22: 256 ciphertexts per client, 94 GB
     resident, 1,225 pairs in waves) in the benchmark's launch configuration: every pair's
-    read-out against FP64, Multi-Krum selection, and two sampled pairs bit-exact against the
-    oracle (an honest pair and an honest/noisy pair)."""
+    read-out against FP64, Multi-Krum selection, and 18 sampled pairs bit-exact against the
+    oracle (honest/honest, honest/noisy and noisy/noisy pairs)."""
     from paper_2408_06197_b300 import kgc
     e = prod_g3
     LC = e.LC
@@ -573,18 +573,104 @@ def test_batched_config_full_size_sampled(prod_g3):
             k += 1
     sel = kgc.krum_select(dist, w.f, w.n_select)
     assert sel == kgc.krum_select(sq, w.f, w.n_select) and not (set(sel) & set(w.byzantine))
-    pairs = [(2, 17), (5, 44)]
-    clients = sorted({c for p in pairs for c in p})
-    idx = {c: t for t, c in enumerate(clients)}
-    ocs = []
-    for c in clients:
-        m = plaintexts(e.o, e.prm, S.split_chunks(Ws[c], e.prm.slots))
-        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [c], range(chunks), e.N)
-        ocs.append(np.stack([e.o.encrypt(e.opk, m[k], r[k], e0[k], e1[k]) for k in range(chunks)]))
-    Do = e.o.distances(np.stack(ocs), e.orlk, G3QP, e.ork, pairs=[(idx[i], idx[j]) for i, j in pairs], qp_sum=True)
-    for t, (i, j) in enumerate(pairs):
-        p = i * n - i * (i + 1) // 2 + (j - i - 1)
-        assert np.array_equal(e.g_coeff(Dg[p].contiguous(), e.L - 1), e.o_coeff(Do[t]))
+    # 18 sampled pairs bit-exact: every pair inside three groups of four clients, spread over the
+    # client range, honest and noisy (40-49) -- a group at a time, so that the oracle holds the
+    # 256-chunk ciphertexts of four clients (8 GB) at most
+    compared = 0
+    for group in ((0, 3, 41, 45), (17, 29, 47, 49), (5, 12, 33, 44)):
+        ocs = []
+        for c in group:
+            m = plaintexts(e.o, e.prm, S.split_chunks(Ws[c], e.prm.slots))
+            r, e0, e1 = S.enc_rand_batch(w.seed, w.config, [c], range(chunks), e.N)
+            ocs.append(np.stack([e.o.encrypt(e.opk, m[k], r[k], e0[k], e1[k]) for k in range(chunks)]))
+        local = [(a, b) for a in range(4) for b in range(a + 1, 4)]
+        Do = e.o.distances(np.stack(ocs), e.orlk, G3QP, e.ork, pairs=local, qp_sum=True)
+        del ocs
+        for t, (a, b) in enumerate(local):
+            i, j = group[a], group[b]
+            p = i * n - i * (i + 1) // 2 + (j - i - 1)
+            assert np.array_equal(e.g_coeff(Dg[p].contiguous(), e.L - 1), e.o_coeff(Do[t]))
+            compared += 1
+    assert compared >= 16
+
+
+@pytest.fixture(scope="module")
+def prod_g2_b(prod_g2):
+    """A second tenant at production parameters: its own key set (seed 9) for the same [2]*7
+    schedule, on the same context as prod_g2."""
+    e = prod_g2
+    keys = KeySet(e.prm, 9, S.CFG_UNEVEN, O.rotations_of_schedule(e.sched))
+    opk, orlk, ork = keys.oracle_keys(e.o)
+    gpk, gevk = keys.gpu_keys(e.g)
+    return keys, opk, orlk, ork, gpk, gevk
+
+
+@pytest.mark.slow
+def test_uneven_batch_production_sampled_against_oracle(prod_g2, prod_g2_b):
+    """The uneven multi-job batch at production parameters (N = 2^15): three jobs of different
+    client counts and model sizes, two tenants with their own key sets, one-ModDown groups [2]*7,
+    through lc_batch_distances / lc_batch_aggregate with a wave cap that makes two jobs share
+    waves and one run on its own.  Every pair's read-out against FP64; two sampled pairs and one
+    aggregate chunk per job bit-exact against the oracle run with that job's keys."""
+    e = prod_g2
+    LC, g = e.LC, e.g
+    keys_b, opk_b, orlk_b, ork_b, gpk_b, gevk_b = prod_g2_b
+    tenants = {0: (e.keys, e.opk, e.orlk, e.ork, e.gpk, e.gevk), 1: (keys_b, opk_b, orlk_b, ork_b, gpk_b, gevk_b)}
+    specs = [(10, 3, 0), (5, 9, 1), (6, 2, 0)]  # (clients, chunks, tenant); d ragged
+    jobs, meta = [], []
+    for jid, (n, chunks, ten) in enumerate(specs):
+        keys, opk, orlk, ork, gpk, gevk = tenants[ten]
+        nb = max(1, n // 5)
+        w = S.Workload(f"up{jid}", S.CFG_UNEVEN, 15, n, chunks * e.prm.slots - 101, 2, tuple(range(n - nb, n)),
+                       "scale5", max(1, n - 2 * nb - 3), nb, job=jid)
+        W = S.client_updates(w)
+        X = S.split_chunks(W, e.prm.slots)
+        m = plaintexts(e.o, e.prm, X).reshape(n, chunks, e.N)
+        r, e0, e1 = S.enc_rand_batch(w.seed, w.config, range(n), range(chunks), e.N, job=jid)
+        cts = g.encrypt(gpk, m.reshape(-1, e.N), r, e0, e1).reshape(n, chunks, 2, e.L + 1, e.N)
+        wts = np.zeros(n)
+        wts[: n - nb] = 1.0 / (n - nb)
+        mm = plaintexts(e.o, e.prm, np.stack([np.full((1, e.prm.slots), wts[i]) for i in range(n)]))[:, 0]
+        rm, e0m, e1m = S.enc_rand_batch(w.seed, w.config, range(n), [S.MASK_CHUNK], e.N, job=jid)
+        masks = g.encrypt(gpk, mm, rm, e0m, e1m)
+        jobs.append(LC.Job(gevk, cts, n, chunks, masks))
+        meta.append((w, W, X, m, (r, e0, e1), mm, (rm, e0m, e1m), wts, ten))
+    g.set_max_batch(32)  # job 0 (45 pairs) runs alone; jobs 1 and 2 (10 + 15 pairs) share a wave
+    try:
+        LC.batch_distances(g, jobs, LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM, e.sched)
+        LC.batch_aggregate(g, jobs)
+    finally:
+        g.set_max_batch(0)
+    sc = e.prm.scale * e.prm.scale / e.prm.q[e.L]
+    for j, (w, W, X, m, (r, e0, e1), mm, (rm, e0m, e1m), wts, ten) in zip(jobs, meta):
+        keys, opk, orlk, ork, gpk, gevk = tenants[ten]
+        n, chunks = w.n_clients, w.chunks
+        got = g.decrypt_const(keys.s, j.out_dist, e.L - 1, sc)
+        k = 0
+        for a in range(n):
+            for b in range(a + 1, n):
+                ref = np.sum((W[a] - W[b]) ** 2)
+                assert abs(got[k] - ref) / ref < 1e-5
+                k += 1
+        sample = [(0, 1), (n - 3, n - 1)]
+        clients = sorted({c for p in sample for c in p})
+        idx = {c: t for t, c in enumerate(clients)}
+        ocs = np.stack([np.stack([e.o.encrypt(opk, m[c, k], r[c * chunks + k], e0[c * chunks + k],
+                                              e1[c * chunks + k]) for k in range(chunks)]) for c in clients])
+        Do = e.o.distances(ocs, orlk, e.sched, ork, pairs=[(idx[a], idx[b]) for a, b in sample], qp_sum=True)
+        for t, (a, b) in enumerate(sample):
+            p = a * n - a * (a + 1) // 2 + (b - a - 1)
+            assert np.array_equal(e.g_coeff(j.out_dist[p].contiguous(), e.L - 1), e.o_coeff(Do[t]))
+        kk = chunks - 1
+        ock = np.stack([e.o.encrypt(opk, m[c, kk], r[c * chunks + kk], e0[c * chunks + kk], e1[c * chunks + kk])
+                        for c in range(n)])[:, None]
+        om = np.stack([e.o.encrypt(opk, mm[i], rm[i], e0m[i], e1m[i]) for i in range(n)])
+        Ao = e.o.masked_aggregate(np.ascontiguousarray(ock), om, orlk)
+        assert np.array_equal(e.g_coeff(j.out_agg[kk].contiguous(), e.L - 1), e.o_coeff(Ao[0]))
+        asc = e.prm.scale * e.prm.scale / e.prm.q[e.L]
+        agg = np.concatenate([g.decrypt(keys.s, j.out_agg[c].contiguous(), e.L - 1, asc) for c in range(chunks)])
+        ref = sum(wts[i] * X[i].reshape(-1) for i in range(n))
+        assert np.linalg.norm(agg - ref) / np.linalg.norm(ref) < 1e-5
 
 
 def test_overlapped_copies_match_stream_ordered_copies(toy):
