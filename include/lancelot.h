@@ -215,6 +215,9 @@ void lc_graph_free(lc_graph* graph);
  * e: host int32[N]; pk_out: device uint64[2][n_q][N] (evaluation domain). */
 int lc_pk_gen(lc_ctx* ctx, const int8_t* s, const uint64_t* a, const int32_t* e, uint64_t* pk_out);
 
+/* An evaluation-key set belongs to the context that made it (free it before that context) and
+ * may be used by any context with the same device, ring degree and moduli, e.g. contexts on
+ * other streams; the evaluation calls reject keys of other parameters with LC_EINVAL. */
 int lc_evk_create(lc_ctx* ctx, lc_evk** out);
 void lc_evk_free(lc_evk* evk);
 /* Adds one switching key to evk (Key generation, Evaluation key; hybrid form with dnum
@@ -368,7 +371,8 @@ int lc_rotate(lc_ctx* ctx, const lc_evk* evk, const uint64_t* ct, uint32_t level
  * schedule: groups[n_groups] with sum = log2(N/2); group g with stride s does
  * y <- y + sum_{t=1}^{2^g-1} Rot_{t s}(y) from one ModUp, then s <- s 2^g.  All groups 1 is the
  * plain log-step sum.  Afterwards every slot holds the sum of all slots.  flags: 0 or
- * LC_HOIST_QP_SUM. */
+ * LC_HOIST_QP_SUM.  Group sizes: at most 8 bits, at most 4 (15 rotations) with LC_HOIST_QP_SUM
+ * (LC_EINVAL beyond). */
 int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count, uint32_t level, uint32_t n_groups,
                   const uint32_t* groups, uint32_t flags);
 
@@ -415,7 +419,7 @@ typedef struct {
  * together in batched waves (per-item key tables); a job with at least half a wave of pairs runs
  * on its own through the lc_distances path (keys shared by the launch) after them.  Each job's
  * results are bit-identical to lc_distances on that job alone with the same schedule.  flags: 0
- * or LC_HOIST_QP_SUM; groups as in lc_rotate_sum (sizes <= 3).  Synchronises the stream between
+ * or LC_HOIST_QP_SUM; groups as in lc_rotate_sum (sizes <= 4).  Synchronises the stream between
  * shared waves (descriptors are rewritten). */
 int lc_batch_distances(lc_ctx* ctx, const lc_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t n_groups,
                        const uint32_t* groups);

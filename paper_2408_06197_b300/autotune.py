@@ -21,14 +21,41 @@ import torch
 from . import lancelot as LC
 
 
-def candidate_schedules(log_n: int) -> Dict[str, List[int]]:
-    """log: one rotation per group (log2(N/2) groups); gKqp: groups of 2^K - 1 rotations with one
-    ModDown per group, the remainder in a last smaller group."""
+MAX_GROUP = 4  # the fused one-ModDown group kernel takes groups of up to 4 rotation bits (15 rotations)
+
+
+def _partitions(b: int, m: int):
+    """Non-increasing lists of positive integers <= m summing to b."""
+    if b == 0:
+        yield []
+        return
+    for p in range(min(b, m), 0, -1):
+        for rest in _partitions(b - p, p):
+            yield [p] + rest
+
+
+def candidate_schedules(log_n: int, max_group: int = MAX_GROUP) -> Dict[str, List[int]]:
+    """The unfoldings of the rotate-and-sum the search considers (Section "Dynamic Hoisting": how
+    many rotation bits each hoisted group takes): "log", one rotation per group with a ModDown per
+    rotation (log2(N/2) groups), and every composition of log2(N/2) into one-ModDown groups of at
+    most `max_group` bits, largest first, with at most one single-bit group (two single-bit groups
+    cost more than one group of two).  A group of g bits needs 2^g - 1 rotation keys.  The uniform
+    ones keep short names: g2qp = groups of 2, g3qp = groups of 3 (the remainder last); the others
+    are named by their group sizes, e.g. g4442qp."""
     b = log_n - 1
     out = {"log": [1] * b}
     for g in (2, 3):
         out[f"g{g}qp"] = [g] * (b // g) + ([b % g] if b % g else [])
+    for parts in _partitions(b, max_group):
+        if parts.count(1) > 1 or parts in out.values():
+            continue
+        out["g" + "".join(map(str, parts)) + "qp"] = parts
     return out
+
+
+def schedule_keys(sched: Sequence[int]) -> int:
+    """Rotation keys a schedule needs: 2^g - 1 per group."""
+    return sum((1 << g) - 1 for g in sched)
 
 
 def schedule_mode(name: str) -> int:
@@ -63,8 +90,9 @@ def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunk
          reps: int = 3, schedules: Optional[Dict[str, Sequence[int]]] = None,
          key_budget_bytes: Optional[float] = None, out: Optional[torch.Tensor] = None,
          cache_path: Optional[str] = None, device: Optional[str] = None) -> dict:
-    """Returns {"schedule", "groups", "mode", "knobs", "ms", "trials"}; the context keeps the
-    chosen knob settings (the schedule is an argument of each distances call).
+    """Returns {"schedule", "groups", "mode", "knobs", "ms", "trials", "schedules" (candidates
+    timed), "key_bytes" (device bytes of the winner's relinearisation + rotation keys)}; the
+    context keeps the chosen knob settings (the schedule is an argument of each distances call).
 
     cache_path: a JSON file of earlier results keyed by `cache_key`; a hit sets the cached knobs
     and returns the cached result (with "cached": True) without timing anything, a miss tunes and
@@ -115,7 +143,8 @@ def tune(ctx: "LC.Context", evk: "LC.EvalKeys", cts: torch.Tensor, n: int, chunk
         ctx.set_tuning(knob, pick)
         best_ms = min(best_ms, times[pick])
     res = {"schedule": best, "groups": cands[best], "mode": schedule_mode(best), "knobs": ctx.tuning(),
-           "ms": best_ms, "trials": trials}
+           "ms": best_ms, "trials": trials, "schedules": len(cands),
+           "key_bytes": key_bytes(ctx, len(set(LC.rotations_of_schedule(cands[best]))) + 1)}
     if key:
         cache = _load_cache(cache_path)
         cache[key] = {"schedule": best, "knobs": res["knobs"], "ms": best_ms, "trials": trials}

@@ -448,6 +448,14 @@ static const SwKey* find_key(const lc_evk* evk, int32_t id) {
     return it == evk->keys.end() ? nullptr : &it->second;
 }
 
+// A key set made on another context may be used when that context has the same device, ring
+// degree and moduli (its keys are plain device arrays in the same layout).
+static bool evk_usable(const lc_ctx* c, const lc_evk* evk) {
+    const lc_ctx* o = evk ? evk->ctx : nullptr;
+    return o && (o == c || (o->device == c->device && o->log_n == c->log_n && o->nq == c->nq && o->np == c->np &&
+                            o->dnum == c->dnum && o->mod == c->mod));
+}
+
 // relinearise B triples ct3 [B][3][nl][N] into out [B][2][nl][N] (tmp = ks scratch)
 static int do_relin(lc_ctx* c, const lc_evk* evk, const u64* ct3, int B, int level, u64* out, u64* tmp) {
     const SwKey* k = find_key(evk, -1);
@@ -525,7 +533,7 @@ static int do_rotate_sum(lc_ctx* c, const lc_evk* evk, u64* y, int B, int level,
             if (!keys[t - 1]) return fail(c, LC_EKEY, "rotation key " + std::to_string(t * stride) + " missing");
         }
         ks_modup(c, y + P, 2 * P, B, level, kb);
-        if (qp_sum && cnt > 1 && cnt <= 7) {  // the fused group kernel takes up to 7 rotations
+        if (qp_sum && cnt > 1) {  // the fused group kernel (groups of up to 4 bits: 15 rotations)
             const size_t vsz = (size_t)B * 2 * rows * N;
             u64* usum = wbase;      // [B][2][rows][N]
             u64* c0acc = usum + vsz;  // [B][nl][N]
@@ -1394,8 +1402,8 @@ int lc_rotate_sum(lc_ctx* c, const lc_evk* evk, uint64_t* cts, uint32_t count, u
     if (count == 0 || n_groups == 0) return LC_OK;
     int maxg = 1;
     for (uint32_t i = 0; i < n_groups; i++) maxg = std::max(maxg, (int)(groups ? groups[i] : 1));
-    if (maxg > 8) return fail(c, LC_EINVAL, "group too large");
     const bool qp = (flags & LC_HOIST_QP_SUM) != 0;
+    if (maxg > (qp ? 4 : 8)) return fail(c, LC_EINVAL, "group too large (one-ModDown groups: at most 4 bits)");
     u64* t = lc_scratch(c, rotsum_words(c, (int)count, (int)level, maxg, qp) * 8);
     if (!t) return fail(c, LC_ENOMEM, "scratch");
     int st = do_rotate_sum(c, evk, cts, (int)count, (int)level, (int)n_groups, groups, t, qp);
@@ -1712,7 +1720,8 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     }
     int maxg = 1;
     for (uint32_t g : sched) maxg = std::max(maxg, (int)g);
-    if (maxg > 8) return fail(c, LC_EINVAL, "group too large");
+    if (maxg > (qp ? 4 : 8)) return fail(c, LC_EINVAL, "group too large (one-ModDown groups: at most 4 bits)");
+    if (!evk_usable(c, evk)) return fail(c, LC_EINVAL, "evaluation keys of a context with other parameters");
     if (!find_key(evk, -1)) return fail(c, LC_EKEY, "relinearisation key missing");
     // host buffers are staged through device memory
     const bool in_host = is_host_ptr(cts), out_host = is_host_ptr(out);
@@ -1873,7 +1882,7 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
     }
     int maxg = 1;
     for (uint32_t g : sched) maxg = std::max(maxg, (int)g);
-    if (maxg > 3) return fail(c, LC_EINVAL, "batched groups are limited to size 3");
+    if (maxg > 4) return fail(c, LC_EINVAL, "batched groups are limited to size 4");
     const size_t rot_words = std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp),
                                               ks_words(c, 1, L - 1) + ((((size_t)1 << maxg) - 1) * 2 * (L + c->np) +
                                                                        (((size_t)1 << maxg) - 1) * 2 * L) * N);
@@ -1889,6 +1898,8 @@ int lc_batch_distances(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs, uint32_t 
     for (uint32_t jb = 0; jb < n_jobs; jb++) {
         const lc_job& J = jobs[jb];
         if (!job_ok(c, J, false)) return fail(c, LC_EINVAL, "lc_batch_distances: job " + std::to_string(jb) + " invalid");
+        if (!evk_usable(c, J.evk))
+            return fail(c, LC_EINVAL, "job " + std::to_string(jb) + ": evaluation keys of a context with other parameters");
         if (!find_key(J.evk, -1)) return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": relinearisation key missing");
         long stride = 1;
         for (uint32_t g : sched) {
@@ -2001,6 +2012,8 @@ int lc_batch_aggregate(lc_ctx* c, const lc_job* jobs, uint32_t n_jobs) {
     for (uint32_t jb = 0; jb < n_jobs; jb++) {
         const lc_job& J = jobs[jb];
         if (!job_ok(c, J, true)) return fail(c, LC_EINVAL, "lc_batch_aggregate: job " + std::to_string(jb) + " invalid");
+        if (!evk_usable(c, J.evk))
+            return fail(c, LC_EINVAL, "job " + std::to_string(jb) + ": evaluation keys of a context with other parameters");
         if (!find_key(J.evk, -1)) return fail(c, LC_EKEY, "job " + std::to_string(jb) + ": relinearisation key missing");
         if (J.chunks >= (uint32_t)std::max(1, Bcap / 2)) {
             alone.push_back(jb);
@@ -2068,6 +2081,7 @@ int lc_masked_aggregate(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint3
     const int L = c->nq - 1;
     const size_t N = c->N;
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
+    if (!evk_usable(c, evk)) return fail(c, LC_EINVAL, "evaluation keys of a context with other parameters");
     if (!find_key(evk, -1)) return fail(c, LC_EKEY, "relinearisation key missing");
     const bool in_host = is_host_ptr(cts), m_host = is_host_ptr(masks), out_host = is_host_ptr(out);
     const size_t in_words = (size_t)n * chunks * 2 * Pin, m_words = (size_t)n * 2 * Pin,

@@ -19,11 +19,12 @@ struct ModList {
     u64 val[LC_MAX_ROWS];
 };
 
+// up to 15 rotations of one hoisted group (groups of at most 4 rotation bits)
 struct KeyPtrs {
-    const u64* p[8];
+    const u64* p[16];
 };
 struct Galois {
-    uint64_t g[8];
+    uint64_t g[16];
 };
 
 ModList make_list(const int* mods, int n, const u64* vals = nullptr) {
@@ -1522,7 +1523,7 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
     const int nl = level + 1, rows = nl + c->np;
     KeyPtrs kp{};
     Galois g{};
-    for (int k = 0; k < T && k < 8; k++) {
+    for (int k = 0; k < T && k < 16; k++) {
         kp.p[k] = keys ? keys[k] : nullptr;
         g.g[k] = gs[k];
     }
@@ -1554,6 +1555,7 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
         case 5: LC_IG(5, SPL, BT, SEL, CNT); break; \
         case 6: LC_IG(6, SPL, BT, SEL, CNT); break; \
         case 7: LC_IG(7, SPL, BT, SEL, CNT); break; \
+        case 15: LC_IG(15, SPL, BT, SEL, CNT); break; \
         default: break;                            \
     }
     if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS

@@ -14,8 +14,16 @@ mask, and the server computes the masked aggregate.  The loop
   Multi-Krum on the host, encryption of the masks on the GPU) and times it separately;
 * keeps the tenants' evaluation keys resident for the whole run.
 
-Results of a round do not depend on which other rounds share its batches (exact integer
-arithmetic); tests/test_serving.py checks this.
+With the KGC step on the device a round needs no host round trip, and the loop runs
+asynchronously on lanes instead of ticks: a lane is a CUDA stream with its own library context;
+one batch per lane is in flight at a time, and it carries its rounds all the way (distances,
+read-out, selection, mask encryption, aggregate) before a CUDA event marks them done.  With two
+lanes -- small rounds on a high-priority stream, rounds above a pair cap on a low-priority one --
+a large round no longer holds back the small rounds that arrive while it runs: their batches
+launch at once and the GPU's block scheduler gives their blocks precedence.
+
+Results of a round do not depend on which other rounds share its batches or its lane (exact
+integer arithmetic; every context has the same tables); tests/test_serving.py checks this.
 """
 from __future__ import annotations
 
@@ -30,6 +38,30 @@ from . import kgc
 from . import lancelot as LC
 
 WAITING, DIST, AGG, DONE, CANCELLED = "waiting", "distances", "aggregate", "done", "cancelled"
+RUNNING = "running"  # lanes: the round's whole batch (distances .. aggregate) is on the GPU
+
+
+class Lane:
+    """A CUDA stream with its own library context (own scratch arena).  Batches on one lane run
+    one after another; batches on different lanes overlap on the device.  Rounds with at most
+    `max_pairs` pairs go to the first lane that takes them (None: any size)."""
+
+    def __init__(self, ctx: "LC.Context", max_pairs: Optional[int] = None, name: str = ""):
+        self.ctx, self.max_pairs, self.name = ctx, max_pairs, name
+        self.inflight = None  # (completion marker, rounds)
+        self.batches = 0
+
+    def stream(self):
+        return getattr(self.ctx, "stream", None)
+
+    def mark(self):
+        """A completion marker for the work enqueued on this lane so far (query() -> bool)."""
+        ev = torch.cuda.Event()
+        ev.record(self.ctx.stream)
+        return ev
+
+    def takes(self, r: "Round") -> bool:
+        return self.max_pairs is None or r.pairs <= self.max_pairs
 
 
 @dataclasses.dataclass
@@ -62,6 +94,7 @@ class Round:
     kgc_seconds: float = 0.0
     device_kgc: Optional[tuple] = None  # (read-out values, kept indices) on the device, until read back
     cancel_requested: bool = False
+    lane: int = 0                       # lanes: index of the lane that runs the round
 
     @property
     def pairs(self) -> int:
@@ -77,16 +110,22 @@ class Server:
                  ingest: Callable[[Round], torch.Tensor],
                  mask_rand: Callable[[Round, int], tuple],
                  groups: Optional[Sequence[int]] = None, flags: int = LC.LC_HOIST_QP_SUM,
-                 keep_outputs: bool = False, device_kgc_seed: Optional[int] = None):
+                 keep_outputs: bool = False, device_kgc_seed: Optional[int] = None,
+                 lanes: Optional[Sequence[Lane]] = None):
         """keep_outputs: keep each finished round's device buffers (distances, masks, aggregate) on
         its Job; otherwise they are released as soon as the round no longer needs them.
         device_kgc_seed: run the KGC step on the device (resident KGC keys, device read-out and
         Krum, masks encrypted with device randomness of this seed, ciphertext indices
-        rid * 2^20 + client) instead of on the host with `mask_rand`."""
+        rid * 2^20 + client) instead of on the host with `mask_rand`; run() then uses the
+        asynchronous lane pipeline.  lanes: the lanes of that pipeline (default: one lane on
+        `ctx`); the last lane must take rounds of any size."""
         self.ctx, self.tenants, self.budget = ctx, list(tenants), float(budget_bytes)
         self.keep = keep_outputs
         self.device_kgc_seed = device_kgc_seed
-        self._kgc_keys: Dict[int, "LC.KgcKey"] = {}
+        self.lanes = list(lanes) if lanes else [Lane(ctx, None, "main")]
+        if self.lanes[-1].max_pairs is not None:
+            raise ValueError("the last lane must take rounds of any size")
+        self._kgc_keys: Dict[tuple, "LC.KgcKey"] = {}
         self.ingest, self.mask_rand = ingest, mask_rand
         self.groups = list(groups) if groups else [2] * ((ctx.log_n - 1) // 2) + [1] * ((ctx.log_n - 1) % 2)
         self.flags = flags
@@ -152,14 +191,16 @@ class Server:
             r.state, r.t_admit = DIST, self.now()
             self.active.append(r)
 
-    def _kgc_device(self, r: Round):
+    def _kgc_device(self, r: Round, c: Optional["LC.Context"] = None):
         """The KGC step without a host round trip: read-out and selection on the device, masks
         encrypted with device randomness; the selection is read back after the aggregate."""
         t = time.perf_counter()
-        c, ten = self.ctx, self.tenants[r.tenant]
-        if r.tenant not in self._kgc_keys:
-            self._kgc_keys[r.tenant] = LC.KgcKey(c, ten.s)
-        key = self._kgc_keys[r.tenant]
+        c = c or self.ctx
+        ten = self.tenants[r.tenant]
+        kk = (id(c), r.tenant)
+        if kk not in self._kgc_keys:
+            self._kgc_keys[kk] = LC.KgcKey(c, ten.s)
+        key = self._kgc_keys[kk]
         sc = c.scale * c.scale / c.q[c.L]
         vals = key.readout(r.job.out_dist, c.L - 1, sc)
         w, sel = key.krum(vals, r.n, r.f, r.n_select, r.average)
@@ -239,8 +280,117 @@ class Server:
                 self._kgc(r)
         return True
 
+    # ------------------------------------------------------------------ lanes (device KGC)
+    def _lane_of(self, r: Round) -> int:
+        for k, lane in enumerate(self.lanes):
+            if lane.takes(r):
+                return k
+        return len(self.lanes) - 1
+
+    def _admit_lanes(self):
+        """Admission as in _admit; the round's ciphertexts are assembled on its lane's stream."""
+        while self.waiting:
+            r = self.waiting[0]
+            fp = self.footprint(r)
+            if self.used + fp > self.budget and self.active:
+                break
+            self.waiting.pop(0)
+            self.used += fp
+            self.stats["max_used"] = max(self.stats["max_used"], self.used)
+            r.lane = self._lane_of(r)
+            lane = self.lanes[r.lane]
+            with torch.cuda.stream(lane.stream()):
+                r.cts = self.ingest(r)
+            r.job = LC.Job(self.tenants[r.tenant].evk, r.cts, r.n, r.chunks)
+            r.state, r.t_admit = DIST, self.now()
+            self.active.append(r)
+
+    def _launch(self, k: int) -> bool:
+        """Enqueues one batch on lane k: the distances of every admitted round of the lane, the
+        KGC step of each, and their aggregates; nothing waits on the host."""
+        lane = self.lanes[k]
+        for r in [r for r in self.active if r.lane == k and r.state == DIST and r.cancel_requested]:
+            self._release(r, CANCELLED)
+        rs = [r for r in self.active if r.lane == k and r.state == DIST]
+        if not rs:
+            return False
+        c = lane.ctx
+        with torch.cuda.stream(lane.stream()):
+            LC.batch_distances(c, [r.job for r in rs], LC.LC_MODE_BATCHED | self.flags, self.groups)
+            now = self.now()
+            for r in rs:
+                r.t_dist = now
+                self._kgc_device(r, c)
+            LC.batch_aggregate(c, [r.job for r in rs])
+            lane.inflight = (lane.mark(), rs)
+        for r in rs:
+            r.state = RUNNING
+        lane.batches += 1
+        self.stats["distance_batches"] += 1
+        self.stats["aggregate_batches"] += 1
+        self.stats["rounds_batched"] += len(rs)
+        return True
+
+    def _release(self, r: Round, state: str):
+        self.active.remove(r)
+        self.used -= self.footprint(r)
+        r.state = state
+        r.cts = None
+        r.device_kgc = None
+        if r.job is not None:
+            r.job.cts = None
+            if state == CANCELLED or not self.keep:
+                r.job.masks = r.job.out_agg = None
+            if state == CANCELLED:
+                r.job.out_dist = None
+        (self.cancelled if state == CANCELLED else self.done).append(r)
+
+    def _poll(self) -> bool:
+        """Completes the lanes whose batch has finished on the GPU."""
+        progressed = False
+        for lane in self.lanes:
+            if lane.inflight is None or not lane.inflight[0].query():
+                continue
+            _, rs = lane.inflight
+            lane.inflight = None
+            now = self.now()
+            with torch.cuda.stream(lane.stream()):  # read-backs on the (idle) lane stream
+                for r in rs:
+                    r.t_done = now
+                    if r.cancel_requested:
+                        self._release(r, CANCELLED)
+                        continue
+                    vals, sel = r.device_kgc
+                    r.selected = [int(x) for x in sel.cpu().tolist()]
+                    v = vals.cpu().numpy()
+                    d = np.zeros((r.n, r.n))
+                    d[np.triu_indices(r.n, 1)] = v
+                    r.distances = d + d.T
+                    self._release(r, DONE)
+            progressed = True
+        return progressed
+
+    def _run_lanes(self, rounds: Sequence[Round], realtime: bool) -> List[Round]:
+        pending = sorted(rounds, key=lambda r: r.arrival)
+        self.t0 = time.perf_counter()
+        while pending or self.waiting or self.active:
+            now = self.now()
+            while pending and (not realtime or pending[0].arrival <= now):
+                self.submit(pending.pop(0))
+            progressed = self._poll()
+            self._admit_lanes()
+            for k, lane in enumerate(self.lanes):
+                if lane.inflight is None:
+                    progressed |= self._launch(k)
+            if not progressed:
+                nxt = pending[0].arrival - self.now() if (pending and realtime) else 0.0
+                time.sleep(max(0.0, min(0.0005, nxt)) if nxt > 0 or self.active else 0.0)
+        return self.done
+
     def run(self, rounds: Sequence[Round], realtime: bool = True) -> List[Round]:
         """Feeds rounds at their arrival times (or all at once) and runs until all are done."""
+        if self.device_kgc_seed is not None:
+            return self._run_lanes(rounds, realtime)
         pending = sorted(rounds, key=lambda r: r.arrival)
         self.t0 = time.perf_counter()
         while pending or self.waiting or self.active:

@@ -45,7 +45,7 @@ BASE = {"log": 50.0, "g2qp": 40.0, "g3qp": 30.0}
 
 def _cost(ctx, groups):
     name = {tuple(v): k for k, v in autotune.candidate_schedules(15).items()}[tuple(groups)]
-    ms = BASE[name]
+    ms = BASE.get(name, 35.0 + len(groups))  # the other compositions: slower than g3qp
     for knob, opts in LC.TUNING_OPTIONS.items():
         ms += 0.0 if ctx.knobs[knob] == opts[1 % len(opts)] else 1.0
     return ms
@@ -76,7 +76,10 @@ def test_picks_fastest_schedule_then_each_knob(model):
         assert res["knobs"][LC.TUNING_NAMES[knob]] == opts[1 % len(opts)]
     assert res["ms"] == pytest.approx(30.0)
     n_opts = sum(len(o) for o in LC.TUNING_OPTIONS.values())
-    assert len(res["trials"]) == 3 + n_opts
+    n_sched = len(autotune.candidate_schedules(15))
+    assert res["schedules"] == n_sched >= 10
+    assert len(res["trials"]) == n_sched + n_opts
+    assert res["key_bytes"] == autotune.key_bytes(ctx, 31 + 1)
 
 
 def test_candidates_need_their_keys_and_fit_the_budget(model):
@@ -84,7 +87,7 @@ def test_candidates_need_their_keys_and_fit_the_budget(model):
     log_keys = LC.rotations_of_schedule(autotune.candidate_schedules(15)["log"])
     res = autotune.tune(ctx, FakeEvk(log_keys), None, 10, 64, 1.0)
     assert res["schedule"] == "log"  # only the log-step keys are loaded
-    # a budget that holds the 14 + 1 log-step keys but not the 21 + 1 or 31 + 1 of the others
+    # a budget that holds the 14 + 1 log-step keys but not the 21 + 1 or more of the others
     budget = autotune.key_bytes(ctx, 15) * 1.01
     res = autotune.tune(FakeCtx(), FakeEvk(_all_rots()), None, 10, 64, 1.0, key_budget_bytes=budget)
     assert res["schedule"] == "log"
@@ -108,3 +111,21 @@ def test_cache_file_reuses_a_tuned_shape(model, tmp_path):
     import json
     assert len(json.load(open(path))) == 2
     assert n_calls > 0
+
+
+def test_candidate_schedules_are_every_composition_up_to_four_bits():
+    """The search space: "log" plus every largest-first composition of log2(N/2) into groups of at
+    most 4 bits with at most one single-bit group; each needs 2^g - 1 keys per group."""
+    c = autotune.candidate_schedules(15)
+    assert c["log"] == [1] * 14 and c["g2qp"] == [2] * 7 and c["g3qp"] == [3, 3, 3, 3, 2]
+    assert c["g4442qp"] == [4, 4, 4, 2] and c["g4433qp"] == [4, 4, 3, 3]
+    qp = [v for k, v in c.items() if k != "log"]
+    assert len(qp) == 13 and len({tuple(v) for v in qp}) == 13
+    for v in qp:
+        assert sum(v) == 14 and v == sorted(v, reverse=True) and max(v) <= 4 and v.count(1) <= 1
+    assert autotune.schedule_keys([4, 4, 4, 2]) == 48 and autotune.schedule_keys([1] * 14) == 14
+    # the union of all their rotation keys (what a server loads to search them all)
+    rots = set()
+    for v in c.values():
+        rots |= set(LC.rotations_of_schedule(v))
+    assert len(rots) == 61

@@ -215,6 +215,65 @@ def test_qp_sum_groups_of_seven_bit_exact_toy():
     assert np.array_equal(e.g_coeff(Dg, e.L - 1), e.o_coeff(Do))
 
 
+def test_qp_sum_groups_of_fifteen_bit_exact_toy():
+    """One-ModDown groups of 15 rotations ([4, 4, 3] at 2^11 slots; the largest group the fused
+    kernel takes), against the oracle: a rotate-and-sum, batched distances, and the uneven
+    multi-job path with per-item key tables."""
+    sched = [4, 4, 3]
+    e = Env("toy", 13, S.CFG_TOY, extra_rot=O.rotations_of_schedule(sched))
+    LC = e.LC
+    X = np.random.default_rng(9).normal(0, 0.01, (1, 1, e.prm.slots))
+    ocs, gcs = e.encrypt_both(X, [0], [0])
+    need = O.rotations_of_schedule(sched)
+    yo = e.o.rotate_sum(ocs[0, 0], e.L, sched, {r: e.ork[r] for r in need}, qp_sum=True)
+    yg = e.g.rotate_sum(e.gevk, gcs[0, 0].contiguous(), e.L, sched, qp_sum=True)
+    assert np.array_equal(e.g_coeff(yg, e.L), e.o_coeff(yo))
+    w = S.Workload("t4g4", S.CFG_TOY, 12, 4, 2 * e.prm.slots - 9, 13, (3,), "scale10", 1, 1)
+    W = S.client_updates(w)
+    ocs, gcs = e.encrypt_both(S.split_chunks(W, e.prm.slots), range(4), range(2))
+    mode = LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM
+    Dg, sc = e.g.distances(e.gevk, gcs, 4, 2, e.prm.scale, mode=mode, groups=sched)
+    Do = e.o.distances(ocs, e.orlk, sched, e.ork, qp_sum=True)
+    assert np.array_equal(e.g_coeff(Dg, e.L - 1), e.o_coeff(Do))
+    from test_oracle_pins import toy_distance_tolerance
+    v = e.g.decrypt(e.keys.s, Dg[0].contiguous(), e.L - 1, sc)
+    assert np.abs(v - np.sum((W[0] - W[1]) ** 2)).max() <= toy_distance_tolerance(e.prm)
+    job = LC.Job(e.gevk, gcs, 4, 2)
+    LC.batch_distances(e.g, [job, LC.Job(e.gevk, gcs[:3].contiguous(), 3, 2)], LC.LC_HOIST_QP_SUM, sched)
+    assert torch.equal(job.out_dist, Dg)
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):  # 5-bit one-ModDown groups: not supported
+        e.g.rotate_sum(e.gevk, gcs[0, 0].contiguous(), e.L, [5, 4, 2], qp_sum=True)
+
+
+@pytest.mark.slow
+def test_qp_sum_groups_of_fifteen_production_bit_exact():
+    """A schedule with groups of 4 rotation bits at N = 2^15 ([4,4,4,2], 48 rotation keys): the
+    rotate-and-sum of a fresh ciphertext and the distances of 3 clients bit-exact against the
+    oracle's one-ModDown groups, and the distances within 1e-5 of FP64."""
+    sched = [4, 4, 4, 2]
+    e = Env("prod", 6, S.CFG_PLAIN, extra_rot=O.rotations_of_schedule(sched))
+    LC = e.LC
+    X = np.random.default_rng(10).normal(0, 0.01, (1, 1, e.prm.slots))
+    ocs, gcs = e.encrypt_both(X, [0], [0])
+    need = O.rotations_of_schedule(sched)
+    yo = e.o.rotate_sum(ocs[0, 0], e.L, sched, {r: e.ork[r] for r in need}, qp_sum=True)
+    yg = e.g.rotate_sum(e.gevk, gcs[0, 0].contiguous(), e.L, sched, qp_sum=True)
+    assert np.array_equal(e.g_coeff(yg, e.L), e.o_coeff(yo))
+    w = S.Workload("p3g4", S.CFG_PLAIN, 15, 3, e.prm.slots + 5, 6, (2,), "flip5", 1, 0)
+    W = S.client_updates(w)
+    ocs, gcs = e.encrypt_both(S.split_chunks(W, e.prm.slots), range(3), range(w.chunks))
+    Dg, sc = e.g.distances(e.gevk, gcs, 3, w.chunks, e.prm.scale, mode=LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM,
+                           groups=sched)
+    Do = e.o.distances(ocs, e.orlk, sched, e.ork, qp_sum=True)
+    assert np.array_equal(e.g_coeff(Dg, e.L - 1), e.o_coeff(Do))
+    k = 0
+    for i in range(3):
+        for j in range(i + 1, 3):
+            ref = np.sum((W[i] - W[j]) ** 2)
+            assert abs(e.g.decrypt(e.keys.s, Dg[k].contiguous(), e.L - 1, sc)[0] - ref) / ref < 1e-5
+            k += 1
+
+
 @pytest.fixture(scope="module")
 def prod_g2():
     """Production parameters with the rotation keys of the hoisting schedule [2]*7 (21 keys)."""

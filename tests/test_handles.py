@@ -110,7 +110,9 @@ def test_import_export_round_trip_and_values(htoy):
     r, e0, e1 = (a[:1] for a in rnd)
     ct = e.g.encrypt_values(e.pk, vals, e.prm.scale, r, e0, e1)
     back = e.g.decrypt_values(e.sk, ct, vals.size)
-    assert np.abs(back - vals).max() < 1e-6
+    # toy parameters (scale 2^30, N = 2^12): fresh encryption noise is about 3e-5 per slot
+    assert np.abs(back - vals).max() < 5e-4
+    assert ct.info() == (1, 2, e.L, e.prm.scale)
 
 
 def test_wrong_level_scale_degree_and_shape_are_rejected(htoy):

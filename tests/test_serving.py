@@ -178,3 +178,27 @@ def test_serving_with_device_kgc(feed, toy):
         for k in range(chunks):
             got = toy.g.decrypt(feed.tenants[ten].s, dev[rid].job.out_agg[k].contiguous(), toy.L - 1, sc)
             assert np.abs(got - np.tensordot(wts, X[:, k], axes=1)).max() < 1e-4
+
+
+def test_serving_two_lanes_identical_to_one_lane(feed, toy):
+    """The lane pipeline with two contexts -- rounds of at most 6 pairs on a high-priority stream,
+    the others on a low-priority stream, keys shared -- gives every round the same distances,
+    selection, masks and aggregate as one lane, with rounds arriving while others run."""
+    from paper_2408_06197_b300 import lancelot as LC
+    from paper_2408_06197_b300 import serving as SV
+    one = _by_rid(feed.server(1e12, device_kgc_seed=77).run(feed.rounds(), realtime=False))
+    lo, hi = torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-1)
+    g_fast, g_bulk = LC.Context.toy(stream=hi), LC.Context.toy(stream=lo)
+    srv = SV.Server(toy.g, feed.tenants, 1e12, ingest=lambda r: feed.cts[r.rid].clone(),
+                    mask_rand=None, groups=SCHED, keep_outputs=True, device_kgc_seed=77,
+                    lanes=[SV.Lane(g_fast, 6, "fast"), SV.Lane(g_bulk, None, "bulk")])
+    two = _by_rid(srv.run(feed.rounds(spacing=0.005), realtime=True))
+    torch.cuda.synchronize()
+    assert {r.lane for r in two.values()} == {0, 1}
+    for rid, *_ in feed.specs:
+        a, b = one[rid], two[rid]
+        assert a.selected == b.selected
+        assert np.array_equal(a.distances, b.distances)
+        assert torch.equal(a.job.masks, b.job.masks)
+        assert torch.equal(a.job.out_agg, b.job.out_agg)
+    assert srv.used == 0 and not srv.active

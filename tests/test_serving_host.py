@@ -175,3 +175,143 @@ def test_cancelled_rounds_leave_and_release_their_budget(fake_lib):
     assert sorted(r.rid for r in srv.cancelled) == [0, 2]
     assert all(r.state == SV.CANCELLED for r in srv.cancelled)
     assert srv.used == pytest.approx(0.0)
+
+
+# ------------------------------------------------------------------------------- lanes (device KGC)
+
+class _Arr:
+    """Stands for a small device tensor: .cpu() gives back something with .numpy() / .tolist()."""
+
+    def __init__(self, v):
+        self.v = np.asarray(v)
+
+    def cpu(self):
+        return self
+
+    def numpy(self):
+        return self.v
+
+    def tolist(self):
+        return self.v.tolist()
+
+
+class FakeKgcKey:
+    def __init__(self, ctx, s):
+        self.ctx = ctx
+
+    def readout(self, out_dist, level, scale):
+        return _Arr(out_dist)
+
+    def krum(self, vals, n, f, n_select, average):
+        return _Arr(np.ones(n)), _Arr(np.arange(n_select))
+
+
+class FakeLane(SV.Lane):
+    """A lane whose batches finish after `polls` completion checks (time on the GPU)."""
+
+    def __init__(self, ctx, max_pairs, name, polls, log):
+        super().__init__(ctx, max_pairs, name)
+        self.polls, self.log = polls, log
+
+    def mark(self):
+        lane, state = self, {"left": self.polls}
+
+        class _M:
+            def query(self):
+                state["left"] -= 1
+                if state["left"] <= 0:
+                    lane.log.append(("done", lane.name))
+                    return True
+                return False
+        return _M()
+
+
+class FakeLaneCtx(FakeCtx):
+    stream = None
+
+    def encrypt_const_seeded(self, pk, w, scale, seed, first):
+        return ("masks", first)
+
+
+def _lane_server(monkeypatch, fake_lib, polls_fast, polls_bulk, fast_pairs=45):
+    monkeypatch.setattr(LC, "KgcKey", FakeKgcKey)
+    log = []
+    fast, bulk = FakeLaneCtx(), FakeLaneCtx()
+    lanes = [FakeLane(fast, fast_pairs, "fast", polls_fast, log), FakeLane(bulk, None, "bulk", polls_bulk, log)]
+    ten = [SV.Tenant(evk=f"evk{t}", pk=f"pk{t}", s=np.zeros(fast.N, np.int8)) for t in range(2)]
+    srv = SV.Server(fast, ten, 1e15, lambda r: ("cts", r.rid), lambda r, i: None, groups=[3, 3, 3, 3, 2],
+                    device_kgc_seed=5, lanes=lanes)
+    orig = srv._admit_lanes
+
+    def admit():
+        before = set(id(r) for r in srv.active)
+        orig()
+        for r in srv.active:
+            if id(r) not in before:
+                r.job.rid = r.rid
+    srv._admit_lanes = admit
+    return srv, lanes, log
+
+
+def test_lanes_keep_small_rounds_clear_of_a_large_one(monkeypatch, fake_lib):
+    """A large round (780 pairs) goes to the bulk lane; small rounds that arrive while it is on
+    the GPU launch on the fast lane at once and finish before it."""
+    srv, lanes, log = _lane_server(monkeypatch, fake_lib, polls_fast=2, polls_bulk=50)
+    rounds = [SV.Round(0, 0, 40, 256, 0.0, f=8, n_select=21), SV.Round(1, 1, 5, 4, 0.0, n_select=2),
+              SV.Round(2, 0, 10, 16, 0.0, n_select=5)]
+    done = srv.run(rounds, realtime=False)
+    assert [r.rid for r in done][-1] == 0          # the large round finishes last
+    assert fake_lib["dist"][0] in ([0], [1, 2])    # separate batches per lane
+    assert sorted(map(tuple, fake_lib["dist"])) == [(0,), (1, 2)]
+    by = {r.rid: r for r in done}
+    assert by[0].lane == 1 and by[1].lane == 0 and by[2].lane == 0
+    # both small rounds were done while the large round's batch was still in flight
+    assert log.index(("done", "fast")) < log.index(("done", "bulk"))
+    for r in done:
+        assert r.state == SV.DONE and r.selected == list(range(r.n_select))
+        assert r.distances.shape == (r.n, r.n)
+    assert srv.used == pytest.approx(0.0) and not srv.active
+    assert lanes[0].batches == 1 and lanes[1].batches == 1
+
+
+def test_lanes_one_batch_per_lane_in_flight(monkeypatch, fake_lib):
+    """Rounds that reach a busy lane wait and share its next batch; every round's distances, KGC
+    step and aggregate go out in one batch (no host round trip between them)."""
+    srv, lanes, log = _lane_server(monkeypatch, fake_lib, polls_fast=3, polls_bulk=3, fast_pairs=1000)
+    srv.submit(SV.Round(0, 0, 10, 64, 0.0))
+    srv._admit_lanes()
+    assert srv._launch(0)
+    for i in (1, 2, 3):
+        srv.submit(SV.Round(i, i % 2, 5, 8, 0.0))
+    srv._admit_lanes()
+    assert lanes[0].inflight is not None
+    assert all(r.state == SV.DIST for r in srv.active if r.rid > 0)
+    while not srv._poll():
+        pass
+    assert srv._launch(0)
+    assert fake_lib["dist"] == [[0], [1, 2, 3]] and fake_lib["agg"] == [[0], [1, 2, 3]]
+    while not srv._poll():
+        pass
+    assert [r.rid for r in srv.done] == [0, 1, 2, 3]
+
+
+def test_lanes_cancel_before_launch_and_in_flight(monkeypatch, fake_lib):
+    srv, lanes, log = _lane_server(monkeypatch, fake_lib, polls_fast=2, polls_bulk=2)
+    for i in range(3):
+        srv.submit(SV.Round(i, 0, 5, 8, 0.0))
+    srv._admit_lanes()
+    assert srv.cancel(1)                      # admitted, not launched: dropped at the launch
+    srv._launch(0)
+    assert fake_lib["dist"] == [[0, 2]]
+    assert srv.cancel(2)                      # in flight: finishes on the GPU, then leaves
+    while not srv._poll():
+        pass
+    assert [r.rid for r in srv.done] == [0]
+    assert sorted(r.rid for r in srv.cancelled) == [1, 2]
+    assert srv.used == pytest.approx(0.0)
+
+
+def test_last_lane_must_take_every_size():
+    ctx = FakeLaneCtx()
+    with pytest.raises(ValueError):
+        SV.Server(ctx, [], 1.0, None, None, lanes=[SV.Lane(ctx, 10)])
