@@ -194,7 +194,13 @@ static int build_tables(lc_ctx* c) {
         mc.one_sh = (u64)(((lc::u128)1 << 64) / q);
         mc.n_inv = ninv;
         mc.n_inv_sh = shoup_of(ninv, q);
-        mc.pad = 0;
+        {
+            int b = 0;
+            while (b < 64 && (q >> b)) b++;
+            const int s1 = std::max(0, b - 26), sh = b + 31 - s1;
+            const u64 cc = (b + 31 < 128) ? (u64)(((lc::u128)1 << (b + 31)) / q) : 0;
+            mc.lzr = (b <= 46 && cc < (1ull << 32)) ? (cc | (u64)s1 << 32 | (u64)sh << 40) : 0;
+        }
     }
     // ModUp tables [level][digit]
     std::vector<ModUpTab> mu((size_t)c->nq * c->dnum);
@@ -1571,7 +1577,8 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
         case LC_TUNE_GROUP_SPLIT_ITEMS:
         case LC_TUNE_GROUP_WIDE_ITEMS: ok = value == 1 || value == 2; break;
         case LC_TUNE_TENSOR_WARPS: ok = value == 8 || value == 12 || value == 16; break;
-        case LC_TUNE_NTT_ROW_TMA: ok = value == 0 || value == 1; break;
+        case LC_TUNE_NTT_ROW_TMA:
+        case LC_TUNE_GROUP_KARATSUBA: ok = value == 0 || value == 1; break;
         default: break;
     }
     if (!ok) return fail(c, LC_EINVAL, "lc_set_tuning: knob " + std::to_string(knob) + " has no option " +
@@ -1581,7 +1588,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
 }
 
 int lc_get_tuning(const lc_ctx* c, uint32_t knob, int32_t* value) {
-    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_NTT_ROW_TMA) return LC_EINVAL;
+    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_GROUP_KARATSUBA) return LC_EINVAL;
     *value = c->tune[knob];
     return LC_OK;
 }

@@ -17,8 +17,23 @@ struct ModConst {
     u64 one_sh;   // floor(2^64 / q)
     u64 n_inv;    // N^-1 mod q
     u64 n_inv_sh;
-    u64 pad;
+    // final reduction of lazy transform values (reduce_lazy below): bits 0..31 c = floor(2^(b+31)/q)
+    // with b = bits(q); bits 32..39 s1 = max(0, b - 26); bits 40..47 sh = b + 31 - s1
+    u64 lzr;
 };
+
+// x mod q for x < 64 q (the lazy range of the transforms for primes below 2^46), in [0, q).
+// xh = floor(x / 2^s1) < 2^32 and t = floor(xh c / 2^sh) approximate x / q from below: the
+// truncation of x loses < 2^s1 / q <= 2^-25 and that of c < xh 2^s1 / 2^(b+31) < 2^-25 of a
+// quotient unit, so t is floor(x / q) or one less, x - t q lies in [0, 2q) and one
+// conditional subtraction finishes.
+__device__ __forceinline__ u64 reduce_lazy(u64 x, const ModConst& m) {
+    const unsigned c = (unsigned)m.lzr, s1 = (unsigned)(m.lzr >> 32) & 255u, sh = (unsigned)(m.lzr >> 40) & 255u;
+    const unsigned xh = (unsigned)(x >> s1);
+    const unsigned t = (unsigned)(((u64)xh * c) >> sh);
+    const u64 r = x - (u64)t * m.q;
+    return r >= m.q ? r - m.q : r;
+}
 
 __device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 w_sh, u64 q) {
     u64 hi = __umul64hi(a, w_sh);

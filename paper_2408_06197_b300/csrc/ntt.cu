@@ -54,10 +54,6 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64
     x = LZ ? a : csub(a, two_q);
     y = mul_shoup_lazy(b, w.x, w.y, q);
 }
-// any x < 2^64 -> [0, q)
-__device__ __forceinline__ u64 reduce_word(u64 x, const ModConst& mc) {
-    return csub(x - __umul64hi(x, mc.one_sh) * mc.q, mc.q);
-}
 
 // swizzle for the row-pass tile: XOR word bits 0..3 with bits 4..7
 __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 4) & 15); }
@@ -255,7 +251,7 @@ __device__ __forceinline__ void fwd_row_body(const u64* in, u64* a, u64* s, cons
     }
 #pragma unroll
     for (int u = 0; u < 16; u++)
-        s[swz((blk << 8) + 16 * lo + u)] = LZ ? reduce_word(x[u], mc) : csub(csub(x[u], mc.two_q), mc.q);
+        s[swz((blk << 8) + 16 * lo + u)] = LZ ? reduce_lazy(x[u], mc) : csub(csub(x[u], mc.two_q), mc.q);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 16; u++) a[(blk << 8) + lo + 16 * u] = s[swz((blk << 8) + lo + 16 * u)];

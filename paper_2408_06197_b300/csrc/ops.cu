@@ -175,6 +175,12 @@ __device__ __forceinline__ void mac_split(Acc3& s, unsigned h, unsigned l, unsig
     s.b += (u64)l * h2;
     s.c += (u64)l * l2;
 }
+// Karatsuba form: b collects (h + l)(h2 + l2); the caller subtracts a + c once at the end
+__device__ __forceinline__ void mac_kara(Acc3& s, unsigned h, unsigned l, unsigned hl, unsigned h2, unsigned l2) {
+    s.a += (u64)h * h2;
+    s.b += (u64)hl * (h2 + l2);
+    s.c += (u64)l * l2;
+}
 // the same as explicit 32-bit multiply-adds with a carry chain into the two halves of each
 // 64-bit partial sum (measured faster than 64-bit wide multiply-adds in the distance tensor
 // kernel, slower in the others)
@@ -963,8 +969,12 @@ struct RowSel {
     int a0, na, b0;
 };
 // SPLIT: every selected row's prime is below 2^40, so digits and keys split into 20-bit halves
-// (four 32x32 -> 64-bit products per 128-bit product, three 64-bit partial sums)
-template <int T, bool ITEMS, bool SPLIT, int kBT>
+// (four 32x32 -> 64-bit products per 128-bit product, three 64-bit partial sums).
+// KARA (with SPLIT): three products instead of four -- h h', l l' and (h + l)(h' + l'), whose
+// sum minus the other two is the middle term h l' + l h' (Karatsuba); every term is a
+// non-negative integer, (h + l)(h' + l') < 2^42 and at most 60 of them are summed, so the
+// partial sums stay below 2^48 and the result is the same integer.
+template <int T, bool ITEMS, bool SPLIT, int kBT, bool KARA = false>
 __global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
@@ -1024,7 +1034,14 @@ __global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gath
                 const u64* e = own ? d + (size_t)b * d_stride + ((size_t)r << log_n)
                                    : ext + (((size_t)b * beta + j) * rows + r) * N;
                 const ulonglong2 ev = ld2_swap(e, s0[t], sw[t]);
-                if (SPLIT) {
+                if (SPLIT && KARA) {
+                    const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
+                    const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
+                    mac_kara(h[i][0][0], exh, exl, exh + exl, (unsigned)(k0.x >> 32), (unsigned)k0.x);
+                    mac_kara(h[i][0][1], eyh, eyl, eyh + eyl, (unsigned)(k0.y >> 32), (unsigned)k0.y);
+                    mac_kara(h[i][1][0], exh, exl, exh + exl, (unsigned)(k1.x >> 32), (unsigned)k1.x);
+                    mac_kara(h[i][1][1], eyh, eyl, eyh + eyl, (unsigned)(k1.y >> 32), (unsigned)k1.y);
+                } else if (SPLIT) {
                     const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
                     const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
                     mac_split(h[i][0][0], exh, exl, (unsigned)(k0.x >> 32), (unsigned)k0.x);
@@ -1046,6 +1063,12 @@ __global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gath
             const int b = b0 + i;
             u64* ub = usum + ((size_t)b * 2 * rows + r) * N + x;
             if (SPLIT) {
+                if (KARA) {  // middle terms: sum (h + l)(h' + l') - sum h h' - sum l l'
+#pragma unroll
+                    for (int p2 = 0; p2 < 2; p2++)
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; c2++) h[i][p2][c2].b -= h[i][p2][c2].a + h[i][p2][c2].c;
+                }
                 st2(ub, acc3_reduce(h[i][0][0], 20, mcr), acc3_reduce(h[i][0][1], 20, mcr));
                 st2(ub + (size_t)rows * N, acc3_reduce(h[i][1][0], 20, mcr), acc3_reduce(h[i][1][1], 20, mcr));
             } else {
@@ -1534,43 +1557,40 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
     const RowSel split{k, nl - k, 0}, wide{0, k, nl};
     const int ns = nl - k, nw = k + c->np;
     const unsigned gy = (unsigned)(c->N / (2 * kTG));
-#define LC_IG(TT, SPL, BT, SEL, CNT)                                                                                \
+#define LC_IG(TT, SPL, BT, SEL, CNT, KA)                                                                            \
     {                                                                                                               \
         const dim3 grid((unsigned)((B + BT - 1) / BT), gy, CNT);                                                    \
         if (keys_dev)                                                                                               \
-            k_inner_gather<TT, true, SPL, BT><<<grid, kTG, 0, c->stream>>>(                                         \
+            k_inner_gather<TT, true, SPL, BT, KA><<<grid, kTG, 0, c->stream>>>(                                     \
                 ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
                 keys_dev, g, SEL, c->mc, usum, c0acc);                                                              \
         else                                                                                                        \
-            k_inner_gather<TT, false, SPL, BT><<<grid, kTG, 0, c->stream>>>(                                        \
+            k_inner_gather<TT, false, SPL, BT, KA><<<grid, kTG, 0, c->stream>>>(                                    \
                 ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
                 nullptr, g, SEL, c->mc, usum, c0acc);                                                               \
     }
-#define LC_IG_T(SPL, BT, SEL, CNT)                 \
-    switch (T) {                                   \
-        case 1: LC_IG(1, SPL, BT, SEL, CNT); break; \
-        case 2: LC_IG(2, SPL, BT, SEL, CNT); break; \
-        case 3: LC_IG(3, SPL, BT, SEL, CNT); break; \
-        case 4: LC_IG(4, SPL, BT, SEL, CNT); break; \
-        case 5: LC_IG(5, SPL, BT, SEL, CNT); break; \
-        case 6: LC_IG(6, SPL, BT, SEL, CNT); break; \
-        case 7: LC_IG(7, SPL, BT, SEL, CNT); break; \
-        case 15: LC_IG(15, SPL, BT, SEL, CNT); break; \
-        default: break;                            \
+#define LC_IG_T(SPL, BT, SEL, CNT, KA)                 \
+    switch (T) {                                       \
+        case 1: LC_IG(1, SPL, BT, SEL, CNT, KA); break; \
+        case 3: LC_IG(3, SPL, BT, SEL, CNT, KA); break; \
+        case 7: LC_IG(7, SPL, BT, SEL, CNT, KA); break; \
+        case 15: LC_IG(15, SPL, BT, SEL, CNT, KA); break; \
+        default: break;                                \
     }
-    if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS
+    if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS; products: LC_TUNE_GROUP_KARATSUBA
+        const bool kara = c->tune[LC_TUNE_GROUP_KARATSUBA] == 1;
         if (c->tune[LC_TUNE_GROUP_SPLIT_ITEMS] == 2) {
-            LC_IG_T(true, 2, split, ns)
+            if (kara) LC_IG_T(true, 2, split, ns, true) else LC_IG_T(true, 2, split, ns, false)
         } else {
-            LC_IG_T(true, 1, split, ns)
+            if (kara) LC_IG_T(true, 1, split, ns, true) else LC_IG_T(true, 1, split, ns, false)
         }
         g_lc_launches += 1;
     }
     if (nw) {  // LC_TUNE_GROUP_WIDE_ITEMS
         if (c->tune[LC_TUNE_GROUP_WIDE_ITEMS] == 1) {
-            LC_IG_T(false, 1, wide, nw)
+            LC_IG_T(false, 1, wide, nw, false)
         } else {
-            LC_IG_T(false, 2, wide, nw)
+            LC_IG_T(false, 2, wide, nw, false)
         }
         g_lc_launches += 1;
     }
