@@ -1130,6 +1130,9 @@ def main():
             el = timed(lambda: pipelined(args.steps))
             e2e = {"value": whole_job_rate(w.n_pairs, world, args.steps, el), "unit": UNIT,
                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
+                   "link_GBps": (h2d_bytes + d2h_bytes) * args.steps / el / 1e9,
+                   "bound": "host link: the step's wire-form copies take longer than its compute "
+                            "(link_GBps is the copies' bytes over the pipelined wall time)",
                    "form": "wire form (lc_pack/lc_unpack on the device); double-buffered: next step's H2D and "
                            "previous step's D2H overlap this step's compute",
                    "serial": e2e_serial}

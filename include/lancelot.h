@@ -149,8 +149,8 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  *                              16 (4 pair slots per thread), 8 (8 slots) or 12 (6 slots)
  *   LC_TUNE_NTT_ROW_TMA        forward row pass: 0 = one block per tile, 1 = persistent blocks
  *                              streaming tiles through shared memory with bulk copies (TMA)
- *   LC_TUNE_GROUP_KARATSUBA    one-ModDown group kernel, rows with primes below 2^40: 0 = four
- *                              20-bit partial products per product, 1 = three (Karatsuba)
+ *   LC_TUNE_GROUP_KARATSUBA    one-ModDown group kernel, rows with primes below 2^40: 1 = three
+ *                              20-bit partial products per product (Karatsuba), 0 = four
  * The paper_2408_06197_b300.autotune module times the options on the caller's workload. */
 #define LC_TUNE_NTT_ROW_MINB 1
 #define LC_TUNE_NTT_COL_MINB 2

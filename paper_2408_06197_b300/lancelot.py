@@ -43,7 +43,7 @@ TUNING_OPTIONS = {
     LC_TUNE_GROUP_WIDE_ITEMS: (2, 1),
     LC_TUNE_TENSOR_WARPS: (16, 8, 12),
     LC_TUNE_NTT_ROW_TMA: (0, 1),
-    LC_TUNE_GROUP_KARATSUBA: (0, 1),
+    LC_TUNE_GROUP_KARATSUBA: (1, 0),
 }
 TUNING_NAMES = {LC_TUNE_NTT_ROW_MINB: "ntt_row_minb", LC_TUNE_NTT_COL_MINB: "ntt_col_minb",
                 LC_TUNE_GROUP_SPLIT_ITEMS: "group_split_items", LC_TUNE_GROUP_WIDE_ITEMS: "group_wide_items",
