@@ -151,10 +151,6 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  *                              streaming tiles through shared memory with bulk copies (TMA)
  *   LC_TUNE_GROUP_KARATSUBA    one-ModDown group kernel, rows with primes below 2^40: 1 = three
  *                              20-bit partial products per product (Karatsuba), 0 = four
- *   LC_TUNE_GROUP_SPLIT_MINB   same kernel with one item per thread: minimum resident 128-thread
- *                              blocks, i.e. a register cap: 5, 6, 8
- *   LC_TUNE_GROUP_RING         one-ModDown group kernel operands: 0 = loaded by each thread,
- *                              1 = streamed through a shared-memory ring with asynchronous copies
  * The paper_2408_06197_b300.autotune module times the options on the caller's workload. */
 #define LC_TUNE_NTT_ROW_MINB 1
 #define LC_TUNE_NTT_COL_MINB 2
@@ -163,8 +159,6 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
 #define LC_TUNE_TENSOR_WARPS 5
 #define LC_TUNE_NTT_ROW_TMA 6
 #define LC_TUNE_GROUP_KARATSUBA 7
-#define LC_TUNE_GROUP_SPLIT_MINB 8
-#define LC_TUNE_GROUP_RING 9
 int lc_set_tuning(lc_ctx* ctx, uint32_t knob, int32_t value);
 int lc_get_tuning(const lc_ctx* ctx, uint32_t knob, int32_t* value);
 

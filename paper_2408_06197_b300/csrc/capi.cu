@@ -1578,9 +1578,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
         case LC_TUNE_GROUP_WIDE_ITEMS: ok = value == 1 || value == 2; break;
         case LC_TUNE_TENSOR_WARPS: ok = value == 8 || value == 12 || value == 16; break;
         case LC_TUNE_NTT_ROW_TMA:
-        case LC_TUNE_GROUP_KARATSUBA:
-        case LC_TUNE_GROUP_RING: ok = value == 0 || value == 1; break;
-        case LC_TUNE_GROUP_SPLIT_MINB: ok = value == 5 || value == 6 || value == 8; break;
+        case LC_TUNE_GROUP_KARATSUBA: ok = value == 0 || value == 1; break;
         default: break;
     }
     if (!ok) return fail(c, LC_EINVAL, "lc_set_tuning: knob " + std::to_string(knob) + " has no option " +
@@ -1590,7 +1588,7 @@ int lc_set_tuning(lc_ctx* c, uint32_t knob, int32_t value) {
 }
 
 int lc_get_tuning(const lc_ctx* c, uint32_t knob, int32_t* value) {
-    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_GROUP_RING) return LC_EINVAL;
+    if (!c || !value || knob < LC_TUNE_NTT_ROW_MINB || knob > LC_TUNE_GROUP_KARATSUBA) return LC_EINVAL;
     *value = c->tune[knob];
     return LC_OK;
 }

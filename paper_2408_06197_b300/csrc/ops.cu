@@ -974,10 +974,8 @@ struct RowSel {
 // sum minus the other two is the middle term h l' + l h' (Karatsuba); every term is a
 // non-negative integer, (h + l)(h' + l') < 2^42 and at most 60 of them are summed, so the
 // partial sums stay below 2^48 and the result is the same integer.
-// MINB: minimum resident blocks of the launch (a register cap; a tuning choice for the split
-// kernel with one item per thread, 1 otherwise)
-template <int T, bool ITEMS, bool SPLIT, int kBT, bool KARA = false, int MINB = 1>
-__global__ void __launch_bounds__(kTG, MINB) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+template <int T, bool ITEMS, bool SPLIT, int kBT, bool KARA = false>
+__global__ void __launch_bounds__(kTG, (SPLIT && kBT == 1) ? 5 : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
                                                      int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
@@ -1093,186 +1091,6 @@ __global__ void __launch_bounds__(kTG, MINB) k_inner_gather(const u64* __restric
         }
     }
 }
-
-// The same group inner product with its operands streamed through a shared-memory ring.  A
-// block covers the aligned 256-coefficient tile [x0, x0 + 256) of one row; for every (digit j,
-// rotation t) stage it needs the key tiles k'_t[j] at the tile and, per item, the image of the
-// tile under the rotation in the extended digit E_j -- an aligned 256-block again, because the
-// automorphism maps aligned 2^m-blocks of the bit-reversed order onto aligned 2^m-blocks (fixing
-// the high index bits fixes the low bits of the exponent, which multiplication by the odd g
-// preserves).  Each stage's tiles are copied with cp.async kRingG - 1 stages ahead into a ring
-// of kRingG slots, so the L2 latency of the gathers overlaps the products of earlier stages
-// instead of holding registers; the products, their order and the reduction are those of
-// k_inner_gather, so the results are identical.
-constexpr int kRingG = 4;
-template <int T, bool ITEMS, bool SPLIT, int kBT, bool KARA, int MINB>
-__global__ void __launch_bounds__(kTG, MINB) k_inner_gather_ring(const u64* __restrict__ ext,
-                                                                 const u64* __restrict__ d, size_t d_stride,
-                                                                 const u64* __restrict__ y0, size_t y0_stride,
-                                                                 int B, int beta, int nl, int rows, int alpha, int nq,
-                                                                 int nqp, int log_n, KeyPtrs keys,
-                                                                 const u64* const* __restrict__ keys_dev, Galois gs,
-                                                                 RowSel sel, const ModConst* __restrict__ mc,
-                                                                 u64* __restrict__ usum, u64* __restrict__ c0acc) {
-    constexpr int NK = ITEMS ? kBT : 1;  // key sets per stage
-    constexpr int ARR = kBT + 2 * NK;    // 256-word tiles per stage: the items' digit images, the keys
-    constexpr int SLOT = ARR * 2 * kTG;  // words per ring slot
-    extern __shared__ __align__(16) u64 gring[];
-    __shared__ unsigned sbase[T];
-    __shared__ const u64* skey[T];
-    const size_t N = (size_t)1 << log_n;
-    const int tid = threadIdx.x;
-    const unsigned x0 = blockIdx.y * kTG * 2;
-    const unsigned x = x0 + tid * 2;
-    const int z = blockIdx.z;
-    const int r = z < sel.na ? sel.a0 + z : sel.b0 + (z - sel.na);
-    const int b0 = blockIdx.x * kBT;
-    const int nb = min(kBT, B - b0);
-    const int kt = r < nl ? r : nq + (r - nl);
-    const ModConst& mcr = mc[kt];
-    const u64 q = __ldg(&mcr.q), r64 = __ldg(&mcr.r64), r64sh = __ldg(&mcr.r64_sh), osh = __ldg(&mcr.one_sh);
-#pragma unroll
-    for (int t = 0; t < T; t++)  // compile-time indices into the parameter arrays
-        if (tid == t) {
-            sbase[t] = auto_src(x0, gs.g[t], log_n) & ~255u;  // the image block of the tile
-            skey[t] = ITEMS ? nullptr : keys.p[t];
-        }
-    unsigned s0[T];
-    bool sw[T];
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-        const unsigned sv = auto_src(x, gs.g[t], log_n);
-        s0[t] = sv & ~1u;
-        sw[t] = sv & 1u;
-    }
-    // items past the end of the batch repeat the last one; their results are not stored
-    int bi[kBT];
-#pragma unroll
-    for (int i = 0; i < kBT; i++) bi[i] = b0 + min(i, nb - 1);
-    const int own_j = r < nl ? r / alpha : -1;
-    const size_t ka = (size_t)nqp * N;
-    __syncthreads();
-    const int stages = beta * T;
-    // per item: its extended digits (digit j at + j rows N) and its own rows in d; this thread's
-    // 16-byte column of every tile
-    const u64* ebase0 = ext + ((size_t)bi[0] * beta * rows + r) * N + 2 * tid;
-    const u64* dbase0 = d + (size_t)bi[0] * d_stride + ((size_t)r << log_n) + 2 * tid;
-    const u64* ebase1 = ext + ((size_t)bi[kBT - 1] * beta * rows + r) * N + 2 * tid;
-    const u64* dbase1 = d + (size_t)bi[kBT - 1] * d_stride + ((size_t)r << log_n) + 2 * tid;
-    const size_t ej = (size_t)rows * N;
-    u64* const ring_t = gring + 2 * tid;
-    // stage s = (j, t): its tiles into ring slot s % kRingG (an empty group past the end keeps
-    // the group count uniform)
-#define LC_RING_ISSUE(S_)                                                                                       \
-    {                                                                                                           \
-        const int s_ = (S_);                                                                                    \
-        if (s_ < stages) {                                                                                      \
-            const int j_ = s_ / T, t_ = s_ - j_ * T;                                                            \
-            u64* slot_ = ring_t + (size_t)(s_ % kRingG) * SLOT;                                                 \
-            const unsigned base_ = sbase[t_];                                                                   \
-            const size_t ko_ = ((size_t)j_ * 2 * nqp + kt) * N + x0 + 2 * tid;                                  \
-            cp_async16(slot_, (j_ == own_j ? dbase0 : ebase0 + j_ * ej) + base_);                               \
-            if (kBT == 2) cp_async16(slot_ + 2 * kTG, (j_ == own_j ? dbase1 : ebase1 + j_ * ej) + base_);       \
-            const u64* kp0_ = ITEMS ? keys_dev[(size_t)bi[0] * T + t_] : skey[t_];                              \
-            cp_async16(slot_ + kBT * 2 * kTG, kp0_ + ko_);                                                      \
-            cp_async16(slot_ + (kBT + 1) * 2 * kTG, kp0_ + ko_ + ka);                                           \
-            if (ITEMS && kBT == 2) {                                                                            \
-                const u64* kp1_ = keys_dev[(size_t)bi[kBT - 1] * T + t_];                                       \
-                cp_async16(slot_ + (kBT + 2) * 2 * kTG, kp1_ + ko_);                                            \
-                cp_async16(slot_ + (kBT + 3) * 2 * kTG, kp1_ + ko_ + ka);                                       \
-            }                                                                                                   \
-        }                                                                                                       \
-        cp_async_commit();                                                                                      \
-    }
-    u128v a[SPLIT ? 1 : kBT][2][2];
-    Acc3 h[SPLIT ? kBT : 1][2][2];
-#pragma unroll
-    for (int i = 0; i < kBT; i++) {
-        if (SPLIT)
-            h[i][0][0] = h[i][0][1] = h[i][1][0] = h[i][1][1] = Acc3{0, 0, 0};
-        else
-            a[i][0][0] = a[i][0][1] = a[i][1][0] = a[i][1][1] = u128v{0, 0};
-    }
-    static_assert(kBT == 1 || kBT == 2, "one or two items per thread");
-#pragma unroll
-    for (int s = 0; s < kRingG - 1; s++) LC_RING_ISSUE(s)
-    for (int j = 0; j < beta; j++) {
-#pragma unroll
-        for (int t = 0; t < T; t++) {
-            const int s = j * T + t;
-            cp_async_wait<kRingG - 2>();
-            __syncthreads();  // stage s has landed for every thread; slot (s - 1) % kRingG is free
-            LC_RING_ISSUE(s + kRingG - 1)
-            const u64* slot = gring + (size_t)(s % kRingG) * SLOT;
-            const unsigned loc = s0[t] - sbase[t];
-#pragma unroll
-            for (int i = 0; i < kBT; i++) {
-                const int kk = ITEMS ? i : 0;
-                const ulonglong2 k0 = *reinterpret_cast<const ulonglong2*>(slot + (kBT + 2 * kk) * 2 * kTG + 2 * tid);
-                const ulonglong2 k1 =
-                    *reinterpret_cast<const ulonglong2*>(slot + (kBT + 2 * kk + 1) * 2 * kTG + 2 * tid);
-                const ulonglong2 raw = *reinterpret_cast<const ulonglong2*>(slot + i * 2 * kTG + loc);
-                const ulonglong2 ev = sw[t] ? make_ulonglong2(raw.y, raw.x) : raw;
-                if (SPLIT && KARA) {
-                    const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
-                    const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
-                    mac_kara(h[i][0][0], exh, exl, exh + exl, (unsigned)(k0.x >> 32), (unsigned)k0.x);
-                    mac_kara(h[i][0][1], eyh, eyl, eyh + eyl, (unsigned)(k0.y >> 32), (unsigned)k0.y);
-                    mac_kara(h[i][1][0], exh, exl, exh + exl, (unsigned)(k1.x >> 32), (unsigned)k1.x);
-                    mac_kara(h[i][1][1], eyh, eyl, eyh + eyl, (unsigned)(k1.y >> 32), (unsigned)k1.y);
-                } else if (SPLIT) {
-                    const unsigned exh = (unsigned)(ev.x >> 20), exl = (unsigned)ev.x & 0xFFFFFu;
-                    const unsigned eyh = (unsigned)(ev.y >> 20), eyl = (unsigned)ev.y & 0xFFFFFu;
-                    mac_split(h[i][0][0], exh, exl, (unsigned)(k0.x >> 32), (unsigned)k0.x);
-                    mac_split(h[i][0][1], eyh, eyl, (unsigned)(k0.y >> 32), (unsigned)k0.y);
-                    mac_split(h[i][1][0], exh, exl, (unsigned)(k1.x >> 32), (unsigned)k1.x);
-                    mac_split(h[i][1][1], eyh, eyl, (unsigned)(k1.y >> 32), (unsigned)k1.y);
-                } else {
-                    mac128(a[i][0][0], ev.x, k0.x);
-                    mac128(a[i][0][1], ev.y, k0.y);
-                    mac128(a[i][1][0], ev.x, k1.x);
-                    mac128(a[i][1][1], ev.y, k1.y);
-                }
-            }
-        }
-    }
-    cp_async_wait<0>();
-#pragma unroll
-    for (int i = 0; i < kBT; i++) {
-        if (i < nb) {
-            const int b = b0 + i;
-            u64* ub = usum + ((size_t)b * 2 * rows + r) * N + x;
-            if (SPLIT) {
-                if (KARA) {
-#pragma unroll
-                    for (int p2 = 0; p2 < 2; p2++)
-#pragma unroll
-                        for (int c2 = 0; c2 < 2; c2++) h[i][p2][c2].b -= h[i][p2][c2].a + h[i][p2][c2].c;
-                }
-                st2(ub, acc3_reduce(h[i][0][0], 20, mcr), acc3_reduce(h[i][0][1], 20, mcr));
-                st2(ub + (size_t)rows * N, acc3_reduce(h[i][1][0], 20, mcr), acc3_reduce(h[i][1][1], 20, mcr));
-            } else {
-                st2(ub, reduce128c(a[i][0][0], q, r64, r64sh, osh), reduce128c(a[i][0][1], q, r64, r64sh, osh));
-                st2(ub + (size_t)rows * N, reduce128c(a[i][1][0], q, r64, r64sh, osh),
-                    reduce128c(a[i][1][1], q, r64, r64sh, osh));
-            }
-            if (r < nl) {
-                const u64* yb = y0 + (size_t)b * y0_stride + ((size_t)r << log_n);
-                const ulonglong2 self = ld2(yb + x);
-                u64 c0 = self.x, c1 = self.y;  // T + 1 <= 16 terms below q < 2^60
-#pragma unroll
-                for (int t = 0; t < T; t++) {
-                    const ulonglong2 v = ld2_swap(yb, s0[t], sw[t]);
-                    c0 += v.x;
-                    c1 += v.y;
-                }
-                st2(c0acc + ((size_t)b * nl + r) * N + x, reduce64(c0, mcr), reduce64(c1, mcr));
-            }
-        }
-    }
-}
-
-#undef LC_RING_ISSUE
 
 // ModDown conversion of the K special-prime rows.  grid: x = tile of 2*kT coefficients, y = b*2 + k
 template <int K>
@@ -1587,16 +1405,6 @@ void op_sq_acc_pairs(lc_ctx* c, const u64* cts, int n, int chunks, int nl, int p
     g_lc_launches += 1;
 }
 
-// dynamic shared memory above the default 48 KB: the attribute is set once per kernel
-template <typename K>
-static void dyn_smem_attr(K kernel, size_t bytes) {
-    static std::mutex mu;
-    static std::set<const void*> done;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done.insert(reinterpret_cast<const void*>(kernel)).second)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(bytes, 1));
-}
-
 // the tensor kernels' ring lives in dynamic shared memory (above the 48 KB static limit); the
 // attribute is set once per kernel instantiation
 template <typename K>
@@ -1749,68 +1557,45 @@ void op_inner_gather(lc_ctx* c, const u64* ext, const u64* d, size_t d_stride, c
     const RowSel split{k, nl - k, 0}, wide{0, k, nl};
     const int ns = nl - k, nw = k + c->np;
     const unsigned gy = (unsigned)(c->N / (2 * kTG));
-    const bool ring = c->tune[LC_TUNE_GROUP_RING] == 1;
-#define LC_IG_ONE(KERNEL, SMEM, SEL, grid)                                                                          \
-    KERNEL<<<grid, kTG, SMEM, c->stream>>>(ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq,      \
-                                          c->nq + c->np, c->log_n, kp, keys_dev, g, SEL, c->mc, usum, c0acc)
-#define LC_IG(TT, SPL, BT, SEL, CNT, KA, MB)                                                                        \
+#define LC_IG(TT, SPL, BT, SEL, CNT, KA)                                                                            \
     {                                                                                                               \
         const dim3 grid((unsigned)((B + BT - 1) / BT), gy, CNT);                                                    \
-        if (ring) {                                                                                                 \
-            if (keys_dev) {                                                                                         \
-                const size_t sm = (size_t)kRingG * (BT + 2 * BT) * 2 * kTG * 8;                                     \
-                dyn_smem_attr(k_inner_gather_ring<TT, true, SPL, BT, KA, MB>, sm);                                  \
-                LC_IG_ONE((k_inner_gather_ring<TT, true, SPL, BT, KA, MB>), sm, SEL, grid);                         \
-            } else {                                                                                                \
-                const size_t sm = (size_t)kRingG * (BT + 2) * 2 * kTG * 8;                                          \
-                dyn_smem_attr(k_inner_gather_ring<TT, false, SPL, BT, KA, MB>, sm);                                 \
-                LC_IG_ONE((k_inner_gather_ring<TT, false, SPL, BT, KA, MB>), sm, SEL, grid);                        \
-            }                                                                                                       \
-        } else if (keys_dev) {                                                                                      \
-            LC_IG_ONE((k_inner_gather<TT, true, SPL, BT, KA, MB>), 0, SEL, grid);                                   \
-        } else {                                                                                                    \
-            LC_IG_ONE((k_inner_gather<TT, false, SPL, BT, KA, MB>), 0, SEL, grid);                                  \
-        }                                                                                                           \
+        if (keys_dev)                                                                                               \
+            k_inner_gather<TT, true, SPL, BT, KA><<<grid, kTG, 0, c->stream>>>(                                     \
+                ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
+                keys_dev, g, SEL, c->mc, usum, c0acc);                                                              \
+        else                                                                                                        \
+            k_inner_gather<TT, false, SPL, BT, KA><<<grid, kTG, 0, c->stream>>>(                                    \
+                ext, d, d_stride, y0, y0_stride, B, beta, nl, rows, c->alpha, c->nq, c->nq + c->np, c->log_n, kp,    \
+                nullptr, g, SEL, c->mc, usum, c0acc);                                                               \
     }
     // groups of 2, 3 and 4 rotation bits (a group of one rotation takes the per-rotation path)
-#define LC_IG_T(SPL, BT, SEL, CNT, KA, MB)                  \
-    switch (T) {                                            \
-        case 3: LC_IG(3, SPL, BT, SEL, CNT, KA, MB); break;   \
-        case 7: LC_IG(7, SPL, BT, SEL, CNT, KA, MB); break;   \
-        case 15: LC_IG(15, SPL, BT, SEL, CNT, KA, MB); break; \
-        default: break;                                     \
+#define LC_IG_T(SPL, BT, SEL, CNT, KA)                  \
+    switch (T) {                                        \
+        case 3: LC_IG(3, SPL, BT, SEL, CNT, KA); break;   \
+        case 7: LC_IG(7, SPL, BT, SEL, CNT, KA); break;   \
+        case 15: LC_IG(15, SPL, BT, SEL, CNT, KA); break; \
+        default: break;                                 \
     }
-    if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS; products: LC_TUNE_GROUP_KARATSUBA;
-               // register cap of the one-item kernel: LC_TUNE_GROUP_SPLIT_MINB
+    if (ns) {  // items per thread: LC_TUNE_GROUP_SPLIT_ITEMS; products: LC_TUNE_GROUP_KARATSUBA
         const bool kara = c->tune[LC_TUNE_GROUP_KARATSUBA] == 1;
         if (c->tune[LC_TUNE_GROUP_SPLIT_ITEMS] == 2) {
-            if (kara) LC_IG_T(true, 2, split, ns, true, 1) else LC_IG_T(true, 2, split, ns, false, 1)
+            if (kara) LC_IG_T(true, 2, split, ns, true) else LC_IG_T(true, 2, split, ns, false)
         } else {
-            switch (c->tune[LC_TUNE_GROUP_SPLIT_MINB]) {
-                case 6:
-                    if (kara) LC_IG_T(true, 1, split, ns, true, 6) else LC_IG_T(true, 1, split, ns, false, 6)
-                    break;
-                case 8:
-                    if (kara) LC_IG_T(true, 1, split, ns, true, 8) else LC_IG_T(true, 1, split, ns, false, 8)
-                    break;
-                default:
-                    if (kara) LC_IG_T(true, 1, split, ns, true, 5) else LC_IG_T(true, 1, split, ns, false, 5)
-                    break;
-            }
+            if (kara) LC_IG_T(true, 1, split, ns, true) else LC_IG_T(true, 1, split, ns, false)
         }
         g_lc_launches += 1;
     }
     if (nw) {  // LC_TUNE_GROUP_WIDE_ITEMS
         if (c->tune[LC_TUNE_GROUP_WIDE_ITEMS] == 1) {
-            LC_IG_T(false, 1, wide, nw, false, 1)
+            LC_IG_T(false, 1, wide, nw, false)
         } else {
-            LC_IG_T(false, 2, wide, nw, false, 1)
+            LC_IG_T(false, 2, wide, nw, false)
         }
         g_lc_launches += 1;
     }
 #undef LC_IG_T
 #undef LC_IG
-#undef LC_IG_ONE
 }
 
 void op_gather_sum_qp(lc_ctx* c, const u64* src, size_t src_stride, u64* usum, int n_polys, int nl,

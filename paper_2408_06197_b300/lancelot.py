@@ -35,8 +35,6 @@ LC_TUNE_GROUP_WIDE_ITEMS = 4
 LC_TUNE_TENSOR_WARPS = 5
 LC_TUNE_NTT_ROW_TMA = 6
 LC_TUNE_GROUP_KARATSUBA = 7
-LC_TUNE_GROUP_SPLIT_MINB = 8
-LC_TUNE_GROUP_RING = 9
 LC_PROBE_IMAD, LC_PROBE_IMAD_WIDE, LC_PROBE_NTT_BFLY = 0, 1, 2
 TUNING_OPTIONS = {
     LC_TUNE_NTT_ROW_MINB: (4, 5, 6),
@@ -46,14 +44,11 @@ TUNING_OPTIONS = {
     LC_TUNE_TENSOR_WARPS: (16, 8, 12),
     LC_TUNE_NTT_ROW_TMA: (0, 1),
     LC_TUNE_GROUP_KARATSUBA: (1, 0),
-    LC_TUNE_GROUP_SPLIT_MINB: (5, 6, 8),
-    LC_TUNE_GROUP_RING: (0, 1),
 }
 TUNING_NAMES = {LC_TUNE_NTT_ROW_MINB: "ntt_row_minb", LC_TUNE_NTT_COL_MINB: "ntt_col_minb",
                 LC_TUNE_GROUP_SPLIT_ITEMS: "group_split_items", LC_TUNE_GROUP_WIDE_ITEMS: "group_wide_items",
                 LC_TUNE_TENSOR_WARPS: "tensor_warps", LC_TUNE_NTT_ROW_TMA: "ntt_row_tma",
-                LC_TUNE_GROUP_KARATSUBA: "group_karatsuba", LC_TUNE_GROUP_SPLIT_MINB: "group_split_minb",
-                LC_TUNE_GROUP_RING: "group_ring"}
+                LC_TUNE_GROUP_KARATSUBA: "group_karatsuba"}
 _ERRS = {-1: "LC_EINVAL", -2: "LC_ELEVEL", -3: "LC_ESCALE", -4: "LC_ENOMEM", -5: "LC_ECUDA",
          -6: "LC_ETIMEOUT", -7: "LC_EBUSY", -8: "LC_EKEY"}
 
