@@ -86,6 +86,14 @@ typedef struct {
  * group are summed after the key switching).  Identical results for groups of size 1;
  * a different rounding (not the same bits) for larger groups. */
 #define LC_HOIST_QP_SUM 2
+/* Level drop before the rotate-and-sum (or-ed into the mode of lc_distances / lc_ct_distances):
+ * each relinearised and rescaled pair is reduced to level l (its limbs q_0 .. q_l are kept, the
+ * others discarded -- a ciphertext mod Q is one mod every Q' dividing Q, with the same message
+ * while that message stays below Q'/2) and rotated and summed there: the rotations' key switches
+ * then work on l + 1 limbs instead of L.  Outputs are at level l.  0 <= l <= L - 1; without it
+ * the rotations run at level L - 1.  Different bits from the default (the ciphertexts have other
+ * limbs); the decrypted distances agree within the noise. */
+#define LC_ROTATE_AT_LEVEL(l) ((((uint32_t)(l)) + 1u) << 8)
 
 /* ---------------------------------------------------------------- parameters / context */
 
@@ -384,8 +392,10 @@ int lc_rotate_sum(lc_ctx* ctx, const lc_evk* evk, uint64_t* cts, uint32_t count,
 /* Encrypted pairwise squared distances (Algorithm 1, "Server Executes"), for every pair i<j
  * in lexicographic order: Dis = rotate_sum(rescale(relin(sum_k (ct_i[k] - ct_j[k])^2))).
  * cts: host or device [n][chunks][2][n_q][N] at level L and scale `scale`;
- * out: host or device [n(n-1)/2][2][n_q-1][N]; *out_scale = scale^2 / q_L.
- * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits), optionally | LC_HOIST_QP_SUM.
+ * out: host or device [n(n-1)/2][2][n_q-1][N] ([n(n-1)/2][2][l+1][N] with LC_ROTATE_AT_LEVEL(l));
+ * *out_scale = scale^2 / q_L.
+ * mode: LC_MODE_PER_OP or LC_MODE_BATCHED (same bits), optionally | LC_HOIST_QP_SUM and
+ * | LC_ROTATE_AT_LEVEL(l) (LC_ELEVEL for l > L - 1).
  * groups: hoisting schedule as in
  * lc_rotate_sum (NULL = all ones).  evk must hold the relinearisation key and every
  * rotation key the schedule needs (else LC_EKEY); a scale that is not finite and positive is

@@ -67,6 +67,8 @@ def lib():
         L.or_rotate_sum.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
         L.or_distances.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
                                    ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
+        L.or_distances_dropped.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
+                                           ctypes.c_int, vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp]
         L.or_masked_aggregate.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         _lib = L
     return _lib
@@ -373,10 +375,15 @@ class Context:
             raise KeyError("missing rotation key")
         return x
 
-    def distances(self, cts: np.ndarray, rlk, groups, rot_keys: dict, pairs=None, qp_sum: bool = False) -> np.ndarray:
-        """cts [n][chunks][2][L+1][N] -> [n_pairs][2][L][N] (i<j lexicographic, or `pairs`)."""
+    def distances(self, cts: np.ndarray, rlk, groups, rot_keys: dict, pairs=None, qp_sum: bool = False,
+                  rot_level: int | None = None) -> np.ndarray:
+        """cts [n][chunks][2][L+1][N] -> [n_pairs][2][L][N] (i<j lexicographic, or `pairs`).
+        rot_level: reduce each rescaled pair to that level (keep its limbs 0..rot_level) before the
+        rotate-and-sum; the output is then [n_pairs][2][rot_level+1][N]."""
         n, chunks = cts.shape[0], cts.shape[1]
         L = len(self.prm.q) - 1
+        if rot_level is not None:
+            return self._distances_dropped(cts, rlk, groups, rot_keys, pairs, qp_sum, rot_level)
         g = np.array(groups, dtype=np.int32)
         kr = np.array(list(rot_keys.keys()), dtype=np.int32)
         ks = [rot_keys[k] for k in rot_keys]
@@ -391,6 +398,27 @@ class Context:
         out = np.zeros((npairs, 2, L, self.N), dtype=np.uint64)
         st = lib().or_distances(self.h, _p(np.ascontiguousarray(cts)), n, chunks, _p(rlk), len(g), _p(g),
                                 len(kr), _p(kr), _ptr_array(ks), nsel, _p(pl), int(qp_sum), _p(out))
+        if st:
+            raise KeyError("missing rotation key")
+        return out
+
+    def _distances_dropped(self, cts, rlk, groups, rot_keys, pairs, qp_sum, rot_level):
+        n, chunks = cts.shape[0], cts.shape[1]
+        g = np.array(groups, dtype=np.int32)
+        kr = np.array(list(rot_keys.keys()), dtype=np.int32)
+        ks = [rot_keys[k] for k in rot_keys]
+        if pairs is None:
+            pl = np.zeros(2, dtype=np.int32)
+            nsel, npairs = 0, n * (n - 1) // 2
+        else:
+            pl = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
+            nsel = npairs = len(pairs)
+        out = np.zeros((npairs, 2, rot_level + 1, self.N), dtype=np.uint64)
+        st = lib().or_distances_dropped(self.h, _p(np.ascontiguousarray(cts)), n, chunks, _p(rlk), len(g), _p(g),
+                                        len(kr), _p(kr), _ptr_array(ks), nsel, _p(pl), int(qp_sum), int(rot_level),
+                                        _p(out))
+        if st == -2:
+            raise ValueError("rot_level outside [0, L-1]")
         if st:
             raise KeyError("missing rotation key")
         return out

@@ -815,9 +815,32 @@ int or_rotate_sum(OrCtx* c, u64* ct, int level, int n_groups, const int* groups,
 // cts: evaluation domain [n][chunks][2][L+1][N]; out: [n_pairs][2][L][N].
 // pair_list (optional, length 2*n_pairs_sel) restricts the work to the listed pairs, written
 // to out in list order.
+static int distances_at(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, int n_groups,
+                        const int* groups, int n_keys, const int* key_rot, const u64* const* keys,
+                        int n_sel, const int* pair_list, int qp_sum, int rot_level, u64* out);
+
 int or_distances(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, int n_groups,
                  const int* groups, int n_keys, const int* key_rot, const u64* const* keys,
                  int n_sel, const int* pair_list, int qp_sum, u64* out) {
+    return distances_at(c, cts, n, chunks, rlk, n_groups, groups, n_keys, key_rot, keys, n_sel, pair_list, qp_sum,
+                        c->nq - 2, out);
+}
+
+// The same with the rescaled pair reduced to level rot_level before the rotate-and-sum: a level
+// drop keeps the limbs q_0 .. q_rot_level and discards the others (a ciphertext mod Q is also one
+// mod any Q' dividing Q, encrypting the same message while that message stays below Q'/2).
+// out: [n_pairs][2][rot_level + 1][N].
+int or_distances_dropped(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, int n_groups,
+                         const int* groups, int n_keys, const int* key_rot, const u64* const* keys,
+                         int n_sel, const int* pair_list, int qp_sum, int rot_level, u64* out) {
+    if (rot_level < 0 || rot_level > c->nq - 2) return -2;
+    return distances_at(c, cts, n, chunks, rlk, n_groups, groups, n_keys, key_rot, keys, n_sel, pair_list, qp_sum,
+                        rot_level, out);
+}
+
+static int distances_at(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, int n_groups,
+                        const int* groups, int n_keys, const int* key_rot, const u64* const* keys,
+                        int n_sel, const int* pair_list, int qp_sum, int rot_level, u64* out) {
     const size_t N = c->N;
     const int L = c->nq - 1, nl = L + 1;
     const size_t P = (size_t)nl * N, CT = 2 * P;
@@ -844,9 +867,13 @@ int or_distances(OrCtx* c, const u64* cts, int n, int chunks, const u64* rlk, in
         std::vector<u64> r2(CT), rs(2 * (size_t)L * N);
         relin(*c, acc.data(), L, rlk, r2.data());
         rescale(*c, r2.data(), 2, L, rs.data());
-        int st = rotate_sum(*c, rs.data(), L - 1, n_groups, groups, n_keys, key_rot, keys, qp_sum != 0);
+        // level drop: keep limbs 0 .. rot_level of both polynomials
+        const size_t lo = (size_t)(rot_level + 1) * N;
+        std::vector<u64> y(2 * lo);
+        for (int p = 0; p < 2; p++) std::memcpy(y.data() + p * lo, rs.data() + (size_t)p * L * N, lo * sizeof(u64));
+        int st = rotate_sum(*c, y.data(), rot_level, n_groups, groups, n_keys, key_rot, keys, qp_sum != 0);
         if (st) status = st;
-        std::memcpy(out + (size_t)k * 2 * L * N, rs.data(), rs.size() * sizeof(u64));
+        std::memcpy(out + (size_t)k * 2 * lo, y.data(), y.size() * sizeof(u64));
     }
     return status;
 }

@@ -1713,6 +1713,11 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     const size_t Pin = (size_t)c->nq * N, Pout = (size_t)L * N;
     const int npairs = (int)(n * (n - 1) / 2);
     const bool qp = (mode & LC_HOIST_QP_SUM) != 0;
+    // rotate-and-sum level: L-1 (the rescaled pair as it is) unless a level drop is asked for
+    const uint32_t rl_code = (mode >> 8) & 255u;
+    const int rl = rl_code ? (int)rl_code - 1 : L - 1;
+    if (rl > L - 1) return fail(c, LC_ELEVEL, "lc_distances: rotation level above the rescaled level");
+    const size_t Prl = (size_t)(rl + 1) * N;  // words of one output polynomial
     mode &= 1u;
     std::vector<uint32_t> sched;
     if (n_groups == 0) {
@@ -1732,7 +1737,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     if (!find_key(evk, -1)) return fail(c, LC_EKEY, "relinearisation key missing");
     // host buffers are staged through device memory
     const bool in_host = is_host_ptr(cts), out_host = is_host_ptr(out);
-    const size_t in_words = (size_t)n * chunks * 2 * Pin, out_words = (size_t)npairs * 2 * Pout;
+    const size_t in_words = (size_t)n * chunks * 2 * Pin, out_words = (size_t)npairs * 2 * Prl;
     const u64* din = cts;
     u64* dout = out;
     if (in_host || out_host) {
@@ -1745,8 +1750,10 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         if (out_host) dout = sb + (in_host ? in_words : 0);
     }
     // per-item scratch: acc3 + ct2 + key-switch buffers + rotation outputs
+    // (with a level drop the rescaled pairs wait in scratch, 2 Pout words each, before their low
+    // limbs are copied out)
     const size_t per_item = 3 * Pin + 2 * Pin + std::max(ks_words(c, 1, L), rescale_words(c, 1, 2, L)) +
-                            std::max<size_t>(rotsum_words(c, 1, L - 1, maxg, qp), 0);
+                            std::max<size_t>(rotsum_words(c, 1, rl, maxg, qp), 0) + (rl < L - 1 ? 2 * Pout : 0);
     const int B = mode == LC_MODE_PER_OP ? 1 : max_batch_for(c, per_item, (size_t)8 << 30 >> 3);
     const int Bw = std::min(B, npairs);
     u64* t = lc_scratch(c, per_item * Bw * 8);
@@ -1757,7 +1764,8 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
     }
     u64* acc3 = t;
     u64* ct2 = acc3 + (size_t)Bw * 3 * Pin;
-    u64* tmp = ct2 + (size_t)Bw * 2 * Pin;
+    u64* yfull = ct2 + (size_t)Bw * 2 * Pin;                  // rescaled pairs before a level drop
+    u64* tmp = yfull + (rl < L - 1 ? (size_t)Bw * 2 * Pout : 0);
     for (int p0 = 0; p0 < npairs; p0 += Bw) {
         const int b = std::min(Bw, npairs - p0);
         {
@@ -1769,7 +1777,7 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         }
         int st = check_launch(c, "lc_distances (tensor accumulate)");
         if (st) return st;
-        u64* y = dout + (size_t)p0 * 2 * Pout;
+        u64* y = rl < L - 1 ? yfull : dout + (size_t)p0 * 2 * Prl;
         if (mode == LC_MODE_PER_OP) {  // one operation per launch sequence: relinearise, then rescale
             st = do_relin(c, evk, acc3, b, L, ct2, tmp);
             if (!st) st = check_launch(c, "lc_distances (relinearisation)");
@@ -1781,7 +1789,14 @@ int lc_distances(lc_ctx* c, const lc_evk* evk, const uint64_t* cts, uint32_t n, 
         }
         st = check_launch(c, "lc_distances (relinearisation + rescale)");
         if (st) return st;
-        st = do_rotate_sum(c, evk, y, b, L - 1, (int)sched.size(), sched.data(), tmp, qp);
+        if (rl < L - 1) {
+            // level drop: the limbs q_0 .. q_rl of each of the 2b polynomials, into the output
+            u64* yl = dout + (size_t)p0 * 2 * Prl;
+            LC_CUDA(c, cudaMemcpy2DAsync(yl, Prl * 8, y, Pout * 8, Prl * 8, (size_t)2 * b, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+            y = yl;
+        }
+        st = do_rotate_sum(c, evk, y, b, rl, (int)sched.size(), sched.data(), tmp, qp);
         if (!st) st = check_launch(c, "lc_distances (rotate-and-sum)");
         if (st) return st;
     }

@@ -394,8 +394,10 @@ int lc_ct_distances(lc_ctx* c, const lc_evk* evk, const lc_ct* const* clients, u
     }
     const u64* in = contiguous(c, clients, n, each, g, &st);
     if (!in) return st;
+    const uint32_t rl_code = (mode >> 8) & 255u;  // LC_ROTATE_AT_LEVEL: the outputs' level
+    if (rl_code > L) return hfail(c, LC_ELEVEL, "lc_ct_distances: rotation level above the rescaled level");
     lc_ct* h = nullptr;
-    st = new_ct(c, n * (n - 1) / 2, 2, L - 1, 1.0, &h);
+    st = new_ct(c, n * (n - 1) / 2, 2, rl_code ? rl_code - 1 : L - 1, 1.0, &h);
     if (st) return st;
     st = lc_distances(c, evk, in, n, chunks, scale, mode, n_groups, groups, h->data, &h->scale);
     if (st) {

@@ -238,6 +238,12 @@ def _whole(buf, unit: int, what: str) -> int:
     return n // unit
 
 
+def rotate_at_level(level: int) -> int:
+    """Mode bits of lc_distances that drop the rescaled pairs to `level` before the
+    rotate-and-sum (LC_ROTATE_AT_LEVEL)."""
+    return (int(level) + 1) << 8
+
+
 def launches() -> int:
     out = np.zeros(1, dtype=np.uint64)
     lib().lc_launches(_np_ptr(out))
@@ -839,15 +845,20 @@ class Context:
 
     # ------------------------------------------------------------------ the method
     def distances(self, evk: "EvalKeys", cts, n: int, chunks: int, scale: float, mode: int = LC_MODE_BATCHED,
-                  groups: Optional[Sequence[int]] = None, out=None):
-        """cts: [n][chunks][2][nq][N] (torch GPU tensor, or numpy uint64 in host memory)."""
+                  groups: Optional[Sequence[int]] = None, out=None, rot_level: Optional[int] = None):
+        """cts: [n][chunks][2][nq][N] (torch GPU tensor, or numpy uint64 in host memory).
+        rot_level: drop each rescaled pair to that level before the rotate-and-sum (outputs
+        [n_pairs][2][rot_level+1][N]); None keeps level L-1."""
         npairs = n * (n - 1) // 2
+        nl_out = self.L if rot_level is None else int(rot_level) + 1
+        if rot_level is not None:
+            mode = int(mode) | rotate_at_level(int(rot_level))
         host = isinstance(cts, np.ndarray)
         if out is None:
-            out = (np.empty((npairs, 2, self.L, self.N), dtype=np.uint64) if host
-                   else self.empty(npairs, 2, self.L, self.N))
+            out = (np.empty((npairs, 2, nl_out, self.N), dtype=np.uint64) if host
+                   else self.empty(npairs, 2, nl_out, self.N))
         _need(cts, n * chunks * 2 * self.nq * self.N, "distances: cts", host_ok=True)
-        _need(out, npairs * 2 * self.L * self.N, "distances: out", host_ok=True)
+        _need(out, npairs * 2 * nl_out * self.N, "distances: out", host_ok=True)
         g = np.array(list(groups) if groups else [], dtype=np.uint32)
         sc = ctypes.c_double()
         pin = _np_ptr(cts) if host else _t_ptr(cts)

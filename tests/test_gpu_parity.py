@@ -314,6 +314,43 @@ def prod_g3():
     return e
 
 
+def test_level_drop_distances_bit_exact_toy(toy):
+    """LC_ROTATE_AT_LEVEL(0): the rescaled pairs dropped to limb q_0 before the rotate-and-sum, in
+    both modes, bit-exact against the oracle's dropped distances; LC_ELEVEL above L - 1."""
+    LC = toy.LC
+    w, W, X, ocs, gcs = _toy_inputs(toy)
+    Do = toy.o.distances(ocs, toy.orlk, toy.sched, toy.ork, rot_level=0)
+    for mode in (LC.LC_MODE_BATCHED, LC.LC_MODE_PER_OP):
+        Dg, sc = toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale, mode=mode, rot_level=0)
+        assert Dg.shape == (w.n_pairs, 2, 1, toy.N)
+        assert np.array_equal(toy.g_coeff(Dg, 0), toy.o_coeff(Do))
+    with pytest.raises(LC.LancelotError, match="LC_ELEVEL"):
+        toy.g.distances(toy.gevk, gcs, w.n_clients, w.chunks, toy.prm.scale, rot_level=toy.L)
+
+
+def test_level_drop_distances_production_bit_exact(prod_g2):
+    """At N = 2^15: pairs rescaled to level 13 and dropped to level 1 (q_0 q_1, 100 bits) before
+    one-ModDown groups [2]*7, bit-exact against the oracle, every distance within 1e-5 of FP64."""
+    e = prod_g2
+    LC = e.LC
+    w = S.Workload("p3drop", S.CFG_PLAIN, 15, 3, 2 * e.prm.slots - 50, 4, (2,), "flip5", 1, 0)
+    W = S.client_updates(w)
+    X = S.split_chunks(W, e.prm.slots)
+    ocs, gcs = e.encrypt_both(X, range(3), range(w.chunks))
+    mode = LC.LC_MODE_BATCHED | LC.LC_HOIST_QP_SUM
+    Dg, sc = e.g.distances(e.gevk, gcs, 3, w.chunks, e.prm.scale, mode=mode, groups=e.sched, rot_level=1)
+    Do = e.o.distances(ocs, e.orlk, e.sched, e.ork, qp_sum=True, rot_level=1)
+    assert np.array_equal(e.g_coeff(Dg, 1), e.o_coeff(Do))
+    k = 0
+    for i in range(3):
+        for j in range(i + 1, 3):
+            ref = np.sum((W[i] - W[j]) ** 2)
+            v = e.g.decrypt(e.keys.s, Dg[k].contiguous(), 1, sc)
+            assert np.abs(v - ref).max() / ref < 1e-5
+            assert abs(e.g.decrypt_const(e.keys.s, Dg[k:k + 1].contiguous(), 1, sc)[0] - ref) / ref < 1e-5
+            k += 1
+
+
 def test_qp_sum_distances_production_bit_exact(prod_g2):
     e = prod_g2
     w = S.Workload("p3g2", S.CFG_PLAIN, 15, 3, e.prm.slots, 4, (2,), "flip5", 1, 0)

@@ -89,6 +89,10 @@ def test_handle_distances_and_aggregate_bit_exact_toy(htoy):
         assert np.array_equal(D.export(), e.o.to_coeff(Do))
         v = e.g.decrypt_values(e.sk, D.view(0, 1))
         assert np.abs(v - np.sum((W[0] - W[1]) ** 2)).max() <= toy_distance_tolerance(e.prm)
+    # a level drop before the rotations: the output handle is at that level
+    D0 = e.g.ct_distances(e.evk, e.clients_views(w, m, rnd), mode=LC.LC_MODE_BATCHED | LC.rotate_at_level(0))
+    assert D0.info()[:3] == (w.n_pairs, 2, 0)
+    assert np.array_equal(D0.export(), e.o.to_coeff(e.o.distances(ocs, e.orlk, e.sched, e.ork, rot_level=0)))
     om, gm = _masks(e, w.n_clients, [1.0, 0.0, 0.0, 0.0])
     Ao = e.o.masked_aggregate(ocs, om, e.orlk)
     for mode in (LC.LC_MODE_BATCHED, LC.LC_MODE_PER_OP):

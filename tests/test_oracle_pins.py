@@ -417,6 +417,46 @@ def test_toy_workload_end_to_end(toy):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
 
 
+def test_level_drop_before_rotations(toy):
+    """Distances with the rescaled pairs dropped to a lower level before the rotate-and-sum: at
+    the rescaled level itself the drop is the identity (bit-exact with the plain distances); one
+    level lower (limb q_0 only) every slot still decrypts to the FP64 distance within the toy
+    tolerance and Krum picks the same clients; a fresh ciphertext dropped to level 0 decrypts to
+    the same residues mod q_0 as the full one (a level drop keeps the message)."""
+    from paper_2408_06197_b300 import kgc
+
+    w, prm, ctx = toy["w"], toy["prm"], toy["ctx"]
+    W = S.client_updates(w)
+    X = S.split_chunks(W, prm.slots)
+    cts = np.zeros((w.n_clients, w.chunks, 2, prm.L + 1, prm.N), dtype=np.uint64)
+    for i in range(w.n_clients):
+        for k in range(w.chunks):
+            cts[i, k], _ = _enc(toy, X[i, k], i, k)
+    D = ctx.distances(cts, toy["rlk"], toy["sched"], toy["rk"])
+    assert np.array_equal(ctx.distances(cts, toy["rlk"], toy["sched"], toy["rk"], rot_level=prm.L - 1), D)
+    D0 = ctx.distances(cts, toy["rlk"], toy["sched"], toy["rk"], rot_level=0)
+    assert D0.shape == (w.n_pairs, 2, 1, prm.N)
+    sc = prm.scale ** 2 / prm.q[prm.L]
+    tol = toy_distance_tolerance(prm)
+    dist = np.zeros((w.n_clients, w.n_clients))
+    k = 0
+    for i in range(w.n_clients):
+        for j in range(i + 1, w.n_clients):
+            v = ctx.decrypt(toy["s"], D0[k], 0, sc)
+            ref = float(np.sum((W[i] - W[j]) ** 2))
+            assert np.abs(v - ref).max() <= tol
+            dist[i, j] = dist[j, i] = v[0]
+            k += 1
+    ref_d = np.array([[np.sum((W[i] - W[j]) ** 2) for j in range(w.n_clients)] for i in range(w.n_clients)])
+    assert kgc.krum_select(dist, f=w.f, n_select=w.n_select) == kgc.krum_select(ref_d, f=w.f, n_select=w.n_select)
+    # a fresh ciphertext dropped to level 0: its decryption residues mod q_0 are those of the
+    # full ciphertext
+    ct = cts[0, 0]
+    full = ctx.decrypt_residues(toy["s"], ct, prm.L)
+    low = ctx.decrypt_residues(toy["s"], np.ascontiguousarray(ct[:, :1]), 0)
+    assert np.array_equal(full[0], low[0])
+
+
 @pytest.mark.slow
 def test_production_parameters_square_relin_rescale_rotate():
     prm = O.params_production()
