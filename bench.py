@@ -458,9 +458,9 @@ SCHEDULES = _schedules()
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
-# forward 449.1 + 453.4 MB, inverse 452.7 + 443.8 MB per 960 limbs (column cap 8, row cap 4).
+# forward 449.1 + 453.1 MB, inverse 453.3 + 443.3 MB per 960 limbs (column cap 8, row cap 4).
 # Valid for the current transform kernels only.
-NTT_DRAM_BYTES_PER_LIMB = (449.1e6 + 453.4e6 + 452.7e6 + 443.8e6) / (2 * 960)
+NTT_DRAM_BYTES_PER_LIMB = (449.1e6 + 453.1e6 + 453.3e6 + 443.3e6) / (2 * 960)
 # SM throughput (% of peak) of the key-switch kernel classes in their ncu captures (k_inner_gather
 # 77-81 %, k_modup 80 %, k_moddown_bconv 78 %).  Static: ncu does not run inside the benchmark.
 KS_SM_PCT = {"inner": "77-81", "modup": "80", "moddown": "78"}
@@ -1201,6 +1201,39 @@ def main():
                  "form": "per-operation launches (one pair / chunk at a time), log-step rotations, 14 keys",
                  "batched_over_plain": (w.n_pairs / (ms_per_step / 1e3)) / (w.n_pairs / (pms / 1e3))}
 
+    # the same step with the rescaled pairs dropped to level 1 (q_0 q_1) before the rotate-and-sum
+    # (LC_ROTATE_AT_LEVEL(1)): the rotations' key switches on 2 limbs instead of 14 (beside the
+    # headline, which keeps the rotations at level 13)
+    level_drop = None
+    if args.mode == "batched" and not args.no_plain:
+        with torch.cuda.stream(stream):
+            out_d1 = g.empty(w.n_pairs, 2, 2, g.N)
+
+            def drop_step():
+                g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d1,
+                            rot_level=1)
+                g.masked_aggregate(evk, cts, w.n_clients, w.chunks, g.scale, masks, g.scale, mode=mode, out=out_a)
+            drop_step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                drop_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lms = e0.elapsed_time(e1) / 3
+            _, sc1 = g.distances(evk, cts, w.n_clients, w.chunks, g.scale, mode=dmode, groups=sched, out=out_d1,
+                                 rot_level=1)
+            got = g.decrypt_const(s, out_d1, 1, sc1)
+            W0 = S.client_updates(w)
+            ref = np.array([np.sum((W0[i] - W0[j]) ** 2) for i in range(w.n_clients) for j in range(i + 1, w.n_clients)])
+            del out_d1, W0
+        level_drop = {"rot_level": 1, "value": w.n_pairs / (lms / 1e3), "unit": UNIT, "ms_per_step": lms,
+                      "max_rel_err_vs_fp64": float(np.max(np.abs(got - ref) / ref)),
+                      "form": "same step with LC_ROTATE_AT_LEVEL(1): rescaled pairs reduced to q_0 q_1 before the "
+                              "rotate-and-sum (eager launches)"}
+
     # roofline of the dominant kernel class
     hbm, peak_kind = peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -1268,7 +1301,7 @@ def main():
                                       if tuning else g.tuning()),
                            "launch": "cuda_graph_replay" if use_graph else "eager"},
             "gpu_launches": launches, "clocks": ck, "roofline": roof, "e2e": e2e, "plain_form": plain,
-            "client_step": client, "step_parts": parts, "serving": serving,
+            "client_step": client, "step_parts": parts, "serving": serving, "level_drop": level_drop,
             "round_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                  "definition": "per-step device time of the fixed n=10 step (45 pair distances + "
                                                "masked aggregate of 64 chunks); served latencies are in 'serving'"}}
