@@ -51,3 +51,18 @@ def test_single_rank_helpers_need_no_process_group():
     import bench
     assert bench.max_over_ranks(1.25, 1) == 1.25
     assert bench.whole_job_rate(45, 1, 5, 0.2) == pytest.approx(1125.0)
+
+
+def test_both_arms_name_the_same_workload():
+    """The benchmark's own line and the reference arm's line carry one `config` (the workload and
+    its shape); run-specific details go elsewhere.  The schedules the bench can run are the
+    autotuner's search space."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cfg = bench.plain_config(1)
+    assert cfg == bench.plain_config(1) and cfg["workload"] == bench.WORKLOAD
+    assert (cfg["n_clients"], cfg["chunks"], cfg["pairs"], cfg["log_n"], cfg["limbs_q"]) == (10, 64, 45, 15, 15)
+    assert "l2" in cfg and "rotation_schedule" not in cfg
+    assert bench.plain_config(4)["parallelism"] == "replicas4"
+    assert bench.SCHEDULES["g3qp"] == [3, 3, 3, 3, 2] and bench.SCHEDULES["g4433qp"] == [4, 4, 3, 3]
+    assert bench.BFLY_MIN_INSTR == 19
