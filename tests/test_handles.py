@@ -204,3 +204,23 @@ def test_handle_distances_production_bit_exact():
     v = e.g.decrypt_values(e.sk, D.view(2, 1), 1)[0]
     ref = np.sum((W[1] - W[2]) ** 2)
     assert abs(v - ref) / ref < 1e-5
+
+
+def test_handle_edge_cases(htoy):
+    """An empty batch runs nothing; a view outside its handle, a zero-count view, a handle of no
+    ciphertexts as a client, and a single client are rejected; a zero-count handle exports
+    nothing and keeps its metadata."""
+    e, LC = htoy, htoy.LC
+    assert e.g.batch_run([]) == []
+    h = e.g.ct_create(3, 2, e.L, e.prm.scale)
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):
+        h.view(2, 2)
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):
+        h.view(0, 0)
+    empty = e.g.ct_create(0, 2, e.L, e.prm.scale)
+    assert empty.info() == (0, 2, e.L, e.prm.scale)
+    assert empty.export().shape == (0, 2, e.L + 1, e.N)
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):
+        e.g.ct_distances(e.evk, [empty, empty])
+    with pytest.raises(LC.LancelotError, match="LC_EINVAL"):
+        e.g.ct_distances(e.evk, [h])
