@@ -109,6 +109,11 @@ def test_import_export_round_trip_and_values(htoy):
     h = e.g.ct_import(coeffs, 2, e.L, e.prm.scale)
     assert h.info() == (w.n_clients, 2, e.L, e.prm.scale)
     assert np.array_equal(h.export(), coeffs)
+    # the handle's device words (evaluation domain) seen as a torch tensor, and a view's
+    t = h.tensor()
+    assert t.shape == (w.n_clients, 2, e.L + 1, e.N)
+    assert torch.equal(t, e.g.to_eval(e.LC.u64_to_torch(coeffs), e.L))
+    assert torch.equal(h.view(1, 2).tensor(), t[1:3])
     # values in, values out: encode + encrypt in one call, decrypt + decode in one call
     vals = X[0, 0][: e.prm.slots - 5]
     r, e0, e1 = (a[:1] for a in rnd)
