@@ -361,17 +361,19 @@ def run_probes(args):
 # (lazy Shoup Cooley-Tukey, twiddles in registers, no memory traffic) on every SM, live in the same
 # run at the same clock.  The IMAD probe checks the unit count behind it: 148 SMs x 64 32-bit
 # multiply-adds per clock x 2.03 GHz = 19.2 T/s nominal, 19.2 T/s measured on a B300.
-BFLY_INSTR = 21.65  # thread instructions per lazy butterfly of the register-resident probe (ncu)
+BFLY_INSTR = 17.78  # thread instructions per lazy butterfly of the register-resident probe (ncu)
 # The fewest thread instructions a lazy Shoup Cooley-Tukey butterfly on 64-bit words can take on
-# 32-bit integer pipes, counted from its partial products:
-#   high 64 bits of y * w'   4 partial products (3 wide + 1 high-half) + 3 carry additions   7
-#   low 64 bits of y * w     1 wide + 2 32-bit multiply-adds into the high word             3
-#   low 64 bits of t * q     the same                                                         3
-#   r = y w - t q            64-bit subtraction (low with borrow, high)                      2
-#   x + r, x + 2q - r        two 64-bit additions (three-input adds with carry)              4
-# = 19.  The issue bound of the SM (148 SMs x 4 schedulers x 32 lanes, one instruction per clock)
-# divided by it is the nominal integer roofline of the transforms.
-BFLY_MIN_INSTR = 19
+# 32-bit integer pipes, counted from its partial products, in the form the transforms use for the
+# primes below 2^46 (a quotient that may fall up to two short, products in [0, 4q)):
+#   quotient t ~ y * w' / 2^64   1 wide + 2 high-half products + 2 carry additions          5
+#   low 64 bits of y * w         1 wide + 2 32-bit multiply-adds into the high word         3
+#   low 64 bits of t * q         the same                                                     3
+#   r = y w - t q                64-bit subtraction (low with borrow, high)                  2
+#   x + r, x + 4q - r            two 64-bit additions (three-input adds with carry)          4
+# = 17 (19 with the exact quotient's four partial products, which the 60-bit primes keep).  The
+# issue bound of the SM (148 SMs x 4 schedulers x 32 lanes, one instruction per clock) divided by
+# it is the nominal integer roofline of the transforms.
+BFLY_MIN_INSTR = 17
 
 
 def alu_roofline(g, ntt_bytes: float, ntt_ms: float, sm_mhz):
@@ -458,12 +460,12 @@ SCHEDULES = _schedules()
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
-# forward 449.1 + 453.1 MB, inverse 453.3 + 443.3 MB per 960 limbs (column cap 8, row cap 4).
+# forward 457.1 + 453.4 MB, inverse 453.2 + 444.7 MB per 960 limbs (column cap 8, row cap 5).
 # Valid for the current transform kernels only.
-NTT_DRAM_BYTES_PER_LIMB = (449.1e6 + 453.1e6 + 453.3e6 + 443.3e6) / (2 * 960)
+NTT_DRAM_BYTES_PER_LIMB = (457.1e6 + 453.4e6 + 453.2e6 + 444.7e6) / (2 * 960)
 # SM throughput (% of peak) of the key-switch kernel classes in their ncu captures (k_inner_gather
-# 77-81 %, k_modup 80 %, k_moddown_bconv 78 %).  Static: ncu does not run inside the benchmark.
-KS_SM_PCT = {"inner": "77-81", "modup": "80", "moddown": "78"}
+# 68-78 %, k_modup 80 %, k_moddown_bconv 78 %).  Static: ncu does not run inside the benchmark.
+KS_SM_PCT = {"inner": "68-78", "modup": "80", "moddown": "78"}
 
 
 def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):

@@ -148,11 +148,11 @@ int lc_set_max_batch(lc_ctx* ctx, uint32_t max_items);
  * the GPU).  Every option computes identical results; only speed differs.  Unknown knobs or
  * options fail with LC_EINVAL and leave the setting unchanged.  Options (default first):
  *   LC_TUNE_NTT_ROW_MINB       row pass of the NTT: minimum resident 128-thread blocks, i.e. a
- *                              register cap: 4, 5, 6
+ *                              register cap: 5, 4, 6
  *   LC_TUNE_NTT_COL_MINB       column pass of the NTT: 8, 1 (no cap), 6, 7
  *   LC_TUNE_GROUP_SPLIT_ITEMS  one-ModDown group kernel, rows with primes below 2^40: items per
  *                              thread, 1 or 2
- *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 2 or 1
+ *   LC_TUNE_GROUP_WIDE_ITEMS   same, other rows: 1 or 2
  *   LC_TUNE_TENSOR_WARPS       batched distance tensor (primes below 2^40): warps per block,
  *                              16 (4 pair slots per thread), 8 (8 slots) or 12 (6 slots)
  *   LC_TUNE_NTT_ROW_TMA        forward row pass: 0 = one block per tile, 1 = persistent blocks

@@ -197,7 +197,7 @@ static int build_tables(lc_ctx* c) {
         {
             int b = 0;
             while (b < 64 && (q >> b)) b++;
-            const int s1 = std::max(0, b - 26), sh = b + 31 - s1;
+            const int s1 = std::max(0, b - 25), sh = b + 31 - s1;
             const u64 cc = (b + 31 < 128) ? (u64)(((lc::u128)1 << (b + 31)) / q) : 0;
             mc.lzr = (b <= 46 && cc < (1ull << 32)) ? (cc | (u64)s1 << 32 | (u64)sh << 40) : 0;
         }

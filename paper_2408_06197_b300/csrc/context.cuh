@@ -103,7 +103,7 @@ struct lc_ctx {
     uint64_t n_keyswitch = 0, n_modup = 0;
     uint32_t max_batch = 0;  // 0 = limited only by the scratch budget
     // tile-shape choices (LC_TUNE_*, set by lc_set_tuning; results never depend on them)
-    int tune[8] = {0, 4, 8, 1, 2, 16, 0, 1};  // [6] LC_TUNE_NTT_ROW_TMA, [7] LC_TUNE_GROUP_KARATSUBA
+    int tune[8] = {0, 5, 8, 1, 1, 16, 0, 1};  // [6] LC_TUNE_NTT_ROW_TMA, [7] LC_TUNE_GROUP_KARATSUBA
     bool debug = false;      // LC_DEBUG set: check every launch, remember the first failure
     std::string debug_err;
     bool capturing = false;  // inside lc_graph_begin / lc_graph_end

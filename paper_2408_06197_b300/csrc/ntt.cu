@@ -32,19 +32,49 @@ __device__ __forceinline__ u64* limb_ptr(u64* base, size_t batch_stride, const R
 // Two value-range disciplines, chosen per CTA from the limb's prime:
 //  * q >= 2^46 (the 50/60-bit primes): Harvey-lazy, forward values in [0, 4q) and inverse values in
 //    [0, 2q), one conditional subtraction per butterfly;
-//  * q < 2^46 (the 30/40-bit primes): no conditional subtraction inside the network.  Forward
-//    values grow by less than 2q per stage (at most 4q + 2q log2(N) < 2^52), inverse values at most
-//    double per stage (below 2^(s+2) q after s stages, < 2^64 for log2(N) <= 16), and the last
-//    stage reduces fully.  Outputs are the same canonical residues in both disciplines.
+//  * q < 2^46 (the 30/40-bit primes): no conditional subtraction inside the network, and the
+//    products take the three-partial-product quotient of mul_shoup_lazy4 (results in [0, 4q)).
+//    Forward values grow by less than 4q per stage (below 4q + 4q log2(N) <= 68q for inputs below
+//    4q and log2(N) <= 16, inside the range reduce_lazy takes); inverse values start below 2q and
+//    at most double per stage (below 2^(s+1) q after s >= 1 stages: each sum adds two such values,
+//    each product is below 4q), so the multiple 2^(b+1) q used at stage b is never below the
+//    subtracted value; the last stage reduces fully.  Outputs are the same canonical residues in
+//    both disciplines.
 constexpr u64 kLazyLimit = 1ull << 46;
 
-// Cooley-Tukey butterfly; t = y w (lazy Shoup) is in [0, 2q) for any y < 2^64
+// y w mod q up to 4q for any y < 2^64: the Shoup quotient floor(y w' / 2^64) from three of the
+// four 32-bit partial products of y w' -- the low x low product and the carry out of the sum of
+// the two middle products' low halves are left out, each of which moves the quotient by at most
+// one -- so the estimate is the exact quotient or up to two below it, and y w - t q, in [0, 2q)
+// with the exact one, lies in [0, 4q).
+// The estimate is y1 w'1 + hi32(y0 w'1) + hi32(y1 w'0) (two high-half products, their 33-bit sum
+// and one 32x32 -> 64-bit multiply-add), the remainder the chain of mul_sub_lo.
+__device__ __forceinline__ u64 mul_shoup_lazy4(u64 y, u64 w, u64 w_sh, u64 q) {
+    u64 t;
+    asm("{\n\t"
+        ".reg .u32 y0, y1, p0, p1, h1, h2, s0, s1;\n\t"
+        ".reg .u64 s;\n\t"
+        "mov.b64 {y0, y1}, %1;\n\t"
+        "mov.b64 {p0, p1}, %2;\n\t"
+        "mul.hi.u32 h1, y0, p1;\n\t"
+        "mul.hi.u32 h2, y1, p0;\n\t"
+        "add.cc.u32 s0, h1, h2;\n\t"
+        "addc.u32 s1, 0, 0;\n\t"
+        "mov.b64 s, {s0, s1};\n\t"
+        "mad.wide.u32 %0, y1, p1, s;\n\t"
+        "}"
+        : "=l"(t)
+        : "l"(y), "l"(w_sh));
+    return mul_sub_lo(y, w, t, 0 - q);
+}
+
+// Cooley-Tukey butterfly; t = y w is in [0, 4q) (LZ) or [0, 2q) (exact lazy Shoup) for any y
 template <bool LZ>
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64 two_q) {
     const u64 xr = LZ ? x : csub(x, two_q);
-    const u64 t = mul_shoup_lazy(y, w.x, w.y, q);
+    const u64 t = LZ ? mul_shoup_lazy4(y, w.x, w.y, q) : mul_shoup_lazy(y, w.x, w.y, q);
     x = xr + t;
-    y = xr + two_q - t;
+    y = xr + (LZ ? two_q << 1 : two_q) - t;
 }
 // Gentleman-Sande butterfly; ky is a multiple of q not below y (LZ), else y < 2q
 template <bool LZ>
@@ -52,7 +82,7 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, ulonglong2 w, u64 q, u64
     const u64 a = x + y;
     const u64 b = x + (LZ ? ky : two_q) - y;
     x = LZ ? a : csub(a, two_q);
-    y = mul_shoup_lazy(b, w.x, w.y, q);
+    y = LZ ? mul_shoup_lazy4(b, w.x, w.y, q) : mul_shoup_lazy(b, w.x, w.y, q);
 }
 
 // swizzle for the row-pass tile: XOR word bits 0..3 with bits 4..7

@@ -37,10 +37,10 @@ LC_TUNE_NTT_ROW_TMA = 6
 LC_TUNE_GROUP_KARATSUBA = 7
 LC_PROBE_IMAD, LC_PROBE_IMAD_WIDE, LC_PROBE_NTT_BFLY = 0, 1, 2
 TUNING_OPTIONS = {
-    LC_TUNE_NTT_ROW_MINB: (4, 5, 6),
+    LC_TUNE_NTT_ROW_MINB: (5, 4, 6),
     LC_TUNE_NTT_COL_MINB: (8, 1, 6, 7),
     LC_TUNE_GROUP_SPLIT_ITEMS: (1, 2),
-    LC_TUNE_GROUP_WIDE_ITEMS: (2, 1),
+    LC_TUNE_GROUP_WIDE_ITEMS: (1, 2),
     LC_TUNE_TENSOR_WARPS: (16, 8, 12),
     LC_TUNE_NTT_ROW_TMA: (0, 1),
     LC_TUNE_GROUP_KARATSUBA: (1, 0),
