@@ -85,6 +85,56 @@ def test_ntt_roundtrip_and_negacyclic_product(env):
         assert np.array_equal(prod_coef[i], env.o.poly_mul(i, a[i], b[i]))
 
 
+def _extreme_polys(prm, N):
+    """Inputs at the edges of the residue range: all q - 1, alternating 0 / q - 1, a single
+    spike, and values in the top 2^10 of [0, q) -- the largest intermediate values a lazy
+    transform sees, where a quotient estimate that falls short matters most."""
+    rng = np.random.default_rng(11)
+    out = []
+    for kind in range(4):
+        rows = []
+        for q in prm.q:
+            q = np.uint64(q)
+            if kind == 0:
+                v = np.full(N, q - np.uint64(1), dtype=np.uint64)
+            elif kind == 1:
+                v = np.where(np.arange(N) % 2 == 0, np.uint64(0), q - np.uint64(1)).astype(np.uint64)
+            elif kind == 2:
+                v = np.zeros(N, dtype=np.uint64)
+                v[N // 3] = q - np.uint64(1)
+            else:
+                v = q - np.uint64(1) - rng.integers(0, 1 << 10, size=N, dtype=np.uint64)
+            rows.append(v)
+        out.append(np.stack(rows))
+    return out
+
+
+def test_ntt_extreme_inputs(env):
+    """Transforms of extreme vectors, where the lazy ranges are widest: forward outputs are
+    canonical and invert exactly; extreme evaluation vectors survive inverse-then-forward; and
+    the negacyclic product of two extreme polynomials (forward, pointwise, inverse) equals the
+    oracle's product in every limb.  (The two sides' evaluation orders and roots differ, so
+    evaluation vectors are not compared across them.)"""
+    LC, g, L = env.LC, env.g, env.L
+    polys = _extreme_polys(env.prm, env.N)
+    evals = []
+    for a in polys:
+        e = g.to_eval(LC.u64_to_torch(a), L)
+        eh = LC.torch_to_u64(e)
+        assert all((eh[i] < np.uint64(q)).all() for i, q in enumerate(env.prm.q))
+        assert np.array_equal(env.g_coeff(e, L), a)
+        # the same words read as an evaluation vector: inverse, then forward, returns them
+        v = LC.u64_to_torch(a)
+        assert np.array_equal(LC.torch_to_u64(g.to_eval(g.to_coeff(v, L), L)), a)
+        evals.append(e)
+    z = torch.zeros_like(evals[0])
+    for ia, ib in ((0, 0), (0, 1), (1, 3), (2, 3)):
+        t = g.tensor(torch.stack([evals[ia], z]).contiguous(), torch.stack([evals[ib], z]).contiguous(), L)
+        prod = env.g_coeff(t[0].contiguous(), L)
+        for i in range(L + 1):
+            assert np.array_equal(prod[i], env.o.poly_mul(i, polys[ia][i], polys[ib][i])), (ia, ib, i)
+
+
 def test_encoder_matches_oracle(env):
     z = np.random.default_rng(2).normal(0, 0.01, env.prm.slots)
     mg = env.g.encode(z, env.prm.scale)
