@@ -464,8 +464,8 @@ SCHEDULES = _schedules()
 # Valid for the current transform kernels only.
 NTT_DRAM_BYTES_PER_LIMB = (457.1e6 + 453.4e6 + 453.2e6 + 444.7e6) / (2 * 960)
 # SM throughput (% of peak) of the key-switch kernel classes in their ncu captures (k_inner_gather
-# 68-78 %, k_modup 80 %, k_moddown_bconv 78 %).  Static: ncu does not run inside the benchmark.
-KS_SM_PCT = {"inner": "68-78", "modup": "80", "moddown": "78"}
+# 68-78 %, k_modup 81 %, k_moddown_bconv 82 %).  Static: ncu does not run inside the benchmark.
+KS_SM_PCT = {"inner": "68-78", "modup": "81", "moddown": "82"}
 
 
 def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):
