@@ -457,6 +457,9 @@ def _schedules():
 # the hoisting schedules at N = 2^15: "log" (14 single rotations), g2qp ([2]*7), g3qp
 # ([3,3,3,3,2]) and every other composition of 14 into one-ModDown groups of at most 4 bits
 SCHEDULES = _schedules()
+# the schedule the autotuner picks for the benchmark workload on a B300 (every run so far); the
+# reference arm, which cannot time GPU candidates, runs the oracle with it
+REFERENCE_SCHEDULE = "g4433qp"
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
@@ -556,31 +559,35 @@ def oracle_sample(w: S.Workload, reps: int = 1, sched_name: str = "g3qp"):
 
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on the host cores.  Each step is a bounded
-    sample of the workload -- the encrypted distance of one pair (64 chunks, the benchmark's
-    one-ModDown schedule [3,3,3,3,2]) and the masked aggregate of one chunk -- and ms_per_step is
-    that sample's measured time; the throughput is the workload's (45 pairs + 64 chunks per
-    step) at the sample's per-pair and per-chunk times."""
+    sample of the workload -- the encrypted distance of one pair (64 chunks, the one-ModDown
+    schedule the benchmark's autotuner picks on a B300, [4,4,3,3], unless --schedule names
+    another) and the masked aggregate of one chunk -- and ms_per_step is that sample's measured
+    time; the throughput is the workload's (45 pairs + 64 chunks per step) at the sample's
+    per-pair and per-chunk times."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
     w = S.PLAIN
     total = args.warmup + args.steps
-    _, per, threads, _ = oracle_sample(w, reps=total)
+    sname = REFERENCE_SCHEDULE if args.schedule == "auto" else args.schedule
+    groups = SCHEDULES[sname]
+    _, per, threads, _ = oracle_sample(w, reps=total, sched_name=sname)
     timed = per[args.warmup:]
     t_pair = statistics.median(p[0] for p in timed)
     t_chunk = statistics.median(p[1] for p in timed)
     full_step = w.n_pairs * t_pair + w.chunks * t_chunk
     value = w.n_pairs / full_step
     sample_ms = statistics.mean(p[0] + p[1] for p in timed) * 1e3
-    sample = (f"per step: oracle distances of 1 pair (64 chunks, rotation schedule g3qp = one-ModDown groups "
-              f"[3,3,3,3,2], 31 rotation keys) and masked aggregate of 1 chunk ({sample_ms:.0f} ms measured); "
+    sample = (f"per step: oracle distances of 1 pair (64 chunks, rotation schedule {sname} = one-ModDown groups "
+              f"{groups}, {sum((1 << gb) - 1 for gb in groups)} rotation keys) and masked aggregate of 1 chunk "
+              f"({sample_ms:.0f} ms measured); "
               f"throughput at the workload's 45 pairs + 64 chunks per step (median pair {t_pair:.2f} s, chunk "
               f"{t_chunk:.2f} s -> {full_step:.1f} s per full step)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sample_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": plain_config(world),
-            "run_detail": {"rotation_schedule": "g3qp", "sample_units_per_step": "1 pair + 1 aggregate chunk",
+            "run_detail": {"rotation_schedule": sname, "sample_units_per_step": "1 pair + 1 aggregate chunk",
                            "full_step_s": full_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
