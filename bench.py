@@ -198,7 +198,8 @@ def run_batched(args):
 
 def run_uneven(args):
     """The uneven batch at full size: 8 jobs (seed 2), each with its own key set (relinearisation +
-    the 31 rotation keys of the [3,3,3,3,2] schedule), n in {5,10,20,40}, d in {2^16..2^22}
+    the rotation keys of the schedule: [4,4,3,3], 44 keys, unless --schedule names another), n in
+    {5,10,20,40}, d in {2^16..2^22}
     (147 GB of ciphertexts resident), distances + masked aggregates of all jobs per step in
     shared launches (lc_batch_distances / lc_batch_aggregate: ragged pair and chunk lists packed
     into waves).  Beside it, the same jobs one after another through lc_distances /
@@ -209,7 +210,8 @@ def run_uneven(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream(0)
-    sched = SCHEDULES["g3qp"]
+    sname = REFERENCE_SCHEDULE if args.schedule == "auto" else args.schedule
+    sched = SCHEDULES[sname]
     jobs_w = S.uneven_jobs()
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=0, stream=stream)
@@ -324,7 +326,7 @@ def run_uneven(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic (GPU encode + encryption with device randomness)",
             "config": {"workload": "uneven_8jobs_seed2_n{5,10,20,40}_d{2^16..2^22}",
                        "jobs": [{"n": w.n_clients, "d": w.d, "chunks": w.chunks, "pairs": w.n_pairs} for w in jobs_w],
-                       "pairs": n_pairs, "pair_chunks": pair_chunks, "rotation_schedule": "g3qp",
+                       "pairs": n_pairs, "pair_chunks": pair_chunks, "rotation_schedule": sname,
                        "launch": "lc_batch_distances + lc_batch_aggregate (shared waves)",
                        "l2": "inputs larger than L2 (147 GB client ciphertexts resident)"},
             "pair_chunks_per_s": pair_chunks / (ms / 1e3), "clocks": ck,
@@ -887,7 +889,7 @@ def run_serving(args):
     stream = torch.cuda.Stream(local)
     with torch.cuda.stream(stream):
         g = LC.Context.production(device=local, stream=stream)
-        sname = "g3qp" if args.schedule == "auto" else args.schedule
+        sname = REFERENCE_SCHEDULE if args.schedule == "auto" else args.schedule
         sched = SCHEDULES[sname]
         flags = LC.LC_HOIST_QP_SUM if sname.endswith("qp") else 0
         st = ServingSetup(args, g, local, sched, flags)
