@@ -109,20 +109,15 @@ def _extreme_polys(prm, N):
     return out
 
 
-def test_ntt_extreme_inputs(env):
-    """Transforms of extreme vectors, where the lazy ranges are widest: forward outputs are
-    canonical and invert exactly; extreme evaluation vectors survive inverse-then-forward; and
-    the negacyclic product of two extreme polynomials (forward, pointwise, inverse) equals the
-    oracle's product in every limb.  (The two sides' evaluation orders and roots differ, so
-    evaluation vectors are not compared across them.)"""
-    LC, g, L = env.LC, env.g, env.L
-    polys = _extreme_polys(env.prm, env.N)
+def _check_extreme_transforms(LC, g, o, prm):
+    L = len(prm.q) - 1
+    polys = _extreme_polys(prm, prm.N)
     evals = []
     for a in polys:
         e = g.to_eval(LC.u64_to_torch(a), L)
         eh = LC.torch_to_u64(e)
-        assert all((eh[i] < np.uint64(q)).all() for i, q in enumerate(env.prm.q))
-        assert np.array_equal(env.g_coeff(e, L), a)
+        assert all((eh[i] < np.uint64(q)).all() for i, q in enumerate(prm.q))
+        assert np.array_equal(LC.torch_to_u64(g.to_coeff(e, L)), a)
         # the same words read as an evaluation vector: inverse, then forward, returns them
         v = LC.u64_to_torch(a)
         assert np.array_equal(LC.torch_to_u64(g.to_eval(g.to_coeff(v, L), L)), a)
@@ -130,9 +125,31 @@ def test_ntt_extreme_inputs(env):
     z = torch.zeros_like(evals[0])
     for ia, ib in ((0, 0), (0, 1), (1, 3), (2, 3)):
         t = g.tensor(torch.stack([evals[ia], z]).contiguous(), torch.stack([evals[ib], z]).contiguous(), L)
-        prod = env.g_coeff(t[0].contiguous(), L)
+        prod = LC.torch_to_u64(g.to_coeff(t[0].contiguous(), L))
         for i in range(L + 1):
-            assert np.array_equal(prod[i], env.o.poly_mul(i, polys[ia][i], polys[ib][i])), (ia, ib, i)
+            assert np.array_equal(prod[i], o.poly_mul(i, polys[ia][i], polys[ib][i])), (ia, ib, i)
+
+
+def test_ntt_extreme_inputs(env):
+    """Transforms of extreme vectors, where the lazy ranges are widest: forward outputs are
+    canonical and invert exactly; extreme evaluation vectors survive inverse-then-forward; and
+    the negacyclic product of two extreme polynomials (forward, pointwise, inverse) equals the
+    oracle's product in every limb.  (The two sides' evaluation orders and roots differ, so
+    evaluation vectors are not compared across them.)"""
+    _check_extreme_transforms(env.LC, env.g, env.o, env.prm)
+
+
+@pytest.mark.parametrize("log_n", [15, 16])
+def test_ntt_extreme_inputs_at_the_lazy_limit(log_n):
+    """The same checks with 46-bit primes, the largest that the transforms run without in-network
+    reductions and with the three-product quotient (forward values up to 68q before the final
+    reduction), at N = 2^15 and 2^16 (16 stages, the widest ranges)."""
+    from paper_2408_06197_b300 import lancelot as LC
+    q = O.gen_primes(log_n, 60, 0, 1) + O.gen_primes(log_n, 46, 0, 3)
+    p = O.gen_primes(log_n, 60, 1, 1)
+    assert all((1 << 45) < x < (1 << 46) for x in q[1:])
+    prm = O.Params(log_n, q, p, 4, float(2 ** 40))
+    _check_extreme_transforms(LC, LC.Context(log_n, q, p, 4, float(2 ** 40)), O.Context(prm), prm)
 
 
 def test_encoder_matches_oracle(env):
