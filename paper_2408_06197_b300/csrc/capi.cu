@@ -186,6 +186,21 @@ static int build_tables(lc_ctx* c) {
         }
         const u64 last = hmul(pwi[lc::bit_reverse(1, c->log_n)], ninv, q);
         inv[m * N + 0] = make_ulonglong2(last, shoup_of(last, q));
+        // entries [N / 2^(b+1), N / 2^b) serve only the row-pass stages b = 0, 1, 2 (the last
+        // three forward stages, the first three inverse ones); store each group of 16 * s entries
+        // (s = 2^(3-b), one group per 256-word block) lane-interleaved: entry lo * s + v at
+        // v * 16 + lo (the device's tw_row_slot)
+        for (int b = 0; b < 3; b++) {
+            const size_t base = N >> (b + 1), s = (size_t)8 >> b, grp = 16 * s;
+            for (ulonglong2* t : {&fwd[m * N], &inv[m * N]}) {
+                std::vector<ulonglong2> g(grp);
+                for (size_t g0 = base; g0 < 2 * base; g0 += grp) {
+                    for (size_t lo = 0; lo < 16; lo++)
+                        for (size_t v = 0; v < s; v++) g[v * 16 + lo] = t[g0 + lo * s + v];
+                    std::copy(g.begin(), g.end(), t + g0);
+                }
+            }
+        }
         ModConst& mc = c->mc_host[m];
         mc.q = q;
         mc.two_q = 2 * q;

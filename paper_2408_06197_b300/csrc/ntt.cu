@@ -90,6 +90,16 @@ __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 4) & 15); }
 
 __device__ __forceinline__ ulonglong2 ldtw(const ulonglong2* t, int i) { return __ldg(t + i); }
 
+// Slot of the twiddle of the row-pass stages b = 0..3 that pair word g0 + 16 lo + u with its
+// partner (g0 a multiple of 256, lo < 16, u < 16): logically entry 2^(log_n-1-b) +
+// ((g0 + 16 lo + u) >> (b+1)).  The tables store each group of 16 * 2^(3-b) consecutive entries of
+// the stages b = 0..2 lane-interleaved (entry lo * 2^(3-b) + v of a group at v * 16 + lo, see
+// the table build), so that for one u the 16 lanes of a half-warp read 16 consecutive entries;
+// for b = 3 the two orders coincide.
+__device__ __forceinline__ int tw_row_slot(int log_n, int b, int g0, int lo, int u) {
+    return (1 << (log_n - 1 - b)) + (g0 >> (b + 1)) + ((u >> (b + 1)) << 4) + lo;
+}
+
 // ------------------------------------------------------------------------------ column pass
 // forward: row bits C-1 .. 0 (global bits log_n-1 .. 8)
 template <int C, bool LZ>
@@ -273,10 +283,8 @@ __device__ __forceinline__ void fwd_row_body(const u64* in, u64* a, u64* s, cons
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            // j = (g0 + 16 lo) + u with the bracket a multiple of 16: offset u >> (b+1)
-            ct_bfly<LZ>(x[u], x[u | (1 << st)],
-                        ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))), mc.q,
-                        mc.two_q);
+            // twiddle (g0 + 16 lo + u) >> (b+1) of the stage, stored lane-interleaved (tw_row_slot)
+            ct_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, tw_row_slot(log_n, b, g0, lo, u)), mc.q, mc.two_q);
         }
     }
 #pragma unroll
@@ -381,9 +389,8 @@ __device__ __forceinline__ void inv_row_body(u64* a, u64* s, const ModConst& mc,
 #pragma unroll
         for (int u = 0; u < 16; u++) {
             if (u >> st & 1) continue;
-            gs_bfly<LZ>(x[u], x[u | (1 << st)],
-                        ldtw(tw, (1 << (log_n - 1 - b)) + ((g0 + 16 * lo) >> (b + 1)) + (u >> (b + 1))), mc.q,
-                        mc.two_q, mc.two_q << b);
+            gs_bfly<LZ>(x[u], x[u | (1 << st)], ldtw(tw, tw_row_slot(log_n, b, g0, lo, u)), mc.q, mc.two_q,
+                        mc.two_q << b);
         }
     }
 #pragma unroll
