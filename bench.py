@@ -465,9 +465,9 @@ REFERENCE_SCHEDULE = "g4433qp"
 
 # DRAM bytes per limb of one transform (column + row pass, N = 2^15), from the ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 960-limb case of `bench.py --micro`:
-# forward 457.1 + 453.4 MB, inverse 453.2 + 444.7 MB per 960 limbs (column cap 8, row cap 5).
+# forward 457.0 + 454.4 MB, inverse 453.0 + 444.9 MB per 960 limbs (column cap 8, row cap 5).
 # Valid for the current transform kernels only.
-NTT_DRAM_BYTES_PER_LIMB = (457.1e6 + 453.4e6 + 453.2e6 + 444.7e6) / (2 * 960)
+NTT_DRAM_BYTES_PER_LIMB = (457.0e6 + 454.4e6 + 453.0e6 + 444.9e6) / (2 * 960)
 # SM throughput (% of peak) of the key-switch kernel classes in their ncu captures (k_inner_gather
 # 68-78 %, k_modup 81 %, k_moddown_bconv 82 %).  Static: ncu does not run inside the benchmark.
 KS_SM_PCT = {"inner": "68-78", "modup": "81", "moddown": "82"}
