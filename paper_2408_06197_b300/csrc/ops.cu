@@ -974,10 +974,11 @@ struct RowSel {
 // sum minus the other two is the middle term h l' + l h' (Karatsuba); every term is a
 // non-negative integer, (h + l)(h' + l') < 2^42 and at most 60 of them are summed, so the
 // partial sums stay below 2^48 and the result is the same integer.
-// Register caps with one item per thread: 5 resident blocks for the split rows, 3 for the 128-bit
-// ones (164-168 registers instead of 208, no spills: 4 % faster than uncapped).
+// Register caps with one item per thread: 4 resident blocks for the split rows (128 registers;
+// 5 blocks: 96 registers and 1.5 % slower, 3 blocks: 6 % slower), 3 for the 128-bit ones (164-168
+// registers instead of 208, no spills: 4 % faster than uncapped).
 template <int T, bool ITEMS, bool SPLIT, int kBT, bool KARA = false>
-__global__ void __launch_bounds__(kTG, kBT == 1 ? (SPLIT ? 5 : 3) : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
+__global__ void __launch_bounds__(kTG, kBT == 1 ? (SPLIT ? 4 : 3) : 1) k_inner_gather(const u64* __restrict__ ext, const u64* __restrict__ d,
                                                      size_t d_stride, const u64* __restrict__ y0, size_t y0_stride,
                                                      int B, int beta, int nl, int rows, int alpha, int nq, int nqp,
                                                      int log_n, KeyPtrs keys, const u64* const* __restrict__ keys_dev,
