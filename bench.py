@@ -469,8 +469,8 @@ REFERENCE_SCHEDULE = "g4433qp"
 # Valid for the current transform kernels only.
 NTT_DRAM_BYTES_PER_LIMB = (457.0e6 + 454.4e6 + 453.0e6 + 444.9e6) / (2 * 960)
 # SM throughput (% of peak) of the key-switch kernel classes in their ncu captures (k_inner_gather
-# 68-78 %, k_modup 81 %, k_moddown_bconv 82 %).  Static: ncu does not run inside the benchmark.
-KS_SM_PCT = {"inner": "68-78", "modup": "81", "moddown": "82"}
+# 68-79 %, k_modup 81 %, k_moddown_bconv 82 %).  Static: ncu does not run inside the benchmark.
+KS_SM_PCT = {"inner": "68-79", "modup": "81", "moddown": "82"}
 
 
 def build_workload(LC, g, w: S.Workload, sched_name: str = "auto"):
